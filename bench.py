@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the quasi-static slice advance on one GB300 (or N replicas).
+
+A "step" is one 3D step of the method: the driver current deposit, the full
+xi-slice loop (deposit, psi / E_z, B_z / B_perp multigrid solves, moments,
+explicit sources, push, adaptive sub-steps) and the frozen-field driver push.
+The workload is the 256^2 blowout case: [-8,8]^2, 1024 base slices over a
+12 k_p^-1 window, 4 plasma particles per cell (262,144), a driver (n_b = 5,
+sigma_r = 0.3, sigma_z = 0.7, 500k macroparticles) and a witness (n_b = 2,
+sigma_z = 0.3, 200k).  Inputs are synthetic (seeded bi-Gaussian beams, lattice
+plasma).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "blowout256"
+METRIC = "xi_slices_per_s"
+UNIT = "slices/s"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--form", default="fp64", choices=["fp64", "fp32r", "both"])
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="target CPU time of the oracle baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default=WORKLOAD)
+    return p.parse_args()
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload_desc(wl):
+    beams = ", ".join(f"n_b={b.amplitude:g} sigma_r={b.sigma_x:g} sigma_z={b.sigma_z:g} "
+                      f"xi_c={b.xi_c:g} N={b.n_particles}" for b in wl.beams)
+    return (f"{wl.name}: {wl.n}x{wl.n} cells over [-{wl.half_width:g},{wl.half_width:g}]^2, "
+            f"{wl.n_xi} base xi-slices over {wl.xi_len:g}, {wl.ppc} ppc "
+            f"({wl.n_plasma} plasma macroparticles), beams [{beams}], refine_k={wl.refine_k}, "
+            f"mg_tol={wl.mg_tol:g}, dt={wl.dt:g}")
+
+
+# ---------------------------------------------------------------- roofline model
+def algorithmic_bytes(stats, wl, b: int, n_xi: int) -> float:
+    """Bytes one slice-engine launch must move at minimum (the design doc model):
+    particles 14b per particle per pushed slice (5b on the last slice), grid
+    phases 50b per point per slice + 10b per point per base slice, multigrid
+    24b per component-point per V-cycle plus 8b per point per screened cycle."""
+    nn = wl.n * wl.n
+    np_ = wl.n_plasma
+    slices = stats["slices"]
+    part = (14 * (slices - 1) + 5) * b * np_
+    grid = (50 * slices + 10 * n_xi) * b * nn
+    v = stats["vcycles"]
+    mg = (v[0] * 24 + v[1] * 48 + v[2] * 56) * b * nn
+    return float(part + grid + mg)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- native arm
+def run_native(args):
+    import numpy as np
+    import torch
+
+    import paper_2012_00881_gb300 as qs
+    import workloads as W
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = W.workload(args.workload)
+    forms = ["fp64", "fp32r"] if args.form == "both" else [args.form]
+    beams_np = [W.sample_beam(b) for b in wl.beams]
+    beam_bytes = sum(7 * 8 * len(b["x"]) for b in beams_np)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    results = {}
+    for form in forms:
+        cfg = qs.config_from_workload(wl, precision=form)
+        ctx = qs.Context(cfg)
+        if wl.profile is None:
+            ctx.init_plasma(wl.ppc)
+        else:
+            ctx.init_plasma(wl.ppc, wl.profile[0], wl.profile[1])
+        master = [qs.Beam(b, device=dev) for b in beams_np]
+        beams = [qs.Beam(b, device=dev) for b in beams_np]
+
+        def reset_beams():
+            for src, dst in zip(master, beams):
+                for k in qs.Beam.KEYS:
+                    dst.t[k].copy_(src.t[k])
+
+        def one_step():
+            st = ctx.step3d(beams)
+            ctx.push_beam(beams, wl.dt)
+            return st
+
+        for _ in range(args.warmup):
+            reset_beams()
+            one_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        times, engine_ms, slices, pushes, bytes_alg = [], [], 0, 0, 0.0
+        vc = [0, 0, 0]
+        max_m = 0
+        for _ in range(args.steps):
+            reset_beams()
+            flush.zero_()  # evict L2 between timed steps (outside the events)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = one_step()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            engine_ms.append(st["gpu_ms"])
+            slices += st["slices"]
+            pushes += st["pushes"]
+            vc = [a + b for a, b in zip(vc, st["vcycles"])]
+            max_m = max(max_m, st["max_m"])
+            bytes_alg += algorithmic_bytes(st, wl, 8 if form == "fp64" else 4, wl.n_xi)
+        clocks = sampler.stop()
+        total_ms = sum(times)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        # end to end through the public API with host buffers
+        host = [{k: torch.as_tensor(b[k]).pin_memory() for k in qs.Beam.KEYS} for b in beams_np]
+        back = [{k: torch.empty_like(h[k]).pin_memory() for k in qs.Beam.KEYS} for h in host]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_slices = 0
+        for _ in range(args.steps):
+            for hb, db in zip(host, beams):
+                for k in qs.Beam.KEYS:
+                    db.t[k].copy_(hb[k], non_blocking=True)
+            st = one_step()
+            e2e_slices += st["slices"]
+            for bb, db in zip(back, beams):
+                for k in qs.Beam.KEYS:
+                    bb[k].copy_(db.t[k], non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        eng_s = sum(engine_ms) / 1e3
+        achieved = bytes_alg / eng_s / 1e9
+        results[form] = dict(
+            value=slices * world / (total_ms / 1e3),
+            pushes_per_s=pushes * world / (total_ms / 1e3),
+            ms_per_step=total_ms / args.steps,
+            slices_per_step=slices / args.steps,
+            vcycles_per_step=[v / args.steps for v in vc],
+            max_m=max_m,
+            engine_ms_per_step=eng_s * 1e3 / args.steps,
+            roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": achieved / hbm_peak, "traffic": None,
+                      "kernel": "slice_engine", "peak_source": peak_src,
+                      "bytes_per_launch": bytes_alg / args.steps},
+            e2e={"value": e2e_slices * world / e2e_s, "unit": UNIT,
+                 "h2d_bytes_per_step": beam_bytes, "d2h_bytes_per_step": beam_bytes},
+            clocks=clocks,
+            gpu_launches=args.steps * (1 + 2 * len(beams)),
+        )
+        ctx.close()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    main_form = "fp32r" if "fp32r" in results else forms[0]
+    r = results[main_form]
+    out = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if main_form == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": _workload_desc(wl), "form": main_form,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "history and beam grid larger than L2; 256 MB write between steps"},
+        "pushes_per_s": r["pushes_per_s"],
+        "slices_per_step": r["slices_per_step"],
+        "vcycles_per_step": r["vcycles_per_step"],
+        "roofline": r["roofline"],
+        "e2e": r["e2e"],
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
+        "forms": {k: {kk: v[kk] for kk in ("value", "pushes_per_s", "ms_per_step",
+                                            "slices_per_step", "vcycles_per_step", "max_m")}
+                  for k, v in results.items()},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------- oracle timing
+def _oracle_sample(wl, seconds: float):
+    """Time the FP64 oracle on the first base slices of one 3D step of the
+    workload, growing the slice count until about `seconds` of CPU work."""
+    import oracle as O
+    import workloads as W
+
+    cfg = O.config_from_workload(wl)
+    pl, n_ion = O.plasma_from_workload(wl)
+    beams = [W.sample_beam(b) for b in wl.beams]
+    t0 = time.perf_counter()
+    jzb = O.deposit_beam(cfg, beams)
+    t_dep = time.perf_counter() - t0
+    n = 2
+    while True:
+        t0 = time.perf_counter()
+        r = O.step3d(cfg, pl, n_ion, beams, jzb=jzb, n_slices=n)
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * seconds or n >= wl.n_xi:
+            break
+        n = min(wl.n_xi, max(n + 1, int(n * max(2.0, 0.5 * seconds / max(dt, 1e-3)))))
+    return r, dt, n, t_dep
+
+
+def cpu_baseline(wl, seconds: float):
+    r, dt, n, t_dep = _oracle_sample(wl, seconds)
+    return {"value": r.slices / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} base slices ({r.slices} computed slices) of one 3D step of "
+                      f"{wl.name}, numpy/scipy FP64, single thread; driver deposit excluded "
+                      f"({t_dep:.1f} s)",
+            "pushes_per_s": r.pushes / dt}
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import workloads as W
+    wl = W.workload(args.workload)
+    per_step = max(2.0, args.cpu_seconds / 2)
+    vals, slices, secs = [], 0, 0.0
+    for i in range(args.warmup + args.steps):
+        r, dt, n, _ = _oracle_sample(wl, per_step)
+        if i >= args.warmup:
+            vals.append(r.slices / dt)
+            slices += r.slices
+            secs += dt
+    v = slices / secs
+    sample = (f"first {n} base slices of one 3D step of {wl.name} per step, numpy/scipy FP64, "
+              f"single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": _workload_desc(wl), "form": "oracle"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_native(a)

@@ -1,0 +1,219 @@
+/*
+ * qs.h -- C ABI of libqs, a single-GPU (GB300, sm_103a) implementation of the
+ * quasi-static xi-slice advance of Wang, Khudik, Kim and Shvets, "WAND-PIC: an
+ * accelerated three-dimensional quasi-static particle-in-cell code"
+ * (arXiv 2012.00881).
+ *
+ * Units are the paper's normalised units (Sec. 3, first paragraph): time in
+ * 1/omega_p, lengths in 1/k_p, momenta in mc, fields in m c omega_p / e,
+ * densities in n0, current density in -e n0 c (electron flux).  xi = t - z
+ * grows from the head of the window backwards (Sec. 2, item 1).
+ *
+ * Conventions shared by every entry point
+ *   - Grids are cell-centred, nx = ny = N cells on a square box;
+ *     h = (x_max - x_min) / N.  2D arrays are row-major [iy][ix], ix fastest.
+ *   - Fields are zero on the box walls (odd ghost cells).  Particles reflect
+ *     specularly at the walls.  CIC weight that falls into a ghost cell is
+ *     folded back into the mirror interior cell (deposits conserve charge);
+ *     gathers use the same weights.
+ *   - Every function returns QS_OK (0) or a negative QS_ERR_* status; nothing
+ *     aborts, traps or throws across the ABI.  qs_strerror() names a status;
+ *     qs_last_error() gives the context's last detailed message.
+ *   - Device pointers are CUDA device addresses on the context's device.
+ *     Caller-owned buffers stay owned by the caller; the library never frees
+ *     them.  The library allocates its own state at qs_create /
+ *     qs_init_plasma and frees it at qs_destroy.
+ *   - All work is issued on the stream given to qs_create.  Calls that return
+ *     results to the host (qs_step3d with stats, qs_fields to a host buffer,
+ *     qs_slice_diagnostics, qs_get_plasma) synchronise that stream.
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define QS_OK 0
+#define QS_ERR_ARG (-1)            /* invalid argument or configuration      */
+#define QS_ERR_CUDA (-2)           /* a CUDA runtime call failed             */
+#define QS_ERR_OOM (-3)            /* device allocation failed               */
+#define QS_ERR_NOT_CONVERGED (-4)  /* a multigrid solve hit mg_max_vcycles;   */
+                                   /* fields hold the last iterate            */
+#define QS_ERR_PSI_FLOOR (-5)      /* 1+psi fell below psi_floor more often   */
+                                   /* than max_psi_guard_hits allows          */
+#define QS_ERR_STATE (-6)          /* calls out of order (e.g. no plasma)     */
+#define QS_ERR_TIMEOUT (-7)        /* a device-side wait exceeded its limit;  */
+                                   /* the kernel returned early               */
+
+/* ---- arithmetic forms -------------------------------------------------- */
+#define QS_FP64 0          /* every step in float64                          */
+#define QS_FP32_REFINED 1  /* float32 particles, smoothing and grid transfers; */
+                           /* float64 residuals, defect correction, coarsest */
+                           /* solve and gamma reconstruction                  */
+
+/* ---- field selection for qs_fields (order of the output blocks) -------- */
+#define QS_FIELD_PSI 1  /* wake potential psi = phi - A_z (Eq. EqM_N8_AA)  */
+#define QS_FIELD_EZ 2   /* E_z (Eq. EqM_N8_A)                              */
+#define QS_FIELD_BZ 4   /* B_z (Eq. Mag_z_A)                               */
+#define QS_FIELD_BX 8   /* B_x (Eq. Main_Eq_A)                             */
+#define QS_FIELD_BY 16  /* B_y (Eq. Main_Eq_A)                             */
+#define QS_FIELD_JZB 32 /* driver-beam j_z deposited on the base slices     */
+#define QS_FIELD_ALL 31
+
+typedef struct qs_ctx qs_ctx; /* opaque, library-owned */
+
+/* Problem description (Sec. 3 normalised units).  Fill with
+ * qs_config_default() and override. */
+typedef struct {
+    int nx, ny;                 /* transverse cells; nx == ny == N required;   */
+                                /* N = c * 2^L with coarsest side c <= 8       */
+    double x_min, x_max;        /* box edges; the box must be square           */
+    double y_min, y_max;
+    int n_xi;                   /* base xi slices                               */
+    double xi_min, xi_max;      /* window; dxi0 = (xi_max - xi_min) / n_xi      */
+    int refine_k;               /* smallest sub-step is dxi0 / refine_k         */
+                                /* (refinement level k of Sec. 5.1), >= 1       */
+    int precision;              /* QS_FP64 or QS_FP32_REFINED                   */
+    double mg_tol;              /* stop when ||f - A u||_2 <= mg_tol ||f||_2    */
+    int mg_max_vcycles;         /* per solve; exceeding it -> NOT_CONVERGED     */
+    double psi_floor;           /* 1+psi is clamped to >= psi_floor             */
+    int64_t max_psi_guard_hits; /* -1: unlimited                                */
+    int sort_every;             /* cell-sort the plasma every this many slices; */
+                                /* 0 = only at the start of a step              */
+    int pre_sweeps, post_sweeps;/* red-black Gauss-Seidel sweeps per level      */
+    int reserved[8];            /* must be zero                                  */
+} qs_config;
+
+/* Driver-beam macroparticles: structure of arrays of float64, n entries each.
+ * For qs_step3d / qs_push_beam the arrays are DEVICE pointers owned by the
+ * caller.  x, y in 1/k_p; xi = t - z in 1/k_p; p in mc; w = number of beam
+ * particles per macroparticle in units of n0 / k_p^3. */
+typedef struct {
+    double *x, *y, *xi, *px, *py, *pz, *w;
+    int64_t n;
+    double charge;   /* charge per particle in units of e (electron: -1)     */
+    double q_over_m; /* charge/mass in units of e/m (electron: -1)           */
+} qs_beam;
+
+/* Counters of one qs_step3d call. */
+typedef struct {
+    int64_t slices;          /* computed slices including sub-steps          */
+    int64_t substeps;        /* computed slices that are not base slices     */
+    int64_t pushes;          /* plasma macroparticle pushes                  */
+    int64_t vcycles[3];      /* V-cycles (or outer refinement iterations):   */
+                             /* [0] psi, [1] (E_z, B_z), [2] (B_x, B_y)       */
+    int64_t psi_guard_hits;  /* clamps of 1+psi (particles and grid points)  */
+    int64_t sorts;           /* cell sorts performed                          */
+    double max_relres;       /* largest final relative residual of any solve */
+    double vmax;             /* largest V_max of any push                     */
+    int32_t max_m;           /* largest sub-step count of any base interval   */
+    int32_t status;          /* same as the return value                      */
+    double gpu_ms;           /* device time of the slice loop (CUDA events)   */
+} qs_step_stats;
+
+/* Defaults: N = 64 on [-6,6]^2, 128 slices on [0,12], refine_k = 8,
+ * QS_FP64, mg_tol = 1e-10, 60 V-cycles, psi_floor = 1e-3, unlimited guard
+ * hits, sort_every = 16, V(2,2). */
+void qs_config_default(qs_config *cfg);
+
+/* Create a context on the current CUDA device; `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Allocates the grids, the
+ * multigrid hierarchy and the base-slice history (6 * n_xi * N^2 float64).
+ * Errors: QS_ERR_ARG (bad config), QS_ERR_OOM, QS_ERR_CUDA. */
+int qs_create(const qs_config *cfg, void *cuda_stream, qs_ctx **out);
+
+/* Free everything the context owns.  NULL is accepted. */
+void qs_destroy(qs_ctx *ctx);
+
+/* Plasma macroparticles at the head of the window (Sec. 3.1: cold plasma,
+ * H = 1, P = 0 before the driver arrives).  A quiet-start lattice of
+ * sqrt(ppc) x sqrt(ppc) particles per cell at offsets (k + 1/2)/sqrt(ppc) of
+ * a cell, p_perp = 0, weight n(r0) h^2 / ppc and id = cell * ppc + k.  The
+ * transverse density n(r) is interpolated piecewise-linearly from
+ * `profile[0..n_coef-1]` at equispaced radii on [0, r_max] (held beyond
+ * r_max); profile == NULL means n = 1.  `profile` is a HOST array.  The ion
+ * background of Eq. EqM_N8_AA is the deposit of this lattice.
+ * Errors: QS_ERR_ARG (ppc not a perfect square, n_coef < 1, r_max <= 0). */
+int qs_init_plasma(qs_ctx *ctx, int ppc, const double *profile, int n_coef, double r_max);
+
+/* One 3D step with the drivers frozen: the xi loop of Algorithm 1
+ * (Collect_Source, Solve_Wakefield, Push_Trajectory, Step_Size_Refinement)
+ * from the unperturbed lattice at xi_min over all n_xi base slices.
+ * Per slice: n_* deposit; psi from lap psi = n_* - n_ion (Eq. EqM_N8_AA);
+ * moments j_perp, T, n_*<gamma> (Eqs. Jr, FluxPres); E_z, B_z (Eqs.
+ * EqM_N8_A, Mag_z_A); B_perp from lap B - n_* / (1+psi) B = -e_z x S with the
+ * explicit source S of Eq. FluxCurr1_A (Eq. Main_Eq_A), no predictor-
+ * corrector; Boris-like push of Eqs. EoM_112_A/EoM_111; then
+ * m = min(refine_k, max(1, ceil(V_max / V0))) sub-steps of dxi0/m for the
+ * next base interval, V0 = h / dxi0 (Algorithm 1, Step_Size_Refinement).
+ * Multigrid solves warm-start from the previous slice (Sec. 7.1).  The
+ * drivers enter through j_z only: CIC in x, y and linear in xi on the base
+ * slices, -charge * w * v_z; sub-steps interpolate linearly in xi.  Fields of
+ * the base slices are stored for qs_fields and qs_push_beam.
+ * `beams` holds n_beams descriptors with DEVICE arrays (n_beams may be 0).
+ * `stats` (may be NULL) receives the counters; the call then synchronises.
+ * Errors: QS_ERR_STATE (no plasma), QS_ERR_ARG, QS_ERR_NOT_CONVERGED,
+ * QS_ERR_PSI_FLOOR, QS_ERR_TIMEOUT, QS_ERR_CUDA. */
+int qs_step3d(qs_ctx *ctx, const qs_beam *beams, int n_beams, qs_step_stats *stats);
+
+/* As qs_step3d, with the sub-step count of every base interval fixed to
+ * m_schedule[j] (HOST array of n_xi ints in [1, refine_k]) instead of the
+ * adaptive rule; used to replay a schedule. */
+int qs_step3d_schedule(qs_ctx *ctx, const qs_beam *beams, int n_beams,
+                       const int32_t *m_schedule, qs_step_stats *stats);
+
+/* Push_Driver of Algorithm 1: advance every beam macroparticle by one
+ * relativistic Boris step of length dt (Eqs. EoM_beam_1/2) in the wake stored
+ * by the last qs_step3d: E = e_z E_z + E_perp, B = e_z B_z + B_perp with
+ * E_perp = -grad psi - e_z x B_perp (the sign that follows from psi = phi -
+ * A_z; the paper prints "+").  Fields are gathered by CIC in x, y and
+ * linearly in xi between base slices; outside the box or the window the
+ * wake is zero.  xi advances by dt (1 - v_z).  Arrays are updated IN PLACE
+ * (DEVICE pointers).  Errors: QS_ERR_STATE (no step yet), QS_ERR_ARG. */
+int qs_push_beam(qs_ctx *ctx, qs_beam *beams, int n_beams, double dt);
+
+/* Copy base-slice fields [slice_begin, slice_end) into `out`, laid out
+ * [field][slice][iy][ix] for the fields selected in `field_mask` in the
+ * order psi, E_z, B_z, B_x, B_y, j_z(beam).  `out` is a device pointer if
+ * out_on_device != 0, else a host pointer (the call then synchronises).
+ * Errors: QS_ERR_ARG (empty mask, bad range), QS_ERR_STATE. */
+int qs_fields(qs_ctx *ctx, int field_mask, int slice_begin, int slice_end, double *out,
+              int out_on_device);
+
+/* Per-base-slice diagnostics of the last step (HOST arrays of n_xi entries;
+ * any may be NULL): m[j] sub-steps used from slice j, vmax[j] = V_max after
+ * the last push of interval j, charge[j] = sum of n_* h^2 at slice j (equal
+ * to the sum of plasma weights by Eq. continuity).  Synchronises. */
+int qs_slice_diagnostics(qs_ctx *ctx, int32_t *m, double *vmax, double *charge);
+
+/* Copy the current plasma macroparticles (after the last step, or the
+ * initial lattice) to HOST arrays of qs_plasma_count() entries, in the
+ * library's current storage order; any pointer may be NULL.  Synchronises. */
+int qs_get_plasma(qs_ctx *ctx, double *x, double *y, double *px, double *py, double *w,
+                  int32_t *id);
+int64_t qs_plasma_count(const qs_ctx *ctx);
+
+/* Stable counting sort of n particles by cell, c = iy * N + ix with
+ * ix = floor((x - x_min) / h) clamped to [0, N-1], ties in ascending id.
+ * DEVICE arrays: x, y (float64, n), id (int32, n) in; cell (int32, n),
+ * count (int32, N^2), offset (int32, N^2 + 1) and perm (int32, n: input
+ * positions in sorted order) out.  The same routine the slice loop uses to
+ * keep particles in cell-ordered tiles.  Synchronises. */
+int qs_cell_sort(qs_ctx *ctx, const double *x, const double *y, const int32_t *id, int64_t n,
+                 int32_t *cell, int32_t *count, int32_t *offset, int32_t *perm);
+
+/* Name of a status code (static string). */
+const char *qs_strerror(int status);
+
+/* Last detailed error message of a context ("" if none). */
+const char *qs_last_error(const qs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_H */

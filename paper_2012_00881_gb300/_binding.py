@@ -1,0 +1,297 @@
+"""ctypes binding of libqs (include/qs.h): argument marshalling only.
+
+Every step of the slice advance runs in the CUDA library; this module only
+converts torch tensors to device pointers and structs to ctypes.  If the
+library is missing, loading fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional, Sequence
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libqs.so")
+
+QS_OK = 0
+QS_ERR_ARG = -1
+QS_ERR_CUDA = -2
+QS_ERR_OOM = -3
+QS_ERR_NOT_CONVERGED = -4
+QS_ERR_PSI_FLOOR = -5
+QS_ERR_STATE = -6
+QS_ERR_TIMEOUT = -7
+QS_FP64 = 0
+QS_FP32_REFINED = 1
+FIELD_PSI, FIELD_EZ, FIELD_BZ, FIELD_BX, FIELD_BY, FIELD_JZB = 1, 2, 4, 8, 16, 32
+FIELD_ALL = 31
+FIELD_NAMES = ("psi", "Ez", "Bz", "Bx", "By", "jzb")
+
+
+class QsConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("x_min", ctypes.c_double), ("x_max", ctypes.c_double),
+        ("y_min", ctypes.c_double), ("y_max", ctypes.c_double),
+        ("n_xi", ctypes.c_int),
+        ("xi_min", ctypes.c_double), ("xi_max", ctypes.c_double),
+        ("refine_k", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("mg_tol", ctypes.c_double),
+        ("mg_max_vcycles", ctypes.c_int),
+        ("psi_floor", ctypes.c_double),
+        ("max_psi_guard_hits", ctypes.c_int64),
+        ("sort_every", ctypes.c_int),
+        ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
+        ("reserved", ctypes.c_int * 8),
+    ]
+
+
+class QsBeam(ctypes.Structure):
+    _fields_ = [
+        ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("xi", ctypes.c_void_p),
+        ("px", ctypes.c_void_p), ("py", ctypes.c_void_p), ("pz", ctypes.c_void_p),
+        ("w", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("charge", ctypes.c_double), ("q_over_m", ctypes.c_double),
+    ]
+
+
+class QsStepStats(ctypes.Structure):
+    _fields_ = [
+        ("slices", ctypes.c_int64), ("substeps", ctypes.c_int64), ("pushes", ctypes.c_int64),
+        ("vcycles", ctypes.c_int64 * 3), ("psi_guard_hits", ctypes.c_int64),
+        ("sorts", ctypes.c_int64), ("max_relres", ctypes.c_double), ("vmax", ctypes.c_double),
+        ("max_m", ctypes.c_int32), ("status", ctypes.c_int32), ("gpu_ms", ctypes.c_double),
+    ]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+# name -> (restype, argtypes), mirroring include/qs.h
+PROTOTYPES = {
+    "qs_config_default": (None, [ctypes.POINTER(QsConfig)]),
+    "qs_create": (_I, [ctypes.POINTER(QsConfig), _P, ctypes.POINTER(_P)]),
+    "qs_destroy": (None, [_P]),
+    "qs_init_plasma": (_I, [_P, _I, _P, _I, _D]),
+    "qs_step3d": (_I, [_P, _P, _I, ctypes.POINTER(QsStepStats)]),
+    "qs_step3d_schedule": (_I, [_P, _P, _I, _P, ctypes.POINTER(QsStepStats)]),
+    "qs_push_beam": (_I, [_P, _P, _I, _D]),
+    "qs_fields": (_I, [_P, _I, _I, _I, _P, _I]),
+    "qs_slice_diagnostics": (_I, [_P, _P, _P, _P]),
+    "qs_get_plasma": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "qs_plasma_count": (_I64, [_P]),
+    "qs_cell_sort": (_I, [_P, _P, _P, _P, _I64, _P, _P, _P, _P]),
+    "qs_strerror": (ctypes.c_char_p, [_I]),
+    "qs_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libqs.so (built in-tree by build()).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libqs.so not found at {path}; run paper_2012_00881_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in PROTOTYPES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class QsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def default_config(**overrides) -> QsConfig:
+    lib = load_library()
+    cfg = QsConfig()
+    lib.qs_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def config_from_workload(wl, precision: Optional[str] = None, **overrides) -> QsConfig:
+    prec = precision or wl.precision
+    cfg = default_config(
+        nx=wl.n, ny=wl.n, x_min=-wl.half_width, x_max=wl.half_width, y_min=-wl.half_width,
+        y_max=wl.half_width, n_xi=wl.n_xi, xi_min=0.0, xi_max=wl.xi_len,
+        refine_k=wl.refine_k, precision=QS_FP64 if prec == "fp64" else QS_FP32_REFINED,
+        mg_tol=wl.mg_tol, psi_floor=wl.psi_floor)
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+class Beam:
+    """Driver macroparticles as float64 CUDA tensors (caller-owned memory)."""
+
+    KEYS = ("x", "y", "xi", "px", "py", "pz", "w")
+
+    def __init__(self, arrays: Dict, charge: float = -1.0, q_over_m: float = -1.0, device="cuda"):
+        import torch
+        self.t = {k: torch.as_tensor(arrays[k], dtype=torch.float64, device=device).contiguous()
+                  for k in self.KEYS}
+        self.charge = float(arrays.get("charge", charge)) if isinstance(arrays, dict) else charge
+        self.q_over_m = float(arrays.get("q_over_m", q_over_m)) if isinstance(arrays, dict) else q_over_m
+
+    @property
+    def n(self) -> int:
+        return int(self.t["x"].numel())
+
+    def struct(self) -> QsBeam:
+        b = QsBeam()
+        for k in self.KEYS:
+            setattr(b, k, _ptr(self.t[k]))
+        b.n = self.n
+        b.charge = self.charge
+        b.q_over_m = self.q_over_m
+        return b
+
+    def numpy(self) -> Dict:
+        out = {k: v.detach().cpu().numpy() for k, v in self.t.items()}
+        out["charge"] = self.charge
+        out["q_over_m"] = self.q_over_m
+        return out
+
+
+def _beam_array(beams: Sequence[Beam]):
+    arr = (QsBeam * max(1, len(beams)))()
+    for i, b in enumerate(beams):
+        arr[i] = b.struct()
+    return arr
+
+
+class Context:
+    """One slice-advance problem on the current CUDA device (qs_ctx)."""
+
+    def __init__(self, cfg: QsConfig, stream=None):
+        import torch
+        self.lib = load_library()
+        self.cfg = cfg
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = _P()
+        st = self.lib.qs_create(ctypes.byref(cfg), _P(stream.cuda_stream), ctypes.byref(h))
+        if st != QS_OK:
+            raise QsError(st, "qs_create: " + self.lib.qs_strerror(st).decode())
+        self.h = h
+
+    # ---- helpers
+    def _check(self, st: int, what: str):
+        if st != QS_OK:
+            msg = self.lib.qs_last_error(self.h).decode()
+            raise QsError(st, f"{what}: {self.lib.qs_strerror(st).decode()}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n(self) -> int:
+        return self.cfg.nx
+
+    @property
+    def n_xi(self) -> int:
+        return self.cfg.n_xi
+
+    # ---- API
+    def init_plasma(self, ppc: int, profile: Optional[Sequence[float]] = None, r_max: float = 1.0):
+        if profile is None:
+            st = self.lib.qs_init_plasma(self.h, ppc, None, 0, 0.0)
+        else:
+            arr = (ctypes.c_double * len(profile))(*[float(v) for v in profile])
+            st = self.lib.qs_init_plasma(self.h, ppc, ctypes.cast(arr, _P), len(profile), float(r_max))
+        self._check(st, "qs_init_plasma")
+
+    def step3d(self, beams: Sequence[Beam] = (), schedule: Optional[Sequence[int]] = None,
+               raise_on_error: bool = True) -> Dict:
+        arr = _beam_array(beams)
+        stats = QsStepStats()
+        if schedule is None:
+            st = self.lib.qs_step3d(self.h, ctypes.cast(arr, _P), len(beams), ctypes.byref(stats))
+        else:
+            sch = (ctypes.c_int32 * len(schedule))(*[int(v) for v in schedule])
+            st = self.lib.qs_step3d_schedule(self.h, ctypes.cast(arr, _P), len(beams),
+                                             ctypes.cast(sch, _P), ctypes.byref(stats))
+        if raise_on_error:
+            self._check(st, "qs_step3d")
+        return dict(status=st, slices=stats.slices, substeps=stats.substeps, pushes=stats.pushes,
+                    vcycles=list(stats.vcycles), psi_guard_hits=stats.psi_guard_hits,
+                    sorts=stats.sorts, max_relres=stats.max_relres, vmax=stats.vmax,
+                    max_m=stats.max_m, gpu_ms=stats.gpu_ms)
+
+    def push_beam(self, beams: Sequence[Beam], dt: float):
+        arr = _beam_array(beams)
+        self._check(self.lib.qs_push_beam(self.h, ctypes.cast(arr, _P), len(beams), float(dt)),
+                    "qs_push_beam")
+
+    def fields(self, mask: int = FIELD_ALL, begin: int = 0, end: Optional[int] = None,
+               device: bool = True):
+        """Base-slice fields as a float64 tensor [field][slice][iy][ix]."""
+        import torch
+        end = self.n_xi if end is None else end
+        nf = bin(mask).count("1")
+        shape = (nf, end - begin, self.n, self.n)
+        if device:
+            out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        else:
+            out = torch.empty(shape, dtype=torch.float64).pin_memory()
+        self._check(self.lib.qs_fields(self.h, mask, begin, end, _ptr(out), 1 if device else 0),
+                    "qs_fields")
+        return out
+
+    def slice_diagnostics(self):
+        import numpy as np
+        m = np.zeros(self.n_xi, dtype=np.int32)
+        vm = np.zeros(self.n_xi)
+        ch = np.zeros(self.n_xi)
+        self._check(self.lib.qs_slice_diagnostics(self.h, m.ctypes.data, vm.ctypes.data,
+                                                  ch.ctypes.data), "qs_slice_diagnostics")
+        return m, vm, ch
+
+    def plasma(self):
+        import numpy as np
+        n = int(self.lib.qs_plasma_count(self.h))
+        arrs = [np.zeros(n) for _ in range(5)]
+        pid = np.zeros(n, dtype=np.int32)
+        self._check(self.lib.qs_get_plasma(self.h, *[a.ctypes.data for a in arrs], pid.ctypes.data),
+                    "qs_get_plasma")
+        return dict(zip(("x", "y", "px", "py", "w"), arrs), id=pid)
+
+    def cell_sort(self, x, y, pid):
+        """Run the library's cell sort on CUDA tensors; returns (cell, count, offset, perm)."""
+        import torch
+        n = int(x.numel())
+        m = self.n * self.n
+        cell = torch.empty(n, dtype=torch.int32, device="cuda")
+        count = torch.empty(m, dtype=torch.int32, device="cuda")
+        offset = torch.empty(m + 1, dtype=torch.int32, device="cuda")
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        self._check(self.lib.qs_cell_sort(self.h, _ptr(x), _ptr(y), _ptr(pid), n, _ptr(cell),
+                                          _ptr(count), _ptr(offset), _ptr(perm)), "qs_cell_sort")
+        return cell, count, offset, perm

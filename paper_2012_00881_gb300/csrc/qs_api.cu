@@ -1,0 +1,575 @@
+// Host side of the libqs C ABI (declared in include/qs.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "qs_internal.cuh"
+
+struct qs_ctx {
+    qs_config cfg;
+    cudaStream_t st = nullptr;
+    int dev = 0;
+    int N = 0;
+    double h = 0.0;
+    int nlev = 0;
+    int lev_n[QS_MAX_LEV] = {};
+    std::vector<void *> allocs;
+    // grids
+    double *n_a = nullptr, *n_b = nullptr, *n_ion = nullptr;
+    double *jx = nullptr, *jy = nullptr, *txx = nullptr, *txy = nullptr, *tyy = nullptr,
+           *G = nullptr;
+    double *psi = nullptr, *ez = nullptr, *bz = nullptr, *bx = nullptr, *by = nullptr;
+    double *f_psi = nullptr, *f_ez = nullptr, *f_bz = nullptr, *f_bx = nullptr, *f_by = nullptr;
+    double *dpx = nullptr, *dpy = nullptr, *jz = nullptr, *kap = nullptr;
+    LevelArrays lev[QS_MAX_LEV] = {};
+    double *hist = nullptr, *jzb = nullptr;
+    DevScalars *sc = nullptr;
+    int32_t *diag_m = nullptr, *d_sched = nullptr;
+    double *diag_vmax = nullptr, *diag_charge = nullptr;
+    // sort scratch
+    int32_t *s_cursor = nullptr;
+    // plasma
+    int64_t np = 0;
+    int ppc = 0;
+    double *t_x = nullptr, *t_y = nullptr, *t_px = nullptr, *t_py = nullptr, *t_w = nullptr;
+    int32_t *t_id = nullptr;
+    double *x = nullptr, *y = nullptr, *px = nullptr, *py = nullptr, *w = nullptr;
+    int32_t *id = nullptr;
+    std::vector<void *> plasma_allocs;
+    bool have_plasma = false, have_step = false;
+    int engine_blocks = 0;
+    size_t engine_smem = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    char msg[512] = {0};
+};
+
+namespace {
+
+int fail(qs_ctx *c, int status, const char *fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+        va_end(ap);
+    }
+    return status;
+}
+
+int cuda_fail(qs_ctx *c, cudaError_t e, const char *what) {
+    cudaGetLastError();
+    int st = (e == cudaErrorMemoryAllocation) ? QS_ERR_OOM : QS_ERR_CUDA;
+    return fail(c, st, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+template <typename T>
+int dalloc(qs_ctx *c, std::vector<void *> &list, T **p, size_t count) {
+    void *q = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+    list.push_back(q);
+    *p = static_cast<T *>(q);
+    return QS_OK;
+}
+
+#define AL(list, ptr, count)                        \
+    do {                                            \
+        int r_ = dalloc(c, list, &(ptr), (count));  \
+        if (r_ != QS_OK) return r_;                 \
+    } while (0)
+
+int validate(const qs_config *cfg, char *why, size_t nwhy) {
+    if (!cfg) {
+        snprintf(why, nwhy, "config is NULL");
+        return QS_ERR_ARG;
+    }
+    if (cfg->nx != cfg->ny || cfg->nx < 2) {
+        snprintf(why, nwhy, "nx must equal ny and be >= 2 (got %d, %d)", cfg->nx, cfg->ny);
+        return QS_ERR_ARG;
+    }
+    const double lx = cfg->x_max - cfg->x_min, ly = cfg->y_max - cfg->y_min;
+    if (!(lx > 0.0) || !(ly > 0.0) || std::fabs(lx - ly) > 1e-12 * lx) {
+        snprintf(why, nwhy, "the box must be square with positive extent");
+        return QS_ERR_ARG;
+    }
+    int n = cfg->nx;
+    while (n % 2 == 0 && n > 4) n /= 2;
+    if (n > 8) {
+        snprintf(why, nwhy, "N = %d does not coarsen to a side <= 8", cfg->nx);
+        return QS_ERR_ARG;
+    }
+    if (cfg->n_xi < 1 || !(cfg->xi_max > cfg->xi_min)) {
+        snprintf(why, nwhy, "need n_xi >= 1 and xi_max > xi_min");
+        return QS_ERR_ARG;
+    }
+    if (cfg->refine_k < 1 || cfg->refine_k > 1024) {
+        snprintf(why, nwhy, "refine_k must be in [1, 1024]");
+        return QS_ERR_ARG;
+    }
+    if (cfg->precision != QS_FP64 && cfg->precision != QS_FP32_REFINED) {
+        snprintf(why, nwhy, "unknown precision %d", cfg->precision);
+        return QS_ERR_ARG;
+    }
+    if (!(cfg->mg_tol > 0.0) || cfg->mg_max_vcycles < 1 || !(cfg->psi_floor > 0.0)) {
+        snprintf(why, nwhy, "need mg_tol > 0, mg_max_vcycles >= 1, psi_floor > 0");
+        return QS_ERR_ARG;
+    }
+    if (cfg->pre_sweeps < 0 || cfg->post_sweeps < 0 || cfg->pre_sweeps + cfg->post_sweeps < 1 ||
+        cfg->pre_sweeps > 8 || cfg->post_sweeps > 8) {
+        snprintf(why, nwhy, "sweeps must be in [0, 8] with at least one");
+        return QS_ERR_ARG;
+    }
+    if (cfg->sort_every < 0) {
+        snprintf(why, nwhy, "sort_every must be >= 0");
+        return QS_ERR_ARG;
+    }
+    for (int i = 0; i < 8; ++i)
+        if (cfg->reserved[i] != 0) {
+            snprintf(why, nwhy, "reserved fields must be zero");
+            return QS_ERR_ARG;
+        }
+    return QS_OK;
+}
+
+int create_impl(qs_ctx *c) {
+    const qs_config &g = c->cfg;
+    CK(cudaGetDevice(&c->dev), "cudaGetDevice");
+    c->N = g.nx;
+    c->h = (g.x_max - g.x_min) / g.nx;
+    int n = c->N;
+    c->nlev = 0;
+    c->lev_n[c->nlev++] = n;
+    while (n % 2 == 0 && n > 4 && c->nlev < QS_MAX_LEV) {
+        n /= 2;
+        c->lev_n[c->nlev++] = n;
+    }
+    const size_t nn = (size_t)c->N * c->N;
+    auto &L = c->allocs;
+    double **grids[] = {&c->n_a, &c->n_b, &c->n_ion, &c->jx,  &c->jy,   &c->txx, &c->txy,
+                        &c->tyy, &c->G,   &c->psi,   &c->ez,  &c->bz,   &c->bx,  &c->by,
+                        &c->f_psi, &c->f_ez, &c->f_bz, &c->f_bx, &c->f_by, &c->dpx, &c->dpy,
+                        &c->jz,  &c->kap};
+    for (double **p : grids) AL(L, *p, nn);
+    for (int l = 1; l < c->nlev; ++l) {
+        const size_t m = (size_t)c->lev_n[l] * c->lev_n[l];
+        AL(L, c->lev[l].u[0], m);
+        AL(L, c->lev[l].u[1], m);
+        AL(L, c->lev[l].f[0], m);
+        AL(L, c->lev[l].f[1], m);
+        AL(L, c->lev[l].kap, m);
+    }
+    AL(L, c->hist, 5 * (size_t)g.n_xi * nn);
+    AL(L, c->jzb, (size_t)g.n_xi * nn);
+    AL(L, c->sc, 1);
+    AL(L, c->diag_m, (size_t)g.n_xi);
+    AL(L, c->d_sched, (size_t)g.n_xi);
+    AL(L, c->diag_vmax, (size_t)g.n_xi);
+    AL(L, c->diag_charge, (size_t)g.n_xi);
+    AL(L, c->s_cursor, nn);
+    // fields start at zero (the warm start of the first slice)
+    for (double **p : grids) CK(cudaMemsetAsync(*p, 0, nn * sizeof(double), c->st), "memset");
+    CK(cudaMemsetAsync(c->hist, 0, 5 * (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
+    CK(cudaMemsetAsync(c->jzb, 0, (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
+    c->engine_smem = 36 * 1024;
+    int blocks = 0;
+    if (qs_engine_max_blocks(c->dev, c->engine_smem, &blocks) != 0 || blocks < 1)
+        return fail(c, QS_ERR_CUDA, "slice engine cannot be made resident");
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev), "attr");
+    c->engine_blocks = blocks < sms ? blocks : sms;
+    CK(cudaEventCreate(&c->ev0), "event");
+    CK(cudaEventCreate(&c->ev1), "event");
+    CK(cudaStreamSynchronize(c->st), "sync");
+    return QS_OK;
+}
+
+void free_list(std::vector<void *> &l) {
+    for (void *p : l) cudaFree(p);
+    l.clear();
+}
+
+int check_ctx(qs_ctx *c) { return c ? QS_OK : QS_ERR_ARG; }
+
+}  // namespace
+
+extern "C" {
+
+void qs_config_default(qs_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->nx = cfg->ny = 64;
+    cfg->x_min = cfg->y_min = -6.0;
+    cfg->x_max = cfg->y_max = 6.0;
+    cfg->n_xi = 128;
+    cfg->xi_min = 0.0;
+    cfg->xi_max = 12.0;
+    cfg->refine_k = 8;
+    cfg->precision = QS_FP64;
+    cfg->mg_tol = 1e-10;
+    cfg->mg_max_vcycles = 60;
+    cfg->psi_floor = 1e-3;
+    cfg->max_psi_guard_hits = -1;
+    cfg->sort_every = 16;
+    cfg->pre_sweeps = 2;
+    cfg->post_sweeps = 2;
+}
+
+int qs_create(const qs_config *cfg, void *cuda_stream, qs_ctx **out) {
+    if (!out) return QS_ERR_ARG;
+    *out = nullptr;
+    char why[256];
+    int v = validate(cfg, why, sizeof(why));
+    if (v != QS_OK) return v;
+    qs_ctx *c = new (std::nothrow) qs_ctx();
+    if (!c) return QS_ERR_OOM;
+    c->cfg = *cfg;
+    c->st = static_cast<cudaStream_t>(cuda_stream);
+    int r = create_impl(c);
+    if (r != QS_OK) {
+        free_list(c->allocs);
+        if (c->ev0) cudaEventDestroy(c->ev0);
+        if (c->ev1) cudaEventDestroy(c->ev1);
+        delete c;
+        return r;
+    }
+    *out = c;
+    return QS_OK;
+}
+
+void qs_destroy(qs_ctx *c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    free_list(c->plasma_allocs);
+    free_list(c->allocs);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+int qs_init_plasma(qs_ctx *c, int ppc, const double *profile, int n_coef, double r_max) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    int s = 1;
+    while (s * s < ppc) ++s;
+    if (ppc < 1 || s * s != ppc) return fail(c, QS_ERR_ARG, "ppc must be a perfect square");
+    if (profile && (n_coef < 1 || !(r_max > 0.0)))
+        return fail(c, QS_ERR_ARG, "profile needs n_coef >= 1 and r_max > 0");
+    const size_t nn = (size_t)c->N * c->N;
+    const int64_t np = (int64_t)nn * ppc;
+    if (np > (int64_t)0x7fffffff) return fail(c, QS_ERR_ARG, "too many particles for int32 ids");
+    CK(cudaStreamSynchronize(c->st), "sync");
+    free_list(c->plasma_allocs);
+    c->have_plasma = c->have_step = false;
+    auto &L = c->plasma_allocs;
+    AL(L, c->t_x, np);
+    AL(L, c->t_y, np);
+    AL(L, c->t_px, np);
+    AL(L, c->t_py, np);
+    AL(L, c->t_w, np);
+    AL(L, c->t_id, np);
+    AL(L, c->x, np);
+    AL(L, c->y, np);
+    AL(L, c->px, np);
+    AL(L, c->py, np);
+    AL(L, c->w, np);
+    AL(L, c->id, np);
+    double *d_table = nullptr;
+    if (profile) {
+        AL(L, d_table, (size_t)n_coef);
+        CK(cudaMemcpyAsync(d_table, profile, sizeof(double) * n_coef, cudaMemcpyHostToDevice,
+                           c->st),
+           "copy profile");
+    }
+    c->np = np;
+    c->ppc = ppc;
+    const qs_config &g = c->cfg;
+    CK(qs_launch_init_plasma(c->st, c->N, ppc, g.x_min, g.y_min, c->h, d_table, n_coef, r_max,
+                             c->t_x, c->t_y, c->t_px, c->t_py, c->t_w, c->t_id),
+       "init plasma");
+    CK(cudaMemsetAsync(c->n_ion, 0, nn * sizeof(double), c->st), "memset");
+    CK(qs_launch_deposit(c->st, c->t_x, c->t_y, c->t_w, np, c->N, g.x_min, g.y_min, c->h,
+                         1.0 / (c->h * c->h), c->n_ion),
+       "deposit n_ion");
+    const size_t bd = np * sizeof(double);
+    CK(cudaMemcpyAsync(c->x, c->t_x, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->y, c->t_y, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->px, c->t_px, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->py, c->t_py, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->w, c->t_w, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->id, c->t_id, np * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st),
+       "copy");
+    CK(cudaStreamSynchronize(c->st), "init plasma");
+    c->have_plasma = true;
+    return QS_OK;
+}
+
+static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t *sched,
+                     qs_step_stats *stats) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_plasma) return fail(c, QS_ERR_STATE, "qs_init_plasma has not been called");
+    if (n_beams < 0 || (n_beams > 0 && !beams)) return fail(c, QS_ERR_ARG, "bad beam list");
+    const qs_config &g = c->cfg;
+    for (int b = 0; b < n_beams; ++b) {
+        const qs_beam &bm = beams[b];
+        if (bm.n < 0) return fail(c, QS_ERR_ARG, "beam %d: negative count", b);
+        if (bm.n > 0 && (!bm.x || !bm.y || !bm.xi || !bm.px || !bm.py || !bm.pz || !bm.w))
+            return fail(c, QS_ERR_ARG, "beam %d: NULL array", b);
+    }
+    if (sched) {
+        for (int j = 0; j < g.n_xi; ++j)
+            if (sched[j] < 1 || sched[j] > g.refine_k)
+                return fail(c, QS_ERR_ARG, "m_schedule[%d] = %d outside [1, refine_k]", j,
+                            sched[j]);
+    }
+    const size_t nn = (size_t)c->N * c->N;
+    const double dxi0 = (g.xi_max - g.xi_min) / g.n_xi;
+    // fresh plasma at the head of the window
+    const size_t bd = c->np * sizeof(double);
+    CK(cudaMemcpyAsync(c->x, c->t_x, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->y, c->t_y, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->px, c->t_px, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->py, c->t_py, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->w, c->t_w, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->id, c->t_id, c->np * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st),
+       "copy");
+    CK(cudaMemsetAsync(c->n_a, 0, nn * sizeof(double), c->st), "memset");
+    // driver current on the base slices
+    CK(cudaMemsetAsync(c->jzb, 0, (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
+    for (int b = 0; b < n_beams; ++b)
+        CK(qs_launch_beam_deposit(c->st, beams[b], c->N, g.x_min, g.x_max, g.y_min, g.y_max,
+                                  c->h, g.n_xi, g.xi_min, dxi0, c->jzb),
+           "beam deposit");
+    CK(cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->st), "memset");
+    CK(cudaMemsetAsync(c->diag_m, 0, g.n_xi * sizeof(int32_t), c->st), "memset");
+    CK(cudaMemsetAsync(c->diag_vmax, 0, g.n_xi * sizeof(double), c->st), "memset");
+    CK(cudaMemsetAsync(c->diag_charge, 0, g.n_xi * sizeof(double), c->st), "memset");
+    if (sched)
+        CK(cudaMemcpyAsync(c->d_sched, sched, g.n_xi * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           c->st),
+           "copy schedule");
+
+    EngineArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.N = c->N;
+    a.h = c->h;
+    a.inv_h = 1.0 / c->h;
+    a.x_min = g.x_min;
+    a.x_max = g.x_max;
+    a.y_min = g.y_min;
+    a.y_max = g.y_max;
+    a.n_xi = g.n_xi;
+    a.dxi0 = dxi0;
+    a.V0 = c->h / dxi0;
+    a.refine_k = g.refine_k;
+    a.psi_floor = g.psi_floor;
+    a.mg_tol = g.mg_tol;
+    a.mg_atol = 1e-15 * c->N;
+    a.mg_max_vcycles = g.mg_max_vcycles;
+    a.nu1 = g.pre_sweeps;
+    a.nu2 = g.post_sweeps;
+    a.np = c->np;
+    a.spin_cycles = 4000000000LL;
+    a.x = c->x;
+    a.y = c->y;
+    a.px = c->px;
+    a.py = c->py;
+    a.w = c->w;
+    a.n_a = c->n_a;
+    a.n_b = c->n_b;
+    a.n_ion = c->n_ion;
+    a.jx = c->jx;
+    a.jy = c->jy;
+    a.txx = c->txx;
+    a.txy = c->txy;
+    a.tyy = c->tyy;
+    a.G = c->G;
+    a.psi = c->psi;
+    a.ez = c->ez;
+    a.bz = c->bz;
+    a.bx = c->bx;
+    a.by = c->by;
+    a.f_psi = c->f_psi;
+    a.f_ez = c->f_ez;
+    a.f_bz = c->f_bz;
+    a.f_bx = c->f_bx;
+    a.f_by = c->f_by;
+    a.dpx = c->dpx;
+    a.dpy = c->dpy;
+    a.jz = c->jz;
+    a.kap = c->kap;
+    a.nlev = c->nlev;
+    for (int l = 0; l < c->nlev; ++l) {
+        a.lev_n[l] = c->lev_n[l];
+        const double hl = c->h * (double)(1 << l);
+        a.lev_h2[l] = hl * hl;
+        a.lev[l] = c->lev[l];
+    }
+    a.block_level_n = 16;
+    a.hist = c->hist;
+    a.jzb = c->jzb;
+    a.m_sched = sched ? c->d_sched : nullptr;
+    a.diag_m = c->diag_m;
+    a.diag_vmax = c->diag_vmax;
+    a.diag_charge = c->diag_charge;
+    a.sc = c->sc;
+    CK(cudaEventRecord(c->ev0, c->st), "event");
+    CK(qs_launch_engine(c->st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
+    CK(cudaEventRecord(c->ev1, c->st), "event");
+    CK(cudaStreamSynchronize(c->st), "slice engine");
+    DevScalars hs;
+    CK(cudaMemcpy(&hs, c->sc, sizeof(hs), cudaMemcpyDeviceToHost), "copy scalars");
+    c->have_step = true;
+    int status = QS_OK;
+    if (hs.err != 0) {
+        status = hs.err;
+        fail(c, status, "device wait timed out at phase %d", hs.err_where);
+    } else if (hs.not_converged) {
+        status = fail(c, QS_ERR_NOT_CONVERGED, "a multigrid solve reached %d V-cycles (relres %g)",
+                      g.mg_max_vcycles, hs.max_relres);
+    } else if (g.max_psi_guard_hits >= 0 && (int64_t)hs.guard_hits > g.max_psi_guard_hits) {
+        status = fail(c, QS_ERR_PSI_FLOOR, "1+psi clamped %llu times", hs.guard_hits);
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->slices = hs.slices;
+        stats->substeps = hs.slices - g.n_xi;
+        stats->pushes = hs.pushes;
+        for (int k = 0; k < 3; ++k) stats->vcycles[k] = hs.vcycles[k];
+        stats->psi_guard_hits = (int64_t)hs.guard_hits;
+        stats->sorts = 0;
+        stats->max_relres = hs.max_relres;
+        unsigned long long vb = hs.vmax_all_bits;
+        double vm;
+        std::memcpy(&vm, &vb, sizeof(vm));
+        stats->vmax = vm;
+        stats->max_m = hs.max_m;
+        stats->status = status;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        stats->gpu_ms = ms;
+    }
+    return status;
+}
+
+int qs_step3d(qs_ctx *c, const qs_beam *beams, int n_beams, qs_step_stats *stats) {
+    return step_impl(c, beams, n_beams, nullptr, stats);
+}
+
+int qs_step3d_schedule(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t *m_schedule,
+                       qs_step_stats *stats) {
+    if (!m_schedule) return fail(c, QS_ERR_ARG, "m_schedule is NULL");
+    return step_impl(c, beams, n_beams, m_schedule, stats);
+}
+
+int qs_push_beam(qs_ctx *c, qs_beam *beams, int n_beams, double dt) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_step) return fail(c, QS_ERR_STATE, "qs_step3d has not been run");
+    if (n_beams < 0 || (n_beams > 0 && !beams)) return fail(c, QS_ERR_ARG, "bad beam list");
+    const qs_config &g = c->cfg;
+    const double dxi0 = (g.xi_max - g.xi_min) / g.n_xi;
+    for (int b = 0; b < n_beams; ++b) {
+        const qs_beam &bm = beams[b];
+        if (bm.n < 0) return fail(c, QS_ERR_ARG, "beam %d: negative count", b);
+        if (bm.n > 0 && (!bm.x || !bm.y || !bm.xi || !bm.px || !bm.py || !bm.pz))
+            return fail(c, QS_ERR_ARG, "beam %d: NULL array", b);
+        CK(qs_launch_beam_push(c->st, bm, c->N, g.x_min, g.x_max, g.y_min, g.y_max, c->h, g.n_xi,
+                               g.xi_min, dxi0, c->hist, dt),
+           "beam push");
+    }
+    return QS_OK;
+}
+
+int qs_fields(qs_ctx *c, int field_mask, int slice_begin, int slice_end, double *out,
+              int out_on_device) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_step) return fail(c, QS_ERR_STATE, "qs_step3d has not been run");
+    const qs_config &g = c->cfg;
+    if (!out || (field_mask & ~63) || field_mask == 0 || slice_begin < 0 ||
+        slice_end > g.n_xi || slice_begin >= slice_end)
+        return fail(c, QS_ERR_ARG, "bad field mask or slice range");
+    const size_t nn = (size_t)c->N * c->N;
+    const size_t cnt = (size_t)(slice_end - slice_begin) * nn;
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    size_t off = 0;
+    for (int f = 0; f < 6; ++f) {
+        if (!(field_mask & (1 << f))) continue;
+        const double *src = (f < 5) ? c->hist + (size_t)f * g.n_xi * nn + slice_begin * nn
+                                    : c->jzb + slice_begin * nn;
+        CK(cudaMemcpyAsync(out + off, src, cnt * sizeof(double), kind, c->st), "copy fields");
+        off += cnt;
+    }
+    if (!out_on_device) CK(cudaStreamSynchronize(c->st), "sync");
+    return QS_OK;
+}
+
+int qs_slice_diagnostics(qs_ctx *c, int32_t *m, double *vmax, double *charge) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_step) return fail(c, QS_ERR_STATE, "qs_step3d has not been run");
+    const int n = c->cfg.n_xi;
+    if (m) CK(cudaMemcpyAsync(m, c->diag_m, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st), "copy");
+    if (vmax) CK(cudaMemcpyAsync(vmax, c->diag_vmax, n * sizeof(double), cudaMemcpyDeviceToHost, c->st), "copy");
+    if (charge) CK(cudaMemcpyAsync(charge, c->diag_charge, n * sizeof(double), cudaMemcpyDeviceToHost, c->st), "copy");
+    CK(cudaStreamSynchronize(c->st), "sync");
+    return QS_OK;
+}
+
+int64_t qs_plasma_count(const qs_ctx *c) { return (c && c->have_plasma) ? c->np : 0; }
+
+int qs_get_plasma(qs_ctx *c, double *x, double *y, double *px, double *py, double *w,
+                  int32_t *id) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_plasma) return fail(c, QS_ERR_STATE, "qs_init_plasma has not been called");
+    const size_t bd = c->np * sizeof(double);
+    const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
+    if (x) CK(cudaMemcpyAsync(x, c->x, bd, k, c->st), "copy");
+    if (y) CK(cudaMemcpyAsync(y, c->y, bd, k, c->st), "copy");
+    if (px) CK(cudaMemcpyAsync(px, c->px, bd, k, c->st), "copy");
+    if (py) CK(cudaMemcpyAsync(py, c->py, bd, k, c->st), "copy");
+    if (w) CK(cudaMemcpyAsync(w, c->w, bd, k, c->st), "copy");
+    if (id) CK(cudaMemcpyAsync(id, c->id, c->np * sizeof(int32_t), k, c->st), "copy");
+    CK(cudaStreamSynchronize(c->st), "sync");
+    return QS_OK;
+}
+
+int qs_cell_sort(qs_ctx *c, const double *x, const double *y, const int32_t *id, int64_t n,
+                 int32_t *cell, int32_t *count, int32_t *offset, int32_t *perm) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (n < 0 || n > (int64_t)0x7fffffff || !count || !offset ||
+        (n > 0 && (!x || !y || !id || !cell || !perm)))
+        return fail(c, QS_ERR_ARG, "bad cell-sort arguments");
+    const qs_config &g = c->cfg;
+    CK(qs_launch_cell_sort(c->st, x, y, id, n, c->N, g.x_min, g.y_min, c->h, cell, count, offset,
+                           c->s_cursor, perm),
+       "cell sort");
+    CK(cudaStreamSynchronize(c->st), "cell sort");
+    return QS_OK;
+}
+
+const char *qs_strerror(int status) {
+    switch (status) {
+        case QS_OK: return "ok";
+        case QS_ERR_ARG: return "invalid argument";
+        case QS_ERR_CUDA: return "CUDA error";
+        case QS_ERR_OOM: return "out of device memory";
+        case QS_ERR_NOT_CONVERGED: return "multigrid did not converge";
+        case QS_ERR_PSI_FLOOR: return "1+psi fell below psi_floor too often";
+        case QS_ERR_STATE: return "call out of order";
+        case QS_ERR_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char *qs_last_error(const qs_ctx *c) { return c ? c->msg : ""; }
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Internal declarations shared by the libqs translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qs.h"
+
+#define QS_MAX_LEV 12
+#define QS_ENGINE_THREADS 512
+
+// ---------------------------------------------------------------------------
+// device scalars of the slice engine (one instance per context, in global
+// memory; reset before every launch)
+// ---------------------------------------------------------------------------
+struct DevScalars {
+    unsigned int bar_count;        // grid barrier: arrivals
+    unsigned int bar_gen;          // grid barrier: generation
+    int err;                       // first error status seen on the device
+    int err_where;                 // phase id of a timeout
+    double rnorm[4][4];            // ||r||^2 (comps 0,1) and ||u||^2 (2,3), ring of 4
+    double fnorm[3][2];            // ||f||^2 of the psi / (Ez,Bz) / (Bx,By) solves
+    unsigned long long vmax_bits[2];  // V_max of a push (bits of a double >= 0)
+    unsigned long long guard_hits;
+    long long vcycles[3];
+    long long slices;
+    long long pushes;
+    int max_m;
+    int not_converged;
+    double max_relres;
+    unsigned long long vmax_all_bits;
+};
+
+// one grid level of a multigrid hierarchy
+struct LevelArrays {
+    double *u[2];
+    double *f[2];
+    double *kap;
+};
+
+// Everything the slice engine reads or writes (passed by value).
+struct EngineArgs {
+    // geometry (Sec. 3 normalised units)
+    int N;
+    double h, inv_h, x_min, x_max, y_min, y_max;
+    int n_xi;
+    double dxi0, V0;
+    int refine_k;
+    double psi_floor;
+    double mg_tol, mg_atol;
+    int mg_max_vcycles;
+    int nu1, nu2;
+    int64_t np;
+    long long spin_cycles;
+    // plasma macroparticles (working copy)
+    double *x, *y, *px, *py, *w;
+    // deposited grids
+    double *n_a, *n_b, *n_ion;
+    double *jx, *jy, *txx, *txy, *tyy, *G;
+    // level-0 fields (multigrid unknowns) and right-hand sides
+    double *psi, *ez, *bz, *bx, *by;
+    double *f_psi, *f_ez, *f_bz, *f_bx, *f_by;
+    double *dpx, *dpy, *jz, *kap;
+    // coarse levels 1..nlev-1 (scratch shared by the three solves)
+    int nlev;
+    int lev_n[QS_MAX_LEV];
+    double lev_h2[QS_MAX_LEV];
+    LevelArrays lev[QS_MAX_LEV];
+    int block_level_n;  // levels with side <= this are relaxed by one block
+    // outputs
+    double *hist;        // [5][n_xi][N*N]
+    const double *jzb;   // [n_xi][N*N]
+    const int32_t *m_sched;  // optional [n_xi]
+    int32_t *diag_m;
+    double *diag_vmax, *diag_charge;
+    DevScalars *sc;
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+
+// Two-cell linear (CIC) weights along one axis for s = (x - x_min) / h; cell
+// centres at s = i + 1/2.  Index -1 folds to 0, index n to n-1 (the ghost
+// weight goes to the mirror interior cell).  Indices are clamped to [0, n-1]
+// for memory safety.
+__device__ __forceinline__ void cic_axis(double s, int n, int &i0, int &i1, double &w0,
+                                         double &w1) {
+    double t = s - 0.5;
+    double fl = floor(t);
+    double f = t - fl;
+    int a = (int)fl;
+    int b = a + 1;
+    if (a < 0) a = -1 - a;
+    if (b > n - 1) b = 2 * n - 1 - b;
+    a = min(max(a, 0), n - 1);
+    b = min(max(b, 0), n - 1);
+    i0 = a;
+    i1 = b;
+    w0 = 1.0 - f;
+    w1 = f;
+}
+
+struct Cic {
+    int i00, i01, i10, i11;  // flat indices (iy0,ix0) (iy0,ix1) (iy1,ix0) (iy1,ix1)
+    double w00, w01, w10, w11;
+};
+
+__device__ __forceinline__ Cic cic_stencil(double x, double y, double x_min, double y_min,
+                                           double h, int n) {
+    int ix0, ix1, iy0, iy1;
+    double wx0, wx1, wy0, wy1;
+    cic_axis((x - x_min) / h, n, ix0, ix1, wx0, wx1);
+    cic_axis((y - y_min) / h, n, iy0, iy1, wy0, wy1);
+    Cic c;
+    c.i00 = iy0 * n + ix0;
+    c.i01 = iy0 * n + ix1;
+    c.i10 = iy1 * n + ix0;
+    c.i11 = iy1 * n + ix1;
+    c.w00 = wy0 * wx0;
+    c.w01 = wy0 * wx1;
+    c.w10 = wy1 * wx0;
+    c.w11 = wy1 * wx1;
+    return c;
+}
+
+__device__ __forceinline__ double cic_gather(const double *u, const Cic &c) {
+    return u[c.i00] * c.w00 + u[c.i01] * c.w01 + u[c.i10] * c.w10 + u[c.i11] * c.w11;
+}
+
+__device__ __forceinline__ void cic_deposit(double *g, const Cic &c, double q) {
+    atomicAdd(g + c.i00, q * c.w00);
+    atomicAdd(g + c.i01, q * c.w01);
+    atomicAdd(g + c.i10, q * c.w10);
+    atomicAdd(g + c.i11, q * c.w11);
+}
+
+// Cell index c = iy * N + ix, ix = floor((x - x_min) / h) clamped to [0, N-1].
+__device__ __forceinline__ int cell_of(double x, double y, double x_min, double y_min, double h,
+                                       int n) {
+    int ix = (int)floor((x - x_min) / h);
+    int iy = (int)floor((y - y_min) / h);
+    ix = min(max(ix, 0), n - 1);
+    iy = min(max(iy, 0), n - 1);
+    return iy * n + ix;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers implemented in qs_aux.cu
+// ---------------------------------------------------------------------------
+cudaError_t qs_launch_init_plasma(cudaStream_t st, int n, int ppc, double x_min, double y_min,
+                                  double h, const double *table, int n_coef, double r_max,
+                                  double *x, double *y, double *px, double *py, double *w,
+                                  int32_t *id);
+cudaError_t qs_launch_deposit(cudaStream_t st, const double *x, const double *y,
+                              const double *q, int64_t np, int n, double x_min, double y_min,
+                              double h, double scale, double *grid);
+cudaError_t qs_launch_beam_deposit(cudaStream_t st, const qs_beam &b, int n, double x_min,
+                                   double x_max, double y_min, double y_max, double h,
+                                   int n_xi, double xi_min, double dxi0, double *jzb);
+cudaError_t qs_launch_beam_push(cudaStream_t st, const qs_beam &b, int n, double x_min,
+                                double x_max, double y_min, double y_max, double h, int n_xi,
+                                double xi_min, double dxi0, const double *hist, double dt);
+cudaError_t qs_launch_cell_sort(cudaStream_t st, const double *x, const double *y,
+                                const int32_t *id, int64_t np, int n, double x_min,
+                                double y_min, double h, int32_t *cell, int32_t *count,
+                                int32_t *offset, int32_t *cursor, int32_t *perm);
+cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_blocks,
+                             size_t smem_bytes);
+int qs_engine_max_blocks(int device, size_t smem_bytes, int *blocks);

@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports what include/qs.h declares (CPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(qs_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2012_00881_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "qs_step3d" in names and "qs_init_plasma" in names and "qs_fields" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_prototypes_cover_the_header():
+    import paper_2012_00881_gb300 as qs
+    assert set(_declared_functions()) == set(qs.PROTOTYPES)
+
+
+def test_default_config_through_the_abi(lib):
+    """qs_config_default fills the ctypes mirror field by field."""
+    import paper_2012_00881_gb300 as qs
+    cfg = qs.default_config()
+    assert cfg.nx == 64 and cfg.ny == 64 and cfg.refine_k == 8 and cfg.mg_tol == 1e-10
+    assert cfg.x_min == -6.0 and cfg.xi_max == 12.0 and cfg.n_xi == 128
+    assert cfg.max_psi_guard_hits == -1 and cfg.sort_every == 16
+    assert cfg.pre_sweeps == 2 and cfg.post_sweeps == 2 and list(cfg.reserved) == [0] * 8
+
+
+def test_status_strings(lib):
+    import paper_2012_00881_gb300 as qs
+    l = qs.load_library()
+    assert l.qs_strerror(0) == b"ok"
+    assert l.qs_strerror(qs.QS_ERR_NOT_CONVERGED) == b"multigrid did not converge"
+    assert l.qs_strerror(12345) == b"unknown status"
+
+
+def test_invalid_config_rejected_without_gpu(lib):
+    """Argument validation runs before any device call."""
+    import paper_2012_00881_gb300 as qs
+    l = qs.load_library()
+    h = ctypes.c_void_p()
+    for bad in (dict(nx=64, ny=32), dict(nx=100, ny=100), dict(refine_k=0),
+                dict(precision=7), dict(mg_tol=0.0), dict(x_max=7.0)):
+        cfg = qs.default_config(**bad)
+        assert l.qs_create(ctypes.byref(cfg), None, ctypes.byref(h)) == qs.QS_ERR_ARG, bad
+    assert l.qs_create(None, None, ctypes.byref(h)) == qs.QS_ERR_ARG

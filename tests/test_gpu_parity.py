@@ -1,0 +1,151 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (GPU)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b, scale=None):
+    d = np.linalg.norm(a - b)
+    s = max(np.linalg.norm(b), scale or 0.0, 1e-300)
+    return d / s
+
+
+def _run_both(qs, wl, tol=1e-12, schedule=None, **cfg_over):
+    beams_np = [W.sample_beam(b) for b in wl.beams]
+    ctx = qs.Context(qs.config_from_workload(wl, mg_tol=tol, **cfg_over))
+    if wl.profile is None:
+        ctx.init_plasma(wl.ppc)
+    else:
+        ctx.init_plasma(wl.ppc, wl.profile[0], wl.profile[1])
+    beams = [qs.Beam(b) for b in beams_np]
+    stats = ctx.step3d(beams, schedule=schedule)
+    got = ctx.fields(qs.FIELD_ALL | qs.FIELD_JZB, device=False).numpy()
+    m, vmax, charge = ctx.slice_diagnostics()
+    cfg = O.config_from_workload(wl)
+    pl, n_ion = O.plasma_from_workload(wl)
+    ref = O.step3d(cfg, pl, n_ion, beams_np, m_schedule=schedule)
+    jzb = O.deposit_beam(cfg, beams_np)
+    return dict(ctx=ctx, stats=stats, got=got, m=m, vmax=vmax, charge=charge, ref=ref, jzb=jzb,
+                beams=beams, beams_np=beams_np, cfg=cfg, pl=pl)
+
+
+def _check_fields(r, tol):
+    ref = r["ref"].history
+    scale = np.linalg.norm(ref[0])
+    errs = {}
+    for i, name in enumerate(O.FIELD_NAMES):
+        errs[name] = _rel(r["got"][i], ref[i], scale)
+    assert max(errs.values()) < tol, errs
+    return errs
+
+
+def test_init_plasma_matches_oracle_lattice(qs):
+    wl = W.workload("linear64")
+    ctx = qs.Context(qs.config_from_workload(wl))
+    ctx.init_plasma(4)
+    p = ctx.plasma()
+    pl, _ = O.plasma_from_workload(wl)
+    assert np.array_equal(p["id"], pl.pid)
+    assert np.max(np.abs(p["x"] - pl.x)) < 1e-14 and np.max(np.abs(p["y"] - pl.y)) < 1e-14
+    assert np.max(np.abs(p["w"] - pl.w)) < 1e-16
+    # parabolic channel weights
+    prof = W.workload("blowout512").profile
+    ctx2 = qs.Context(qs.config_from_workload(wl))
+    ctx2.init_plasma(9, prof[0], prof[1])
+    p2 = ctx2.plasma()
+    g = O.Grid.square(wl.n, wl.half_width)
+    pl2, _ = O.init_plasma(g, 9, prof[0], prof[1])
+    assert np.max(np.abs(p2["w"] - pl2.w)) < 1e-15 * pl2.w.max()
+
+
+@pytest.mark.parametrize("n,np_", [(8, 1000), (64, 50000), (256, 262144)])
+def test_cell_sort_bit_exact(qs, n, np_):
+    import torch
+    rng = np.random.default_rng(n)
+    L = 8.0
+    x = rng.uniform(-L, L, np_)
+    y = rng.uniform(-L, L, np_)
+    h = 2 * L / n
+    x[: min(50, np_)] = -L + h * rng.integers(0, n + 1, min(50, np_))  # on cell faces and walls
+    pid = rng.permutation(np_).astype(np.int32)
+    wl = W.Workload(name="s", n=n, half_width=L, n_xi=4, xi_len=1.0, ppc=4, beams=())
+    ctx = qs.Context(qs.config_from_workload(wl))
+    t = lambda a: torch.as_tensor(a, device="cuda")
+    cell, count, offset, perm = (v.cpu().numpy() for v in ctx.cell_sort(t(x), t(y), t(pid)))
+    c_o, count_o, off_o, perm_o = O.cell_sort(x, y, pid, O.Grid.square(n, L))
+    assert np.array_equal(cell, c_o)
+    assert np.array_equal(count, count_o)
+    assert np.array_equal(offset, off_o)
+    assert np.array_equal(perm, perm_o)
+
+
+def test_linear_driver_step_parity(qs):
+    """The 64^2, 128-slice linear workload: every field of every base slice."""
+    wl = W.workload("linear64")
+    r = _run_both(qs, wl)
+    _check_fields(r, 1e-9)
+    assert r["stats"]["slices"] == r["ref"].slices == 128
+    assert np.array_equal(r["m"], r["ref"].m)
+    assert np.max(np.abs(r["charge"] - r["pl"].w.sum())) < 1e-11 * r["pl"].w.sum()
+    assert _rel(r["got"][5], r["jzb"]) < 1e-13
+
+
+def test_nonlinear_refined_step_parity(qs):
+    """A strong driver on a small grid: adaptive sub-steps, nonlinear sources."""
+    wl = W.Workload(name="t", n=32, half_width=3.0, n_xi=32, xi_len=8.0, ppc=4,
+                    beams=(W.BeamSpec(amplitude=20.0, sigma_x=0.5, sigma_y=0.5, sigma_z=0.6,
+                                      xi_c=1.8, n_particles=20000, seed=3),))
+    r = _run_both(qs, wl)
+    assert np.array_equal(r["m"], r["ref"].m), (r["m"], r["ref"].m)
+    assert r["ref"].m.max() > 2
+    assert r["stats"]["slices"] == r["ref"].slices
+    _check_fields(r, 1e-9)
+
+
+def test_beam_push_parity(qs):
+    wl = W.workload("linear64")
+    r = _run_both(qs, wl)
+    ctx = r["ctx"]
+    ctx.push_beam(r["beams"], 10.0)
+    got = r["beams"][0].numpy()
+    b0 = r["beams_np"][0]
+    ref = O.push_beam(r["cfg"], r["ref"].history, b0, 10.0)
+    for k in ("px", "py", "pz"):
+        dg, dr = got[k] - b0[k], ref[k] - b0[k]
+        assert _rel(dg, dr) < 1e-8, k
+    for k in ("x", "y", "xi"):
+        assert np.max(np.abs(got[k] - ref[k])) < 1e-10, k
+
+
+def test_schedule_replay(qs):
+    wl = W.workload("linear64").with_(n_xi=32, xi_len=3.0)
+    sched = [1, 2, 1, 3] * 8
+    r = _run_both(qs, wl, schedule=sched)
+    assert list(r["m"]) == sched
+    assert r["stats"]["slices"] == r["ref"].slices
+    _check_fields(r, 1e-9)
+
+
+def test_errors_are_statuses(qs):
+    wl = W.workload("linear64")
+    ctx = qs.Context(qs.config_from_workload(wl))
+    with pytest.raises(qs.QsError) as e:
+        ctx.step3d([])
+    assert e.value.status == qs.QS_ERR_STATE
+    with pytest.raises(qs.QsError) as e:
+        ctx.fields()
+    assert e.value.status == qs.QS_ERR_STATE
+    # a V-cycle cap of one with a tight tolerance cannot converge
+    ctx2 = qs.Context(qs.config_from_workload(wl.with_(n_xi=8, xi_len=2.0), mg_tol=1e-14,
+                                              mg_max_vcycles=1))
+    ctx2.init_plasma(4)
+    st = ctx2.step3d([qs.Beam(W.sample_beam(wl.beams[0]))], raise_on_error=False)
+    assert st["status"] == qs.QS_ERR_NOT_CONVERGED
+    # the context stays usable afterwards
+    ctx3 = qs.Context(qs.config_from_workload(wl.with_(n_xi=8, xi_len=2.0)))
+    ctx3.init_plasma(4)
+    assert ctx3.step3d([])["status"] == 0
