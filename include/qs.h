@@ -85,7 +85,12 @@ typedef struct {
     int sort_every;             /* cell-sort the plasma every this many slices; */
                                 /* 0 = only at the start of a step              */
     int pre_sweeps, post_sweeps;/* red-black Gauss-Seidel sweeps per level      */
-    int reserved[8];            /* must be zero                                  */
+    int coarse_block_n;         /* multigrid levels of side <= this are relaxed  */
+                                /* by one thread block in shared memory;         */
+                                /* 0 = default (16 for QS_FP64, 64 for refined) */
+    int trace_capacity;         /* > 0: record up to this many phase timestamps */
+                                /* per step (see qs_phase_trace); 0 = off        */
+    int reserved[6];            /* must be zero                                  */
 } qs_config;
 
 /* Driver-beam macroparticles: structure of arrays of float64, n entries each.
@@ -196,6 +201,13 @@ int qs_slice_diagnostics(qs_ctx *ctx, int32_t *m, double *vmax, double *charge);
 int qs_get_plasma(qs_ctx *ctx, double *x, double *y, double *px, double *py, double *w,
                   int32_t *id);
 int64_t qs_plasma_count(const qs_ctx *ctx);
+
+/* Phase trace of the last qs_step3d (config.trace_capacity > 0): for each
+ * grid barrier of the slice engine, in order, the id of the phase that
+ * ended there (`where`) and the device clock in nanoseconds
+ * (`t_ns`, %globaltimer).  Entry 0 is the kernel start.  HOST arrays of `cap`
+ * entries; returns the number of entries written (>= 0) or a status < 0. */
+int qs_phase_trace(qs_ctx *ctx, int32_t *where, int64_t *t_ns, int cap);
 
 /* Stable counting sort of n particles by cell, c = iy * N + ix with
  * ix = floor((x - x_min) / h) clamped to [0, N-1], ties in ascending id.

@@ -43,7 +43,9 @@ class QsConfig(ctypes.Structure):
         ("max_psi_guard_hits", ctypes.c_int64),
         ("sort_every", ctypes.c_int),
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
-        ("reserved", ctypes.c_int * 8),
+        ("coarse_block_n", ctypes.c_int),
+        ("trace_capacity", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
     ]
 
 
@@ -85,6 +87,7 @@ PROTOTYPES = {
     "qs_get_plasma": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "qs_plasma_count": (_I64, [_P]),
     "qs_cell_sort": (_I, [_P, _P, _P, _P, _I64, _P, _P, _P, _P]),
+    "qs_phase_trace": (_I, [_P, _P, _P, _I]),
     "qs_strerror": (ctypes.c_char_p, [_I]),
     "qs_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -282,6 +285,17 @@ class Context:
         self._check(self.lib.qs_get_plasma(self.h, *[a.ctypes.data for a in arrs], pid.ctypes.data),
                     "qs_get_plasma")
         return dict(zip(("x", "y", "px", "py", "w"), arrs), id=pid)
+
+    def phase_trace(self):
+        """(where, t_ns) arrays of the last step's phase trace."""
+        import numpy as np
+        cap = max(1, int(self.cfg.trace_capacity))
+        wh = np.zeros(cap, dtype=np.int32)
+        tn = np.zeros(cap, dtype=np.int64)
+        k = self.lib.qs_phase_trace(self.h, wh.ctypes.data, tn.ctypes.data, cap)
+        if k < 0:
+            self._check(k, "qs_phase_trace")
+        return wh[:k], tn[:k]
 
     def cell_sort(self, x, y, pid):
         """Run the library's cell sort on CUDA tensors; returns (cell, count, offset, perm)."""

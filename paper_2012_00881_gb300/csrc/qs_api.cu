@@ -24,14 +24,20 @@ struct qs_ctx {
            *G = nullptr;
     double *psi = nullptr, *ez = nullptr, *bz = nullptr, *bx = nullptr, *by = nullptr;
     double *f_psi = nullptr, *f_ez = nullptr, *f_bz = nullptr, *f_bx = nullptr, *f_by = nullptr;
-    double *dpx = nullptr, *dpy = nullptr, *jz = nullptr, *kap = nullptr;
+    double *dpx = nullptr, *dpy = nullptr, *jz = nullptr, *kap = nullptr, *invd0 = nullptr;
     LevelArrays lev[QS_MAX_LEV] = {};
+    float *e32[2] = {nullptr, nullptr}, *r32[2] = {nullptr, nullptr};
+    float *k32 = nullptr, *d32 = nullptr;
+    LevelArrays32 lev32[QS_MAX_LEV] = {};
+    int block_level_n = 16;
+    int tile_x = 0, tile_y = 0;
     double *hist = nullptr, *jzb = nullptr;
     DevScalars *sc = nullptr;
     int32_t *diag_m = nullptr, *d_sched = nullptr;
     double *diag_vmax = nullptr, *diag_charge = nullptr;
     // sort scratch
     int32_t *s_cursor = nullptr;
+    int64_t *trace = nullptr;
     // plasma
     int64_t np = 0;
     int ppc = 0;
@@ -134,7 +140,15 @@ int validate(const qs_config *cfg, char *why, size_t nwhy) {
         snprintf(why, nwhy, "sort_every must be >= 0");
         return QS_ERR_ARG;
     }
-    for (int i = 0; i < 8; ++i)
+    if (cfg->coarse_block_n < 0 || cfg->coarse_block_n > 4096) {
+        snprintf(why, nwhy, "coarse_block_n must be in [0, 4096]");
+        return QS_ERR_ARG;
+    }
+    if (cfg->trace_capacity < 0 || cfg->trace_capacity > (1 << 26)) {
+        snprintf(why, nwhy, "trace_capacity must be in [0, 2^26]");
+        return QS_ERR_ARG;
+    }
+    for (int i = 0; i < 6; ++i)
         if (cfg->reserved[i] != 0) {
             snprintf(why, nwhy, "reserved fields must be zero");
             return QS_ERR_ARG;
@@ -159,15 +173,35 @@ int create_impl(qs_ctx *c) {
     double **grids[] = {&c->n_a, &c->n_b, &c->n_ion, &c->jx,  &c->jy,   &c->txx, &c->txy,
                         &c->tyy, &c->G,   &c->psi,   &c->ez,  &c->bz,   &c->bx,  &c->by,
                         &c->f_psi, &c->f_ez, &c->f_bz, &c->f_bx, &c->f_by, &c->dpx, &c->dpy,
-                        &c->jz,  &c->kap};
+                        &c->jz,  &c->kap, &c->invd0};
     for (double **p : grids) AL(L, *p, nn);
+    const bool ref = g.precision == QS_FP32_REFINED;
     for (int l = 1; l < c->nlev; ++l) {
         const size_t m = (size_t)c->lev_n[l] * c->lev_n[l];
-        AL(L, c->lev[l].u[0], m);
-        AL(L, c->lev[l].u[1], m);
-        AL(L, c->lev[l].f[0], m);
-        AL(L, c->lev[l].f[1], m);
-        AL(L, c->lev[l].kap, m);
+        if (ref) {
+            AL(L, c->lev32[l].u[0], m);
+            AL(L, c->lev32[l].u[1], m);
+            AL(L, c->lev32[l].f[0], m);
+            AL(L, c->lev32[l].f[1], m);
+            AL(L, c->lev32[l].k, m);
+            AL(L, c->lev32[l].d, m);
+            AL(L, c->lev32[l].up[0], m);
+            AL(L, c->lev32[l].up[1], m);
+        } else {
+            AL(L, c->lev[l].u[0], m);
+            AL(L, c->lev[l].u[1], m);
+            AL(L, c->lev[l].f[0], m);
+            AL(L, c->lev[l].f[1], m);
+            AL(L, c->lev[l].kap, m);
+            AL(L, c->lev[l].d, m);
+        }
+    }
+    if (ref) {
+        float **g32[] = {&c->e32[0], &c->e32[1], &c->r32[0], &c->r32[1], &c->k32, &c->d32};
+        for (float **p : g32) {
+            AL(L, *p, nn);
+            CK(cudaMemsetAsync(*p, 0, nn * sizeof(float), c->st), "memset");
+        }
     }
     AL(L, c->hist, 5 * (size_t)g.n_xi * nn);
     AL(L, c->jzb, (size_t)g.n_xi * nn);
@@ -177,13 +211,22 @@ int create_impl(qs_ctx *c) {
     AL(L, c->diag_vmax, (size_t)g.n_xi);
     AL(L, c->diag_charge, (size_t)g.n_xi);
     AL(L, c->s_cursor, nn);
+    if (g.trace_capacity > 0) AL(L, c->trace, 2 * (size_t)g.trace_capacity);
     // fields start at zero (the warm start of the first slice)
     for (double **p : grids) CK(cudaMemsetAsync(*p, 0, nn * sizeof(double), c->st), "memset");
     CK(cudaMemsetAsync(c->hist, 0, 5 * (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
     CK(cudaMemsetAsync(c->jzb, 0, (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
-    c->engine_smem = 36 * 1024;
+    c->block_level_n = g.coarse_block_n > 0 ? g.coarse_block_n : (ref ? 64 : 16);
+    c->tile_x = ref ? 32 : 0;
+    c->tile_y = ref ? 16 : 0;
+    const int nu = g.pre_sweeps > g.post_sweeps ? g.pre_sweeps : g.post_sweeps;
+    c->engine_smem = qs_engine_smem_bytes(c->lev_n, c->nlev, c->block_level_n, g.precision,
+                                          c->tile_x, c->tile_y, nu);
+    if (c->engine_smem > 200 * 1024)
+        return fail(c, QS_ERR_ARG, "coarse_block_n = %d needs %zu bytes of shared memory",
+                    c->block_level_n, c->engine_smem);
     int blocks = 0;
-    if (qs_engine_max_blocks(c->dev, c->engine_smem, &blocks) != 0 || blocks < 1)
+    if (qs_engine_max_blocks(c->dev, g.precision, c->engine_smem, &blocks) != 0 || blocks < 1)
         return fail(c, QS_ERR_CUDA, "slice engine cannot be made resident");
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev), "attr");
@@ -408,14 +451,25 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
     a.dpy = c->dpy;
     a.jz = c->jz;
     a.kap = c->kap;
+    a.invd0 = c->invd0;
     a.nlev = c->nlev;
     for (int l = 0; l < c->nlev; ++l) {
         a.lev_n[l] = c->lev_n[l];
         const double hl = c->h * (double)(1 << l);
         a.lev_h2[l] = hl * hl;
         a.lev[l] = c->lev[l];
+        a.lev32[l] = c->lev32[l];
     }
-    a.block_level_n = 16;
+    a.block_level_n = c->block_level_n;
+    a.tile_x = c->tile_x;
+    a.tile_y = c->tile_y;
+    a.precision = g.precision;
+    for (int k = 0; k < 2; ++k) {
+        a.e32[k] = c->e32[k];
+        a.r32[k] = c->r32[k];
+    }
+    a.k32 = c->k32;
+    a.d32 = c->d32;
     a.hist = c->hist;
     a.jzb = c->jzb;
     a.m_sched = sched ? c->d_sched : nullptr;
@@ -423,6 +477,8 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
     a.diag_vmax = c->diag_vmax;
     a.diag_charge = c->diag_charge;
     a.sc = c->sc;
+    a.trace = c->trace;
+    a.trace_cap = g.trace_capacity;
     CK(cudaEventRecord(c->ev0, c->st), "event");
     CK(qs_launch_engine(c->st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
     CK(cudaEventRecord(c->ev1, c->st), "event");
@@ -554,6 +610,25 @@ int qs_cell_sort(qs_ctx *c, const double *x, const double *y, const int32_t *id,
        "cell sort");
     CK(cudaStreamSynchronize(c->st), "cell sort");
     return QS_OK;
+}
+
+int qs_phase_trace(qs_ctx *c, int32_t *where, int64_t *t_ns, int cap) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_step) return fail(c, QS_ERR_STATE, "qs_step3d has not been run");
+    if (!c->trace || cap < 0) return 0;
+    DevScalars hs;
+    CK(cudaMemcpy(&hs, c->sc, sizeof(hs), cudaMemcpyDeviceToHost), "copy scalars");
+    long long n = (long long)hs.trace_n;
+    if (n > cap) n = cap;
+    std::vector<int64_t> buf(2 * (size_t)n);
+    if (n > 0)
+        CK(cudaMemcpy(buf.data(), c->trace, 2 * n * sizeof(int64_t), cudaMemcpyDeviceToHost),
+           "copy trace");
+    for (long long k = 0; k < n; ++k) {
+        if (where) where[k] = (int32_t)buf[2 * k];
+        if (t_ns) t_ns[k] = buf[2 * k + 1];
+    }
+    return (int)n;
 }
 
 const char *qs_strerror(int status) {

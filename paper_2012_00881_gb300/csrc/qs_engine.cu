@@ -11,7 +11,7 @@
 // is at most block_level_n are relaxed by block 0 alone.
 #include <cuda_runtime.h>
 
-#include "qs_internal.cuh"
+#include "qs_tile.cuh"
 
 namespace {
 
@@ -31,11 +31,19 @@ __device__ __forceinline__ unsigned long long vload(const unsigned long long *p)
     return *(const volatile unsigned long long *)p;
 }
 
+__device__ __forceinline__ int64_t global_ns() {
+    int64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).
 struct Sync {
     DevScalars *sc;
     unsigned nblk;
     long long limit;
+    int64_t *trace;
+    int trace_cap;
     __device__ bool operator()(int where) const {
         __shared__ int s_ok;
         __syncthreads();
@@ -69,19 +77,24 @@ struct Sync {
                 __threadfence();
             }
             s_ok = ok;
+            if (trace && blockIdx.x == 0) {
+                const unsigned long long k = sc->trace_n;
+                if (k < (unsigned long long)trace_cap) {
+                    trace[2 * k] = where;
+                    trace[2 * k + 1] = global_ns();
+                    sc->trace_n = k + 1;
+                }
+            }
         }
         __syncthreads();
         return s_ok != 0;
     }
 };
 
-struct Thr {
-    int t0, nt;
-};
+using qsmg::Thr;
 __device__ __forceinline__ Thr grid_thr(int bid, int nblk) {
     return Thr{bid * (int)blockDim.x + (int)threadIdx.x, nblk * (int)blockDim.x};
 }
-__device__ __forceinline__ Thr block_thr() { return Thr{(int)threadIdx.x, (int)blockDim.x}; }
 
 // sum over the block; valid in thread 0
 __device__ double block_sum(double v) {
@@ -116,244 +129,198 @@ __device__ double block_max(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// multigrid on one solve (1 or 2 components sharing the operator)
+// multigrid solves (1 or 2 components sharing the operator)
 // ---------------------------------------------------------------------------
-struct SolveView {
-    int ncomp;
+using qsmg::Hier;
+using qsmg::Lvl;
+
+struct SolveSpec {
+    int nc;
     int kind;  // 0 psi, 1 (Ez,Bz), 2 (Bx,By): index into fnorm / vcycles
-    double *u0[2];
-    double *f0[2];
-    double *k0;  // kappa at level 0, nullptr for the Poisson operator
+    double *u[2];
+    double *f[2];
+    bool screened;
 };
 
-__device__ __forceinline__ double *Ul(const EngineArgs &A, const SolveView &V, int l, int c) {
-    return l == 0 ? V.u0[c] : A.lev[l].u[c];
-}
-__device__ __forceinline__ double *Fl(const EngineArgs &A, const SolveView &V, int l, int c) {
-    return l == 0 ? V.f0[c] : A.lev[l].f[c];
-}
-__device__ __forceinline__ const double *Kl(const EngineArgs &A, const SolveView &V, int l) {
-    if (!V.k0) return nullptr;
-    return l == 0 ? V.k0 : A.lev[l].kap;
-}
-
-// (lap_h - kappa) u at (ix, iy) with odd (zero-wall) ghosts
-__device__ __forceinline__ double apply_op(const double *u, const double *kap, int n,
-                                           double inv_h2, int ix, int iy) {
-    int i = iy * n + ix;
-    double uc = u[i];
-    double nb = 0.0;
-    int nw = 0;
-    if (ix > 0) nb += u[i - 1]; else ++nw;
-    if (ix < n - 1) nb += u[i + 1]; else ++nw;
-    if (iy > 0) nb += u[i - n]; else ++nw;
-    if (iy < n - 1) nb += u[i + n]; else ++nw;
-    double r = (nb - (4.0 + nw) * uc) * inv_h2;
-    if (kap) r -= kap[i] * uc;
-    return r;
+__device__ void hier64(const EngineArgs &A, const SolveSpec &V, Hier<double> &H) {
+    H.L = A.nlev;
+    for (int l = 0; l < A.nlev; ++l) {
+        Lvl<double> &v = H.lv[l];
+        v.n = A.lev_n[l];
+        v.h2 = A.lev_h2[l];
+        for (int c = 0; c < 2; ++c) {
+            v.u[c] = l == 0 ? V.u[c] : A.lev[l].u[c];
+            v.f[c] = l == 0 ? V.f[c] : A.lev[l].f[c];
+        }
+        v.k = V.screened ? (l == 0 ? A.kap : A.lev[l].kap) : nullptr;
+        v.d = V.screened ? (l == 0 ? A.invd0 : A.lev[l].d) : nullptr;
+    }
 }
 
-__device__ void relax_half(const EngineArgs &A, const SolveView &V, int l, int color, Thr T) {
-    const int n = A.lev_n[l];
-    const double h2 = A.lev_h2[l];
-    const double *kap = Kl(A, V, l);
+__device__ void hier32(const EngineArgs &A, const SolveSpec &V, Hier<float> &H) {
+    H.L = A.nlev;
+    for (int l = 0; l < A.nlev; ++l) {
+        Lvl<float> &v = H.lv[l];
+        v.n = A.lev_n[l];
+        v.h2 = A.lev_h2[l];
+        for (int c = 0; c < 2; ++c) {
+            v.u[c] = l == 0 ? A.e32[c] : A.lev32[l].u[c];
+            v.f[c] = l == 0 ? A.r32[c] : A.lev32[l].f[c];
+        }
+        v.k = V.screened ? (l == 0 ? A.k32 : A.lev32[l].k) : nullptr;
+        v.d = V.screened ? (l == 0 ? A.d32 : A.lev32[l].d) : nullptr;
+    }
+}
+
+// Level-0 red-black half sweep of the float32 correction that also adds the
+// final correction into the float64 iterate: u64 += e at the points this
+// thread updates and at the points of the other colour (not written here).
+__device__ void relax_half_finalize(const Lvl<float> &L, int nc, int color, Thr R,
+                                    double *const u64[2]) {
+    const int n = L.n;
+    const float h2 = (float)L.h2;
     const int npts = (n & 1) ? n * n : (n * n) / 2;
     const int hn = n >> 1;
-    for (int k = T.t0; k < npts; k += T.nt) {
-        int ix, iy;
-        if (n & 1) {
-            iy = k / n;
-            ix = k - iy * n;
-            if (((ix + iy) & 1) != color) continue;
-        } else {
-            iy = k / hn;
-            ix = 2 * (k - iy * hn) + ((iy + color) & 1);
-        }
-        const int i = iy * n + ix;
-        int nw = (ix == 0) + (ix == n - 1) + (iy == 0) + (iy == n - 1);
-        double d = 4.0 + nw + (kap ? h2 * kap[i] : 0.0);
-        double inv_d = 1.0 / d;
-        for (int c = 0; c < V.ncomp; ++c) {
-            double *u = Ul(A, V, l, c);
-            const double *f = Fl(A, V, l, c);
-            double nb = 0.0;
-            if (ix > 0) nb += u[i - 1];
-            if (ix < n - 1) nb += u[i + 1];
-            if (iy > 0) nb += u[i - n];
-            if (iy < n - 1) nb += u[i + n];
-            u[i] = (nb - h2 * f[i]) * inv_d;
-        }
-    }
-}
-
-// f_{l+1} = 4-cell average of (f - A u) at level l; u_{l+1} = 0; for the
-// screened operator also kappa_{l+1} = 4-cell average of kappa_l
-__device__ void restrict_residual(const EngineArgs &A, const SolveView &V, int l, Thr T) {
-    const int n = A.lev_n[l], nc = A.lev_n[l + 1];
-    const double inv_h2 = 1.0 / A.lev_h2[l];
-    const double *kap = Kl(A, V, l);
-    for (int k = T.t0; k < nc * nc; k += T.nt) {
-        const int J = k / nc, I = k - J * nc;
-        for (int c = 0; c < V.ncomp; ++c) {
-            const double *u = Ul(A, V, l, c);
-            const double *f = Fl(A, V, l, c);
-            double s = 0.0;
-            for (int b = 0; b < 2; ++b)
-                for (int a = 0; a < 2; ++a) {
-                    int ix = 2 * I + a, iy = 2 * J + b;
-                    s += f[iy * n + ix] - apply_op(u, kap, n, inv_h2, ix, iy);
+    for (int pass = 0; pass < 2; ++pass) {
+        const int col = pass == 0 ? color : 1 - color;
+        for (int q = R.t0; q < npts; q += R.nt) {
+            int ix, iy;
+            if (n & 1) {
+                iy = q / n;
+                ix = q - iy * n;
+                if (((ix + iy) & 1) != col) continue;
+            } else {
+                iy = q / hn;
+                ix = 2 * (q - iy * hn) + ((iy + col) & 1);
+            }
+            const int i = iy * n + ix;
+            if (pass == 0) {
+                const float di = qsmg::inv_diag(L, i, qsmg::walls(ix, iy, n));
+                for (int c = 0; c < nc; ++c) {
+                    float *u = L.u[c];
+                    float nb = 0.f;
+                    if (ix > 0) nb += u[i - 1];
+                    if (ix < n - 1) nb += u[i + 1];
+                    if (iy > 0) nb += u[i - n];
+                    if (iy < n - 1) nb += u[i + n];
+                    const float e = (nb - h2 * L.f[c][i]) * di;
+                    u[i] = e;
+                    u64[c][i] += (double)e;
                 }
-            Fl(A, V, l + 1, c)[k] = 0.25 * s;
-            Ul(A, V, l + 1, c)[k] = 0.0;
-        }
-        if (kap) {  // coarse kappa: average of the four children
-            const int i0 = (2 * J) * n + 2 * I;
-            A.lev[l + 1].kap[k] = 0.25 * (kap[i0] + kap[i0 + 1] + kap[i0 + n] + kap[i0 + n + 1]);
+            } else {
+                for (int c = 0; c < nc; ++c) u64[c][i] += (double)L.u[c][i];
+            }
         }
     }
 }
 
-// u_l += bilinear interpolation of u_{l+1} (cell-centred, odd ghosts)
-__device__ void prolong_correct(const EngineArgs &A, const SolveView &V, int l, Thr T) {
-    const int n = A.lev_n[l], nc = A.lev_n[l + 1];
-    for (int k = T.t0; k < n * n; k += T.nt) {
-        const int iy = k / n, ix = k - iy * n;
-        const int I = ix >> 1, J = iy >> 1;
-        const int I2 = I + ((ix & 1) ? 1 : -1);
-        const int J2 = J + ((iy & 1) ? 1 : -1);
-        const bool xin = (I2 >= 0 && I2 < nc), yin = (J2 >= 0 && J2 < nc);
-        for (int c = 0; c < V.ncomp; ++c) {
-            const double *uc = Ul(A, V, l + 1, c);
-            double v00 = uc[J * nc + I];
-            double v10 = xin ? uc[J * nc + I2] : -v00;
-            double v01 = yin ? uc[J2 * nc + I] : -v00;
-            double v11;
-            if (xin && yin) v11 = uc[J2 * nc + I2];
-            else if (xin) v11 = -uc[J * nc + I2];
-            else if (yin) v11 = -uc[J2 * nc + I];
-            else v11 = v00;
-            Ul(A, V, l, c)[k] += (9.0 * v00 + 3.0 * v10 + 3.0 * v01 + v11) * 0.0625;
-        }
-    }
-}
-
-// Dense solve on the coarsest level by block 0: Gaussian elimination of the
-// symmetric positive definite matrix -(lap_h - kappa), no pivoting needed.
-__device__ void coarse_solve(const EngineArgs &A, const SolveView &V, double *sm) {
-    const int l = A.nlev - 1;
-    const int n = A.lev_n[l], m = n * n, nc = V.ncomp;
-    const int ld = m + 2;
-    const double inv_h2 = 1.0 / A.lev_h2[l];
-    const double *kap = Kl(A, V, l);
-    double *fac = sm + m * ld;  // m factors
-    for (int idx = threadIdx.x; idx < m * ld; idx += blockDim.x) sm[idx] = 0.0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const int iy = i / n, ix = i - iy * n;
-        int nw = (ix == 0) + (ix == n - 1) + (iy == 0) + (iy == n - 1);
-        sm[i * ld + i] = (4.0 + nw) * inv_h2 + (kap ? kap[i] : 0.0);
-        if (ix > 0) sm[i * ld + i - 1] = -inv_h2;
-        if (ix < n - 1) sm[i * ld + i + 1] = -inv_h2;
-        if (iy > 0) sm[i * ld + i - n] = -inv_h2;
-        if (iy < n - 1) sm[i * ld + i + n] = -inv_h2;
-        for (int c = 0; c < nc; ++c) sm[i * ld + m + c] = -Fl(A, V, l, c)[i];
-    }
-    __syncthreads();
-    const int ncol = m + nc;
-    for (int k = 0; k < m - 1; ++k) {
-        const double piv = sm[k * ld + k];
-        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) fac[i] = sm[i * ld + k] / piv;
-        __syncthreads();
-        const int rows = m - k - 1, cols = ncol - k;
-        for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-            const int i = k + 1 + e / cols, j = k + e % cols;
-            sm[i * ld + j] -= fac[i] * sm[k * ld + j];
-        }
-        __syncthreads();
-    }
-    if ((int)threadIdx.x < nc) {
-        const int c = threadIdx.x;
-        double *u = Ul(A, V, l, c);
-        for (int i = m - 1; i >= 0; --i) {
-            double s = sm[i * ld + m + c];
-            for (int j = i + 1; j < m; ++j) s -= sm[i * ld + j] * u[j];
-            u[i] = s / sm[i * ld + i];
-        }
-    }
-    __syncthreads();
-}
-
-__device__ bool vcycle(const EngineArgs &A, const Sync &S, const SolveView &V, int bid, int nblk,
-                       double *sm) {
-    const int L = A.nlev;
+// One V-cycle on hierarchy H.  Levels of side > block_level_n are relaxed by
+// the whole grid, the rest by block 0 in shared memory.  With `fin` set (the
+// refined form) the float32 correction is added into the float64 iterate
+// during the last level-0 phase.
+template <typename T>
+__device__ bool vcycle(const EngineArgs &A, const Sync &S, const Hier<T> &H, int nc, int bid,
+                       int nblk, void *smem, double *const *fin) {
+    const int L = H.L;
     int lg = 0;
-    while (lg < L - 1 && A.lev_n[lg] > A.block_level_n) ++lg;
-    const Thr T = grid_thr(bid, nblk);
+    while (lg < L - 1 && H.lv[lg].n > A.block_level_n) ++lg;
+    const Thr T0 = grid_thr(bid, nblk);
     for (int l = 0; l < lg; ++l) {
         for (int s = 0; s < A.nu1; ++s) {
-            relax_half(A, V, l, 0, T);
+            qsmg::relax_half(H.lv[l], nc, 0, T0);
             SYNC(10);
-            relax_half(A, V, l, 1, T);
+            qsmg::relax_half(H.lv[l], nc, 1, T0);
             SYNC(11);
         }
-        restrict_residual(A, V, l, T);
+        qsmg::restrict_res(H.lv[l], H.lv[l + 1], nc, T0);
         SYNC(12);
     }
-    if (bid == 0) {
-        const Thr B = block_thr();
-        for (int l = lg; l < L - 1; ++l) {
-            for (int s = 0; s < A.nu1; ++s) {
-                relax_half(A, V, l, 0, B);
-                __syncthreads();
-                relax_half(A, V, l, 1, B);
-                __syncthreads();
+    if (bid == 0) qsmg::block_vcycle(H, lg, nc, A.nu1, A.nu2, smem);
+    SYNC(13);
+    if constexpr (sizeof(T) == 4) {
+        if (fin && (lg == 0 || A.nu2 == 0)) {
+            // no fused level-0 sweep: add the correction in a phase of its own
+            for (int l = lg - 1; l >= 0; --l) {
+                qsmg::prolong_add(H.lv[l], H.lv[l + 1], nc, T0);
+                SYNC(14);
             }
-            restrict_residual(A, V, l, B);
-            __syncthreads();
-        }
-        coarse_solve(A, V, sm);
-        for (int l = L - 2; l >= lg; --l) {
-            prolong_correct(A, V, l, B);
-            __syncthreads();
-            for (int s = 0; s < A.nu2; ++s) {
-                relax_half(A, V, l, 0, B);
-                __syncthreads();
-                relax_half(A, V, l, 1, B);
-                __syncthreads();
-            }
+            const int nn = H.lv[0].n * H.lv[0].n;
+            for (int q = T0.t0; q < nn; q += T0.nt)
+                for (int c = 0; c < nc; ++c) fin[c][q] += (double)H.lv[0].u[c][q];
+            SYNC(17);
+            return true;
         }
     }
-    SYNC(13);
     for (int l = lg - 1; l >= 0; --l) {
-        prolong_correct(A, V, l, T);
+        qsmg::prolong_add(H.lv[l], H.lv[l + 1], nc, T0);
         SYNC(14);
         for (int s = 0; s < A.nu2; ++s) {
-            relax_half(A, V, l, 0, T);
+            qsmg::relax_half(H.lv[l], nc, 0, T0);
             SYNC(15);
-            relax_half(A, V, l, 1, T);
+            if constexpr (sizeof(T) == 4) {
+                if (fin && l == 0 && s == A.nu2 - 1) {
+                    relax_half_finalize(H.lv[0], nc, 1, T0, fin);
+                    SYNC(16);
+                    continue;
+                }
+            }
+            qsmg::relax_half(H.lv[l], nc, 1, T0);
             SYNC(16);
         }
     }
     return true;
 }
 
-// ||f - A u||^2 and ||u||^2 per component at level 0, accumulated into
-// out[c] and out[2 + c]
-__device__ void residual_norm(const EngineArgs &A, const SolveView &V, double *out, Thr T) {
-    const int n = A.lev_n[0];
+// Refined form: one float32 V-cycle on the correction with the grid-wide
+// levels staged tile by tile (two grid barriers per level), the coarse levels
+// on block 0 in shared memory, and the correction added into the float64
+// iterate `fin` by the last level-0 phase.
+__device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<float> &H, int nc,
+                              int bid, int nblk, void *smem, double *const *fin) {
+    const int L = H.L;
+    int lg = 0;
+    while (lg < L - 1 && H.lv[lg].n > A.block_level_n) ++lg;
+    if (lg == 0) return vcycle<float>(A, S, H, nc, bid, nblk, smem, fin);
+    float *sm = (float *)smem;
+    for (int l = 0; l < lg; ++l) {
+        qstile::down_level(H.lv[l], H.lv[l + 1], nc, A.nu1, A.tile_x, A.tile_y, sm, bid, nblk);
+        SYNC(30);
+    }
+    if (bid == 0) qsmg::block_vcycle(H, lg, nc, A.nu1, A.nu2, smem);
+    SYNC(31);
+    for (int l = lg - 1; l >= 0; --l) {
+        float *const *cu = (l + 1 == lg) ? H.lv[lg].u : A.lev32[l + 1].up;
+        qstile::up_level(H.lv[l], cu, H.lv[l + 1].n, nc, A.nu2, A.tile_x, A.tile_y, sm, bid, nblk,
+                         A.lev32[l].up, l == 0 ? fin : nullptr);
+        SYNC(32);
+    }
+    return true;
+}
+
+// ||f - A u||^2 and ||u||^2 per component at level 0 in float64, accumulated
+// into out[c] and out[2 + c].  For the refined form the residual also becomes
+// the float32 right-hand side of the next inner cycle, whose correction
+// starts at zero.
+__device__ void residual_norm(const EngineArgs &A, const SolveSpec &V, double *out, Thr T,
+                              bool to32) {
+    const int n = A.N;
     const double inv_h2 = 1.0 / A.lev_h2[0];
-    const double *kap = Kl(A, V, 0);
+    const double *kap = V.screened ? A.kap : nullptr;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k = T.t0; k < n * n; k += T.nt) {
         const int iy = k / n, ix = k - iy * n;
-        for (int c = 0; c < V.ncomp; ++c) {
-            const double r = V.f0[c][k] - apply_op(V.u0[c], kap, n, inv_h2, ix, iy);
-            const double u = V.u0[c][k];
+        for (int c = 0; c < V.nc; ++c) {
+            const double r = V.f[c][k] - qsmg::apply_op<double>(V.u[c], kap, n, inv_h2, ix, iy);
+            const double u = V.u[c][k];
             s[c] += r * r;
             s[2 + c] += u * u;
+            if (to32) {
+                A.r32[c][k] = (float)r;
+                A.e32[c][k] = 0.f;
+            }
         }
     }
-    for (int c = 0; c < V.ncomp; ++c) {
+    for (int c = 0; c < V.nc; ++c) {
         double t = block_sum(s[c]);
         if (threadIdx.x == 0) atomicAdd(out + c, t);
         t = block_sum(s[2 + c]);
@@ -361,16 +328,19 @@ __device__ void residual_norm(const EngineArgs &A, const SolveView &V, double *o
     }
 }
 
-// V-cycles until, for every component,
+// Iterate until, for every component,
 //   ||f - A u|| <= max(tol ||f||, 1e-13 ||u|| / h^2, atol)
 // (the second bound is a small multiple of the rounding level of the
-// residual itself; atol stops solves whose source is rounding noise).
-__device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveView &V, int &slot,
-                         int bid, int nblk, double *sm) {
+// float64 residual; atol stops solves whose source is rounding noise).
+// Float64 form: V-cycles on u.  Refined form: float64 residual, float32
+// V-cycle on the correction, float64 update (iterative refinement).
+template <bool REF>
+__device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V, int &slot,
+                         int bid, int nblk, void *smem) {
     DevScalars *sc = A.sc;
     double fn[2] = {0.0, 0.0};
     bool any_zero = false, all_zero = true;
-    for (int c = 0; c < V.ncomp; ++c) {
+    for (int c = 0; c < V.nc; ++c) {
         fn[c] = vload(&sc->fnorm[V.kind][c]);
         if (fn[c] == 0.0) any_zero = true;
         else all_zero = false;
@@ -378,38 +348,53 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveView &V,
     const Thr T = grid_thr(bid, nblk);
     if (any_zero) {
         const int nn = A.N * A.N;
-        for (int c = 0; c < V.ncomp; ++c)
+        for (int c = 0; c < V.nc; ++c)
             if (fn[c] == 0.0)
-                for (int k = T.t0; k < nn; k += T.nt) V.u0[c][k] = 0.0;
+                for (int k = T.t0; k < nn; k += T.nt) V.u[c][k] = 0.0;
         SYNC(20);
     }
     if (all_zero) return true;
+    Hier<double> H64;
+    Hier<float> H32;
+    if (REF) hier32(A, V, H32);
+    else hier64(A, V, H64);
     bool conv = false;
     double rel = 0.0;
     int it = 0;
-    for (; it < A.mg_max_vcycles; ++it) {
-        if (!vcycle(A, S, V, bid, nblk, sm)) return false;
-        residual_norm(A, V, sc->rnorm[slot & 3], T);
-        if (bid == 0 && threadIdx.x == 0)
-            for (int e = 0; e < 4; ++e) sc->rnorm[(slot + 2) & 3][e] = 0.0;
-        SYNC(21);
-        conv = true;
-        rel = 0.0;
-        for (int c = 0; c < V.ncomp; ++c) {
-            if (fn[c] == 0.0) continue;
-            const double rn = vload(&sc->rnorm[slot & 3][c]);
-            const double un = vload(&sc->rnorm[slot & 3][2 + c]);
-            const double fl = 1e-13 / A.lev_h2[0];
-            double thr = fmax(A.mg_tol * A.mg_tol * fn[c], A.mg_atol * A.mg_atol);
-            thr = fmax(thr, fl * fl * un);
-            if (rn > thr) conv = false;
-            rel = fmax(rel, sqrt(rn / fn[c]));
+    const double fl = 1e-13 / A.lev_h2[0];
+    for (;;) {
+        if (REF || it > 0) {
+            residual_norm(A, V, sc->rnorm[slot & 3], T, REF);
+            if (bid == 0 && threadIdx.x == 0)
+                for (int e = 0; e < 4; ++e) sc->rnorm[(slot + 2) & 3][e] = 0.0;
+            SYNC(21);
+            conv = true;
+            rel = 0.0;
+            for (int c = 0; c < V.nc; ++c) {
+                if (fn[c] == 0.0) continue;
+                const double rn = vload(&sc->rnorm[slot & 3][c]);
+                const double un = vload(&sc->rnorm[slot & 3][2 + c]);
+                double thr = fmax(A.mg_tol * A.mg_tol * fn[c], A.mg_atol * A.mg_atol);
+                thr = fmax(thr, fl * fl * un);
+                if (rn > thr) conv = false;
+                rel = fmax(rel, sqrt(rn / fn[c]));
+            }
+            ++slot;
+            if (conv || it >= A.mg_max_vcycles) break;
         }
-        ++slot;
-        if (conv) break;
+        bool ok;
+        if (REF) {
+            double *fin[2] = {V.u[0], V.u[1]};
+            ok = A.tile_x > 0 ? vcycle_staged(A, S, H32, V.nc, bid, nblk, smem, fin)
+                              : vcycle<float>(A, S, H32, V.nc, bid, nblk, smem, fin);
+        } else {
+            ok = vcycle<double>(A, S, H64, V.nc, bid, nblk, smem, nullptr);
+        }
+        if (!ok) return false;
+        ++it;
     }
     if (bid == 0 && threadIdx.x == 0) {
-        sc->vcycles[V.kind] += (it < A.mg_max_vcycles) ? it + 1 : it;
+        sc->vcycles[V.kind] += it;
         if (rel > sc->max_relres) sc->max_relres = rel;
         if (!conv) sc->not_converged = 1;
     }
@@ -513,7 +498,7 @@ __device__ __forceinline__ double dyo(const double *u, int n, int iy, int i, dou
 }
 
 // sources of E_z, B_z (Eqs. EqM_N8_A, Mag_z_A); j_z (Eq. Jr plus the
-// driver), kappa = n_* / (1+psi), grad psi
+// driver), kappa = n_* / (1+psi) with the smoother's inverse diagonal, grad psi
 __device__ void phase_assemble1(const EngineArgs &A, const double *ncur, int j, int q, int m,
                                 Thr T) {
     const int n = A.N, nn = n * n;
@@ -535,7 +520,16 @@ __device__ void phase_assemble1(const EngineArgs &A, const double *ncur, int j, 
         double jzb = q == 0 ? J0[i] : (1.0 - frac) * J0[i] + frac * (J1 ? J1[i] : 0.0);
         double nv = ncur[i];
         A.jz[i] = A.G[i] / a - nv + jzb;
-        A.kap[i] = nv / a;
+        const double kap = nv / a;
+        A.kap[i] = kap;
+        const int nw = qsmg::walls(ix, iy, n);
+        if (A.precision == QS_FP32_REFINED) {
+            const float k32 = (float)kap;
+            A.k32[i] = k32;
+            A.d32[i] = 1.f / ((float)(4 + nw) + (float)A.lev_h2[0] * k32);
+        } else {
+            A.invd0[i] = 1.0 / ((double)(4 + nw) + A.lev_h2[0] * kap);
+        }
         A.dpx[i] = dxo(A.psi, n, ix, i, inv2h);
         A.dpy[i] = dyo(A.psi, n, iy, i, inv2h);
     }
@@ -641,10 +635,16 @@ __device__ void phase_push(const EngineArgs &A, double *nnext, bool base, bool l
     }
 }
 
+template <bool REF>
 __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs A) {
     extern __shared__ double smem[];
     const int bid = blockIdx.x, nblk = gridDim.x;
-    const Sync S{A.sc, (unsigned)nblk, A.spin_cycles};
+    const Sync S{A.sc, (unsigned)nblk, A.spin_cycles, A.trace, A.trace_cap};
+    if (A.trace && bid == 0 && threadIdx.x == 0) {
+        A.trace[0] = 0;
+        A.trace[1] = global_ns();
+        A.sc->trace_n = 1;
+    }
     DevScalars *sc = A.sc;
     const Thr T = grid_thr(bid, nblk);
     const bool lead = (bid == 0 && threadIdx.x == 0);
@@ -653,9 +653,9 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs 
     phase_deposit_n(A, ncur, T);
     if (!S(1)) return;
 
-    SolveView Vpsi{1, 0, {A.psi, nullptr}, {A.f_psi, nullptr}, nullptr};
-    SolveView Veb{2, 1, {A.ez, A.bz}, {A.f_ez, A.f_bz}, nullptr};
-    SolveView Vbp{2, 2, {A.bx, A.by}, {A.f_bx, A.f_by}, A.kap};
+    const SolveSpec Vpsi{1, 0, {A.psi, nullptr}, {A.f_psi, nullptr}, false};
+    const SolveSpec Veb{2, 1, {A.ez, A.bz}, {A.f_ez, A.f_bz}, false};
+    const SolveSpec Vbp{2, 2, {A.bx, A.by}, {A.f_bx, A.f_by}, true};
 
     int m = A.m_sched ? A.m_sched[0] : 1;
     int slot = 0, pk = 0;
@@ -670,15 +670,15 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs 
             const bool base = (q == 0);
             phase_psi_rhs(A, ncur, nnext, base, j, T);
             if (!S(2)) return;
-            if (!mg_solve(A, S, Vpsi, slot, bid, nblk, smem)) return;
+            if (!mg_solve<REF>(A, S, Vpsi, slot, bid, nblk, smem)) return;
             phase_moments(A, T);
             if (!S(3)) return;
             phase_assemble1(A, ncur, j, q, m, T);
             if (!S(4)) return;
-            if (!mg_solve(A, S, Veb, slot, bid, nblk, smem)) return;
+            if (!mg_solve<REF>(A, S, Veb, slot, bid, nblk, smem)) return;
             phase_assemble2(A, T);
             if (!S(5)) return;
-            if (!mg_solve(A, S, Vbp, slot, bid, nblk, smem)) return;
+            if (!mg_solve<REF>(A, S, Vbp, slot, bid, nblk, smem)) return;
             phase_push(A, nnext, base, last, j, dxi, pk, T);
             if (lead) {
                 sc->slices += 1;
@@ -714,12 +714,14 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs 
 
 }  // namespace
 
-int qs_engine_max_blocks(int device, size_t smem_bytes, int *blocks) {
+int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks) {
+    const void *fn = precision == QS_FP32_REFINED ? (const void *)slice_engine<true>
+                                                  : (const void *)slice_engine<false>;
     int per_sm = 0, sms = 0;
-    if (cudaFuncSetAttribute(slice_engine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
+        cudaSuccess)
         return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, slice_engine, QS_ENGINE_THREADS,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QS_ENGINE_THREADS,
                                                       smem_bytes) != cudaSuccess)
         return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
@@ -728,10 +730,25 @@ int qs_engine_max_blocks(int device, size_t smem_bytes, int *blocks) {
     return 0;
 }
 
+size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
+                            int tile_x, int tile_y, int nu) {
+    int lg = 0;
+    while (lg < nlev - 1 && lev_n[lg] > block_level_n) ++lg;
+    size_t b = precision == QS_FP32_REFINED ? qsmg::block_smem_bytes<float>(lev_n, nlev, lg, 2)
+                                            : qsmg::block_smem_bytes<double>(lev_n, nlev, lg, 2);
+    if (precision == QS_FP32_REFINED && tile_x > 0) {
+        const size_t t = qstile::tile_smem_bytes(tile_x, tile_y, nu);
+        if (t > b) b = t;
+    }
+    return b + 256;
+}
+
 cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_blocks,
                              size_t smem_bytes) {
     EngineArgs copy = a;
     void *args[] = {&copy};
-    return cudaLaunchCooperativeKernel((const void *)slice_engine, dim3(grid_blocks),
-                                       dim3(QS_ENGINE_THREADS), args, smem_bytes, st);
+    const void *fn = a.precision == QS_FP32_REFINED ? (const void *)slice_engine<true>
+                                                    : (const void *)slice_engine<false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid_blocks), dim3(QS_ENGINE_THREADS), args,
+                                       smem_bytes, st);
 }

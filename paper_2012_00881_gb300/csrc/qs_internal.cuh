@@ -29,13 +29,23 @@ struct DevScalars {
     int not_converged;
     double max_relres;
     unsigned long long vmax_all_bits;
+    unsigned long long trace_n;
 };
 
-// one grid level of a multigrid hierarchy
+// one grid level of a multigrid hierarchy (float64 levels, and the float32
+// levels of the refined form's inner cycles)
 struct LevelArrays {
     double *u[2];
     double *f[2];
     double *kap;
+    double *d;
+};
+struct LevelArrays32 {
+    float *u[2];   // pre-smoothed iterate (tiled down leg) / block-level result
+    float *f[2];
+    float *k;
+    float *d;
+    float *up[2];  // post-smoothed iterate of a tiled grid level
 };
 
 // Everything the slice engine reads or writes (passed by value).
@@ -60,13 +70,18 @@ struct EngineArgs {
     // level-0 fields (multigrid unknowns) and right-hand sides
     double *psi, *ez, *bz, *bx, *by;
     double *f_psi, *f_ez, *f_bz, *f_bx, *f_by;
-    double *dpx, *dpy, *jz, *kap;
+    double *dpx, *dpy, *jz, *kap, *invd0;
     // coarse levels 1..nlev-1 (scratch shared by the three solves)
     int nlev;
     int lev_n[QS_MAX_LEV];
     double lev_h2[QS_MAX_LEV];
     LevelArrays lev[QS_MAX_LEV];
     int block_level_n;  // levels with side <= this are relaxed by one block
+    // refined form: float32 inner hierarchy (level 0: correction e, residual r)
+    int precision;
+    int tile_x, tile_y;  // output tile of the staged grid levels (refined form)
+    float *e32[2], *r32[2], *k32, *d32;
+    LevelArrays32 lev32[QS_MAX_LEV];
     // outputs
     double *hist;        // [5][n_xi][N*N]
     const double *jzb;   // [n_xi][N*N]
@@ -74,6 +89,10 @@ struct EngineArgs {
     int32_t *diag_m;
     double *diag_vmax, *diag_charge;
     DevScalars *sc;
+    // optional phase trace: block 0 records (phase id, %globaltimer) after
+    // every grid barrier, up to trace_cap entries
+    int64_t *trace;
+    int trace_cap;
 };
 
 // ---------------------------------------------------------------------------
@@ -167,4 +186,6 @@ cudaError_t qs_launch_cell_sort(cudaStream_t st, const double *x, const double *
                                 int32_t *offset, int32_t *cursor, int32_t *perm);
 cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_blocks,
                              size_t smem_bytes);
-int qs_engine_max_blocks(int device, size_t smem_bytes, int *blocks);
+int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
+size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
+                            int tile_x, int tile_y, int nu);

@@ -45,7 +45,8 @@ def test_default_config_through_the_abi(lib):
     assert cfg.nx == 64 and cfg.ny == 64 and cfg.refine_k == 8 and cfg.mg_tol == 1e-10
     assert cfg.x_min == -6.0 and cfg.xi_max == 12.0 and cfg.n_xi == 128
     assert cfg.max_psi_guard_hits == -1 and cfg.sort_every == 16
-    assert cfg.pre_sweeps == 2 and cfg.post_sweeps == 2 and list(cfg.reserved) == [0] * 8
+    assert cfg.pre_sweeps == 2 and cfg.post_sweeps == 2 and cfg.coarse_block_n == 0
+    assert cfg.trace_capacity == 0 and list(cfg.reserved) == [0] * 6
 
 
 def test_status_strings(lib):

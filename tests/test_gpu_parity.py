@@ -83,9 +83,11 @@ def test_cell_sort_bit_exact(qs, n, np_):
     assert np.array_equal(perm, perm_o)
 
 
-def test_linear_driver_step_parity(qs):
-    """The 64^2, 128-slice linear workload: every field of every base slice."""
-    wl = W.workload("linear64")
+@pytest.mark.parametrize("form", ["fp64", "fp32r"])
+def test_linear_driver_step_parity(qs, form):
+    """The 64^2, 128-slice linear workload: every field of every base slice.
+    The refined form reaches the float64 solution by iterative refinement."""
+    wl = W.workload("linear64").with_(precision=form)
     r = _run_both(qs, wl)
     _check_fields(r, 1e-9)
     assert r["stats"]["slices"] == r["ref"].slices == 128
@@ -94,12 +96,14 @@ def test_linear_driver_step_parity(qs):
     assert _rel(r["got"][5], r["jzb"]) < 1e-13
 
 
-def test_nonlinear_refined_step_parity(qs):
-    """A strong driver on a small grid: adaptive sub-steps, nonlinear sources."""
+@pytest.mark.parametrize("form,cb", [("fp64", 0), ("fp32r", 0), ("fp64", 4), ("fp32r", 32)])
+def test_nonlinear_refined_step_parity(qs, form, cb):
+    """A strong driver on a small grid: adaptive sub-steps, nonlinear sources;
+    both forms, with the single-block coarse part starting at several levels."""
     wl = W.Workload(name="t", n=32, half_width=3.0, n_xi=32, xi_len=8.0, ppc=4,
                     beams=(W.BeamSpec(amplitude=20.0, sigma_x=0.5, sigma_y=0.5, sigma_z=0.6,
-                                      xi_c=1.8, n_particles=20000, seed=3),))
-    r = _run_both(qs, wl)
+                                      xi_c=1.8, n_particles=20000, seed=3),), precision=form)
+    r = _run_both(qs, wl, coarse_block_n=cb)
     assert np.array_equal(r["m"], r["ref"].m), (r["m"], r["ref"].m)
     assert r["ref"].m.max() > 2
     assert r["stats"]["slices"] == r["ref"].slices
