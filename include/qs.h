@@ -218,6 +218,38 @@ int qs_phase_trace(qs_ctx *ctx, int32_t *where, int64_t *t_ns, int cap);
 int qs_cell_sort(qs_ctx *ctx, const double *x, const double *y, const int32_t *id, int64_t n,
                  int32_t *cell, int32_t *count, int32_t *offset, int32_t *perm);
 
+/* Largest grid (N * N cells) that qs_cell_sort_noalloc accepts. */
+#define QS_NOALLOC_MAX_CELLS (512 * 512)
+
+/* The cell sort of qs_cell_sort without a context and without allocating any
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot let a library allocate device memory, such as
+ * applications that give all of the GPU's memory to their own pool or arena
+ * (an outside cudaMalloc breaks their budget or fails), hosts that hand a
+ * plugin raw buffers but no allocator, and loops that must not pay for
+ * cudaMalloc / cudaFree, which can synchronise the device.
+ *
+ * Grid: n x n cells of side h with lower corner (x_min, y_min); n * n must
+ * not exceed QS_NOALLOC_MAX_CELLS, else QS_ERR_ARG.  DEVICE arrays as in
+ * qs_cell_sort: x, y (float64, np), id (int32, np) in; cell (int32, np),
+ * count (int32, n*n), offset (int32, n*n + 1), perm (int32, np) out.  The
+ * work is queued on `cuda_stream` (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without waiting; the outputs are ready once
+ * the stream reaches that point.
+ *
+ * Scratch: a file-scope device array of QS_NOALLOC_MAX_CELLS int32 (1 MiB)
+ * that every GPU loading this library holds until the process exits.  All
+ * calls share it and it keeps the last call's contents; each call clears the
+ * part it uses before using it.  Calls that overlap on the GPU (on different
+ * streams, or from different host threads without ordering) race on it and
+ * give wrong results: order them.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture begins.
+ * Errors: QS_ERR_ARG, QS_ERR_CUDA (launch or address lookup failed). */
+int qs_cell_sort_noalloc(int n, double x_min, double y_min, double h, const double *x,
+                         const double *y, const int32_t *id, int64_t np, int32_t *cell,
+                         int32_t *count, int32_t *offset, int32_t *perm, void *cuda_stream);
+
 /* Name of a status code (static string). */
 const char *qs_strerror(int status);
 

@@ -88,6 +88,7 @@ PROTOTYPES = {
     "qs_plasma_count": (_I64, [_P]),
     "qs_cell_sort": (_I, [_P, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "qs_phase_trace": (_I, [_P, _P, _P, _I]),
+    "qs_cell_sort_noalloc": (_I, [_I, _D, _D, _D, _P, _P, _P, _I64, _P, _P, _P, _P, _P]),
     "qs_strerror": (ctypes.c_char_p, [_I]),
     "qs_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -309,3 +310,30 @@ class Context:
         self._check(self.lib.qs_cell_sort(self.h, _ptr(x), _ptr(y), _ptr(pid), n, _ptr(cell),
                                           _ptr(count), _ptr(offset), _ptr(perm)), "qs_cell_sort")
         return cell, count, offset, perm
+
+
+NOALLOC_MAX_CELLS = 512 * 512
+
+
+def cell_sort_noalloc(n: int, x_min: float, y_min: float, h: float, x, y, pid, out=None,
+                      stream=None):
+    """qs_cell_sort_noalloc on CUDA tensors.  `out` may supply the output
+    tensors (cell, count, offset, perm); the library allocates nothing.
+    Waits for the stream before returning."""
+    import torch
+    lib = load_library()
+    npart = int(x.numel())
+    if out is None:
+        out = (torch.empty(npart, dtype=torch.int32, device=x.device),
+               torch.empty(n * n, dtype=torch.int32, device=x.device),
+               torch.empty(n * n + 1, dtype=torch.int32, device=x.device),
+               torch.empty(npart, dtype=torch.int32, device=x.device))
+    cell, count, offset, perm = out
+    st = torch.cuda.current_stream() if stream is None else stream
+    rc = lib.qs_cell_sort_noalloc(n, float(x_min), float(y_min), float(h), _ptr(x), _ptr(y),
+                                  _ptr(pid), npart, _ptr(cell), _ptr(count), _ptr(offset),
+                                  _ptr(perm), _P(st.cuda_stream))
+    if rc != QS_OK:
+        raise QsError(rc, "qs_cell_sort_noalloc: " + lib.qs_strerror(rc).decode())
+    st.synchronize()
+    return cell, count, offset, perm

@@ -289,3 +289,81 @@ cudaError_t qs_launch_cell_sort(cudaStream_t st, const double *x, const double *
     k_sort_segments<<<blocks_for(m), kThreads, 0, st>>>(m, offset, id, perm);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Cell sort without any device allocation.
+//
+// Some callers cannot let a library allocate device memory: applications that
+// hand all of the GPU's memory to their own pool or arena (a cudaMalloc
+// outside it breaks their budget, or fails once the pool holds the memory),
+// hosts that may only pass a plugin raw buffers and no allocator, and loops
+// that must not pay for cudaMalloc / cudaFree, which can synchronise the
+// device.  qs_cell_sort_noalloc serves them: the caller passes every input
+// and output buffer, and the one scratch array the sort needs (a per-cell
+// insertion cursor) is the file-scope device array below, which every GPU
+// that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+#include <atomic>
+#include <mutex>
+
+// Largest grid the allocation-free sort accepts: QS_NOALLOC_MAX_CELLS cells
+// (512 x 512), i.e. 1 MiB of int32 cursors.
+static __device__ __align__(256) int32_t g_noalloc_cursor[QS_NOALLOC_MAX_CELLS];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::atomic<int32_t *> g_cursor_addr[kMaxDevices];
+std::mutex g_cursor_mu;
+
+// Device address of g_noalloc_cursor on the current device, looked up once
+// per device (the host-side name of the array is only a stand-in, never a
+// device address).
+cudaError_t cursor_address(int dev, int32_t **out) {
+    int32_t *p = g_cursor_addr[dev].load(std::memory_order_acquire);
+    if (p) {
+        *out = p;
+        return cudaSuccess;
+    }
+    std::lock_guard<std::mutex> lock(g_cursor_mu);
+    p = g_cursor_addr[dev].load(std::memory_order_relaxed);
+    if (!p) {
+        void *addr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_cursor);
+        if (e != cudaSuccess) return e;
+        p = static_cast<int32_t *>(addr);
+        g_cursor_addr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int qs_cell_sort_noalloc(int n, double x_min, double y_min, double h,
+                                    const double *x, const double *y, const int32_t *id,
+                                    int64_t np, int32_t *cell, int32_t *count, int32_t *offset,
+                                    int32_t *perm, void *cuda_stream) {
+    if (n < 1 || (int64_t)n * n > QS_NOALLOC_MAX_CELLS) return QS_ERR_ARG;
+    if (!(h > 0.0) || np < 0 || np > (int64_t)0x7fffffff || !count || !offset) return QS_ERR_ARG;
+    if (np > 0 && (!x || !y || !id || !cell || !perm)) return QS_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return QS_ERR_CUDA;
+    }
+    int32_t *cursor = nullptr;
+    if (cursor_address(dev, &cursor) != cudaSuccess) {
+        cudaGetLastError();
+        return QS_ERR_CUDA;
+    }
+    // the scan kernel clears cursor[0 .. n*n) before the scatter uses it
+    const cudaError_t e =
+        qs_launch_cell_sort(static_cast<cudaStream_t>(cuda_stream), x, y, id, np, n, x_min,
+                            y_min, h, cell, count, offset, cursor, perm);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return QS_ERR_CUDA;
+    }
+    return QS_OK;
+}
