@@ -43,7 +43,17 @@ def _args():
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--slices", type=int, default=0,
+                   help="profiling only: truncate the window to this many base slices")
     return p.parse_args()
+
+
+def _load_workload(args):
+    import workloads as W
+    wl = W.workload(args.workload)
+    if args.slices > 0:
+        wl = wl.with_(n_xi=args.slices, xi_len=wl.xi_len * args.slices / wl.n_xi)
+    return wl
 
 
 def _dist_env():
@@ -144,7 +154,7 @@ def run_native(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = W.workload(args.workload)
+    wl = _load_workload(args)
     forms = ["fp64", "fp32r"] if args.form == "both" else [args.form]
     beams_np = [W.sample_beam(b) for b in wl.beams]
     beam_bytes = sum(7 * 8 * len(b["x"]) for b in beams_np)
@@ -320,8 +330,7 @@ def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
         return
-    import workloads as W
-    wl = W.workload(args.workload)
+    wl = _load_workload(args)
     per_step = max(2.0, args.cpu_seconds / 2)
     vals, slices, secs = [], 0, 0.0
     for i in range(args.warmup + args.steps):

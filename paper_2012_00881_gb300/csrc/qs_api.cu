@@ -31,6 +31,7 @@ struct qs_ctx {
     LevelArrays32 lev32[QS_MAX_LEV] = {};
     int block_level_n = 16;
     int tile_x = 0, tile_y = 0;
+    size_t tile_offset = 0, block_offset = 0;
     double *hist = nullptr, *jzb = nullptr;
     DevScalars *sc = nullptr;
     int32_t *diag_m = nullptr, *d_sched = nullptr;
@@ -221,7 +222,8 @@ int create_impl(qs_ctx *c) {
     c->tile_y = ref ? 16 : 0;
     const int nu = g.pre_sweeps > g.post_sweeps ? g.pre_sweeps : g.post_sweeps;
     c->engine_smem = qs_engine_smem_bytes(c->lev_n, c->nlev, c->block_level_n, g.precision,
-                                          c->tile_x, c->tile_y, nu);
+                                          c->tile_x, c->tile_y, nu, &c->block_offset,
+                                          &c->tile_offset);
     if (c->engine_smem > 200 * 1024)
         return fail(c, QS_ERR_ARG, "coarse_block_n = %d needs %zu bytes of shared memory",
                     c->block_level_n, c->engine_smem);
@@ -463,6 +465,8 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
     a.block_level_n = c->block_level_n;
     a.tile_x = c->tile_x;
     a.tile_y = c->tile_y;
+    a.tile_smem_offset = (int)c->tile_offset;
+    a.block_smem_offset = (int)c->block_offset;
     a.precision = g.precision;
     for (int k = 0; k < 2; ++k) {
         a.e32[k] = c->e32[k];

@@ -20,11 +20,6 @@ namespace {
         if (!S(where)) return false; \
     } while (0)
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
 __device__ __forceinline__ double vload(const double *p) { return *(const volatile double *)p; }
 __device__ __forceinline__ unsigned long long vload(const unsigned long long *p) {
@@ -37,13 +32,26 @@ __device__ __forceinline__ int64_t global_ns() {
     return t;
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Each
+// block counts the barriers it has passed (its epoch); on arrival its thread
+// 0 adds 1 to a monotonic counter with a release reduction (no round trip)
+// and polls with acquire loads until the counter reaches epoch * nblk.
 struct Sync {
     DevScalars *sc;
     unsigned nblk;
     long long limit;
     int64_t *trace;
     int trace_cap;
+    unsigned long long *epoch;  // this block's barrier count (shared memory)
     __device__ bool operator()(int where) const {
         __shared__ int s_ok;
         __syncthreads();
@@ -52,16 +60,12 @@ struct Sync {
             if (vload(&sc->err) != 0) {
                 ok = 0;
             } else {
-                unsigned gen = ld_acquire_u32(&sc->bar_gen);
-                __threadfence();
-                unsigned arrived = atomicAdd(&sc->bar_count, 1u);
-                if (arrived == nblk - 1) {
-                    atomicExch(&sc->bar_count, 0u);
-                    __threadfence();
-                    atomicAdd(&sc->bar_gen, 1u);
-                } else {
-                    long long t0 = clock64();
-                    while (ld_acquire_u32(&sc->bar_gen) == gen) {
+                const unsigned long long target = (*epoch + 1) * nblk;
+                *epoch += 1;
+                red_release_add_u64(&sc->bar_arrive, 1ull);
+                if (ld_acquire_u64(&sc->bar_arrive) < target) {
+                    const long long t0 = clock64();
+                    while (ld_acquire_u64(&sc->bar_arrive) < target) {
                         if (vload(&sc->err) != 0) {
                             ok = 0;
                             break;
@@ -71,10 +75,8 @@ struct Sync {
                             ok = 0;
                             break;
                         }
-                        __nanosleep(32);
                     }
                 }
-                __threadfence();
             }
             s_ok = ok;
             if (trace && blockIdx.x == 0) {
@@ -175,96 +177,85 @@ __device__ void hier32(const EngineArgs &A, const SolveSpec &V, Hier<float> &H) 
 // Level-0 red-black half sweep of the float32 correction that also adds the
 // final correction into the float64 iterate: u64 += e at the points this
 // thread updates and at the points of the other colour (not written here).
-__device__ void relax_half_finalize(const Lvl<float> &L, int nc, int color, Thr R,
-                                    double *const u64[2]) {
+template <int NC>
+__device__ void relax_half_finalize(const Lvl<float> L, int color, Thr R, double *fin0,
+                                    double *fin1) {
     const int n = L.n;
     const float h2 = (float)L.h2;
-    const int npts = (n & 1) ? n * n : (n * n) / 2;
-    const int hn = n >> 1;
-    for (int pass = 0; pass < 2; ++pass) {
-        const int col = pass == 0 ? color : 1 - color;
-        for (int q = R.t0; q < npts; q += R.nt) {
-            int ix, iy;
-            if (n & 1) {
-                iy = q / n;
-                ix = q - iy * n;
-                if (((ix + iy) & 1) != col) continue;
-            } else {
-                iy = q / hn;
-                ix = 2 * (q - iy * hn) + ((iy + col) & 1);
-            }
-            const int i = iy * n + ix;
-            if (pass == 0) {
-                const float di = qsmg::inv_diag(L, i, qsmg::walls(ix, iy, n));
-                for (int c = 0; c < nc; ++c) {
-                    float *u = L.u[c];
-                    float nb = 0.f;
-                    if (ix > 0) nb += u[i - 1];
-                    if (ix < n - 1) nb += u[i + 1];
-                    if (iy > 0) nb += u[i - n];
-                    if (iy < n - 1) nb += u[i + n];
-                    const float e = (nb - h2 * L.f[c][i]) * di;
-                    u[i] = e;
-                    u64[c][i] += (double)e;
-                }
-            } else {
-                for (int c = 0; c < nc; ++c) u64[c][i] += (double)L.u[c][i];
-            }
+    float *const u0 = L.u[0];
+    float *const u1 = L.u[NC - 1];
+    const float *const f0 = L.f[0];
+    const float *const f1 = L.f[NC - 1];
+    const int npts = n * n;
+    for (qsmg::Walk w(R.t0, R.nt, n); w.q < npts; w.next()) {
+        const int ix = w.col, iy = w.row;
+        const int i = w.q;
+        if (((ix + iy) & 1) == color) {
+            const float di = L.d ? L.d[i] : qsmg::const_inv_diag<float>(qsmg::walls(ix, iy, n));
+            qsmg::gs_point<float, NC>(u0, u1, f0, f1, h2, di, n, ix, iy);
         }
+        fin0[i] += (double)u0[i];
+        if (NC > 1) fin1[i] += (double)u1[i];
     }
 }
 
 // One V-cycle on hierarchy H.  Levels of side > block_level_n are relaxed by
-// the whole grid, the rest by block 0 in shared memory.  With `fin` set (the
+// the whole grid, the rest by block 0 in shared memory.  With `fin0` set (the
 // refined form) the float32 correction is added into the float64 iterate
 // during the last level-0 phase.
-template <typename T>
-__device__ bool vcycle(const EngineArgs &A, const Sync &S, const Hier<T> &H, int nc, int bid,
-                       int nblk, void *smem, double *const *fin) {
+template <typename T, int NC>
+__device__ bool vcycle(const EngineArgs &A, const Sync &S, const Hier<T> &H, int bid, int nblk,
+                       void *smem, qsmg::CoarseInv ci, double *fin0, double *fin1) {
     const int L = H.L;
     int lg = 0;
     while (lg < L - 1 && H.lv[lg].n > A.block_level_n) ++lg;
     const Thr T0 = grid_thr(bid, nblk);
     for (int l = 0; l < lg; ++l) {
+        const Lvl<T> F = H.lv[l], C = H.lv[l + 1];
         for (int s = 0; s < A.nu1; ++s) {
-            qsmg::relax_half(H.lv[l], nc, 0, T0);
+            qsmg::relax_half<T, NC>(F, 0, T0);
             SYNC(10);
-            qsmg::relax_half(H.lv[l], nc, 1, T0);
+            qsmg::relax_half<T, NC>(F, 1, T0);
             SYNC(11);
         }
-        qsmg::restrict_res(H.lv[l], H.lv[l + 1], nc, T0);
+        qsmg::restrict_res<T, NC>(F, C, T0);
         SYNC(12);
     }
-    if (bid == 0) qsmg::block_vcycle(H, lg, nc, A.nu1, A.nu2, smem);
+    if (bid == 0) qsmg::block_vcycle<T, NC>(H, lg, A.nu1, A.nu2, smem, ci);
     SYNC(13);
     if constexpr (sizeof(T) == 4) {
-        if (fin && (lg == 0 || A.nu2 == 0)) {
+        if (fin0 && (lg == 0 || A.nu2 == 0)) {
             // no fused level-0 sweep: add the correction in a phase of its own
             for (int l = lg - 1; l >= 0; --l) {
-                qsmg::prolong_add(H.lv[l], H.lv[l + 1], nc, T0);
+                qsmg::prolong_add<T, NC>(H.lv[l], H.lv[l + 1], T0);
                 SYNC(14);
             }
             const int nn = H.lv[0].n * H.lv[0].n;
-            for (int q = T0.t0; q < nn; q += T0.nt)
-                for (int c = 0; c < nc; ++c) fin[c][q] += (double)H.lv[0].u[c][q];
+            const float *e0 = H.lv[0].u[0];
+            const float *e1 = H.lv[0].u[NC - 1];
+            for (int q = T0.t0; q < nn; q += T0.nt) {
+                fin0[q] += (double)e0[q];
+                if (NC > 1) fin1[q] += (double)e1[q];
+            }
             SYNC(17);
             return true;
         }
     }
     for (int l = lg - 1; l >= 0; --l) {
-        qsmg::prolong_add(H.lv[l], H.lv[l + 1], nc, T0);
+        const Lvl<T> F = H.lv[l], C = H.lv[l + 1];
+        qsmg::prolong_add<T, NC>(F, C, T0);
         SYNC(14);
         for (int s = 0; s < A.nu2; ++s) {
-            qsmg::relax_half(H.lv[l], nc, 0, T0);
+            qsmg::relax_half<T, NC>(F, 0, T0);
             SYNC(15);
             if constexpr (sizeof(T) == 4) {
-                if (fin && l == 0 && s == A.nu2 - 1) {
-                    relax_half_finalize(H.lv[0], nc, 1, T0, fin);
+                if (fin0 && l == 0 && s == A.nu2 - 1) {
+                    relax_half_finalize<NC>(F, 1, T0, fin0, fin1);
                     SYNC(16);
                     continue;
                 }
             }
-            qsmg::relax_half(H.lv[l], nc, 1, T0);
+            qsmg::relax_half<T, NC>(F, 1, T0);
             SYNC(16);
         }
     }
@@ -272,26 +263,33 @@ __device__ bool vcycle(const EngineArgs &A, const Sync &S, const Hier<T> &H, int
 }
 
 // Refined form: one float32 V-cycle on the correction with the grid-wide
-// levels staged tile by tile (two grid barriers per level), the coarse levels
-// on block 0 in shared memory, and the correction added into the float64
-// iterate `fin` by the last level-0 phase.
-__device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<float> &H, int nc,
-                              int bid, int nblk, void *smem, double *const *fin) {
+// levels staged tile by tile (one grid barrier per level and leg); every
+// block then solves the coarse levels itself in shared memory (no barrier),
+// and the correction is added into the float64 iterate by the last level-0
+// phase.
+template <int NC>
+__device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<float> &H, int bid,
+                              int nblk, void *smem, qsmg::CoarseInv ci, double *fin0,
+                              double *fin1) {
     const int L = H.L;
     int lg = 0;
     while (lg < L - 1 && H.lv[lg].n > A.block_level_n) ++lg;
-    if (lg == 0) return vcycle<float>(A, S, H, nc, bid, nblk, smem, fin);
-    float *sm = (float *)smem;
+    if (lg == 0) return vcycle<float, NC>(A, S, H, bid, nblk, smem, ci, fin0, fin1);
+    // shared memory: the coarse part's levels first, the staged tile after them
+    float *sm = (float *)((char *)smem + A.tile_smem_offset);
     for (int l = 0; l < lg; ++l) {
-        qstile::down_level(H.lv[l], H.lv[l + 1], nc, A.nu1, A.tile_x, A.tile_y, sm, bid, nblk);
+        qstile::down_level<NC>(H.lv[l], H.lv[l + 1], A.nu1, A.tile_x, A.tile_y, sm, bid, nblk);
         SYNC(30);
     }
-    if (bid == 0) qsmg::block_vcycle(H, lg, nc, A.nu1, A.nu2, smem);
-    SYNC(31);
+    qsmg::block_vcycle<float, NC>(H, lg, A.nu1, A.nu2, smem, ci, false,
+                                  qsmg::Marks{A.trace, &A.sc->trace_n, A.trace_cap});
+    const int mg2 = H.lv[lg].n * H.lv[lg].n;
     for (int l = lg - 1; l >= 0; --l) {
-        float *const *cu = (l + 1 == lg) ? H.lv[lg].u : A.lev32[l + 1].up;
-        qstile::up_level(H.lv[l], cu, H.lv[l + 1].n, nc, A.nu2, A.tile_x, A.tile_y, sm, bid, nblk,
-                         A.lev32[l].up, l == 0 ? fin : nullptr);
+        const float *cu0 = (l + 1 == lg) ? (const float *)smem : A.lev32[l + 1].up[0];
+        const float *cu1 = (l + 1 == lg) ? (const float *)smem + 2 * mg2 : A.lev32[l + 1].up[1];
+        qstile::up_level<NC>(H.lv[l], cu0, cu1, H.lv[l + 1].n, A.nu2, A.tile_x, A.tile_y, sm,
+                             bid, nblk, A.lev32[l].up[0], A.lev32[l].up[1],
+                             l == 0 ? fin0 : nullptr, l == 0 ? fin1 : nullptr);
         SYNC(32);
     }
     return true;
@@ -301,26 +299,37 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
 // into out[c] and out[2 + c].  For the refined form the residual also becomes
 // the float32 right-hand side of the next inner cycle, whose correction
 // starts at zero.
+template <int NC>
 __device__ void residual_norm(const EngineArgs &A, const SolveSpec &V, double *out, Thr T,
                               bool to32) {
     const int n = A.N;
     const double inv_h2 = 1.0 / A.lev_h2[0];
-    const double *kap = V.screened ? A.kap : nullptr;
+    const double *const kap = V.screened ? A.kap : nullptr;
+    const double *const u0 = V.u[0];
+    const double *const u1 = V.u[NC - 1];
+    const double *const f0 = V.f[0];
+    const double *const f1 = V.f[NC - 1];
+    float *const r0 = A.r32[0];
+    float *const r1 = A.r32[NC - 1];
+    float *const e0 = A.e32[0];
+    float *const e1 = A.e32[NC - 1];
     double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int k = T.t0; k < n * n; k += T.nt) {
-        const int iy = k / n, ix = k - iy * n;
-        for (int c = 0; c < V.nc; ++c) {
-            const double r = V.f[c][k] - qsmg::apply_op<double>(V.u[c], kap, n, inv_h2, ix, iy);
-            const double u = V.u[c][k];
+    for (qsmg::Walk w(T.t0, T.nt, n); w.q < n * n; w.next()) {
+        const int k = w.q;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const double *u = c ? u1 : u0;
+            const double r = (c ? f1 : f0)[k] - qsmg::apply_op<double>(u, kap, n, inv_h2, w.col, w.row);
             s[c] += r * r;
-            s[2 + c] += u * u;
+            s[2 + c] += u[k] * u[k];
             if (to32) {
-                A.r32[c][k] = (float)r;
-                A.e32[c][k] = 0.f;
+                (c ? r1 : r0)[k] = (float)r;
+                (c ? e1 : e0)[k] = 0.f;
             }
         }
     }
-    for (int c = 0; c < V.nc; ++c) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
         double t = block_sum(s[c]);
         if (threadIdx.x == 0) atomicAdd(out + c, t);
         t = block_sum(s[2 + c]);
@@ -336,8 +345,18 @@ __device__ void residual_norm(const EngineArgs &A, const SolveSpec &V, double *o
 // V-cycle on the correction, float64 update (iterative refinement).
 template <bool REF>
 __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V, int &slot,
-                         int bid, int nblk, void *smem) {
+                         int bid, int nblk, void *smem_base, int *inv_ready) {
     DevScalars *sc = A.sc;
+    // shared memory: [coarsest inverses][coarse levels + work][staged tile]
+    void *smem = (char *)smem_base + A.block_smem_offset;
+    const int mc = A.lev_n[A.nlev - 1] * A.lev_n[A.nlev - 1];
+    const qsmg::CoarseInv ci{(double *)smem_base + (V.screened ? mc * mc : 0),
+                             inv_ready + (V.screened ? 1 : 0)};
+    if (V.screened) {  // kappa changed: the screened inverse must be rebuilt
+        __syncthreads();
+        if (threadIdx.x == 0) inv_ready[1] = 0;
+        __syncthreads();
+    }
     double fn[2] = {0.0, 0.0};
     bool any_zero = false, all_zero = true;
     for (int c = 0; c < V.nc; ++c) {
@@ -364,7 +383,8 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
     const double fl = 1e-13 / A.lev_h2[0];
     for (;;) {
         if (REF || it > 0) {
-            residual_norm(A, V, sc->rnorm[slot & 3], T, REF);
+            if (V.nc == 1) residual_norm<1>(A, V, sc->rnorm[slot & 3], T, REF);
+            else residual_norm<2>(A, V, sc->rnorm[slot & 3], T, REF);
             if (bid == 0 && threadIdx.x == 0)
                 for (int e = 0; e < 4; ++e) sc->rnorm[(slot + 2) & 3][e] = 0.0;
             SYNC(21);
@@ -384,11 +404,15 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
         }
         bool ok;
         if (REF) {
-            double *fin[2] = {V.u[0], V.u[1]};
-            ok = A.tile_x > 0 ? vcycle_staged(A, S, H32, V.nc, bid, nblk, smem, fin)
-                              : vcycle<float>(A, S, H32, V.nc, bid, nblk, smem, fin);
+            if (V.nc == 1)
+                ok = A.tile_x > 0 ? vcycle_staged<1>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[0])
+                                  : vcycle<float, 1>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[0]);
+            else
+                ok = A.tile_x > 0 ? vcycle_staged<2>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[1])
+                                  : vcycle<float, 2>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[1]);
         } else {
-            ok = vcycle<double>(A, S, H64, V.nc, bid, nblk, smem, nullptr);
+            ok = V.nc == 1 ? vcycle<double, 1>(A, S, H64, bid, nblk, smem, ci, nullptr, nullptr)
+                           : vcycle<double, 2>(A, S, H64, bid, nblk, smem, ci, nullptr, nullptr);
         }
         if (!ok) return false;
         ++it;
@@ -639,7 +663,14 @@ template <bool REF>
 __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs A) {
     extern __shared__ double smem[];
     const int bid = blockIdx.x, nblk = gridDim.x;
-    const Sync S{A.sc, (unsigned)nblk, A.spin_cycles, A.trace, A.trace_cap};
+    __shared__ unsigned long long s_epoch;
+    __shared__ int s_inv_ready[2];
+    if (threadIdx.x == 0) {
+        s_epoch = 0ull;
+        s_inv_ready[0] = s_inv_ready[1] = 0;
+    }
+    __syncthreads();
+    const Sync S{A.sc, (unsigned)nblk, A.spin_cycles, A.trace, A.trace_cap, &s_epoch};
     if (A.trace && bid == 0 && threadIdx.x == 0) {
         A.trace[0] = 0;
         A.trace[1] = global_ns();
@@ -670,15 +701,15 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs 
             const bool base = (q == 0);
             phase_psi_rhs(A, ncur, nnext, base, j, T);
             if (!S(2)) return;
-            if (!mg_solve<REF>(A, S, Vpsi, slot, bid, nblk, smem)) return;
+            if (!mg_solve<REF>(A, S, Vpsi, slot, bid, nblk, smem, s_inv_ready)) return;
             phase_moments(A, T);
             if (!S(3)) return;
             phase_assemble1(A, ncur, j, q, m, T);
             if (!S(4)) return;
-            if (!mg_solve<REF>(A, S, Veb, slot, bid, nblk, smem)) return;
+            if (!mg_solve<REF>(A, S, Veb, slot, bid, nblk, smem, s_inv_ready)) return;
             phase_assemble2(A, T);
             if (!S(5)) return;
-            if (!mg_solve<REF>(A, S, Vbp, slot, bid, nblk, smem)) return;
+            if (!mg_solve<REF>(A, S, Vbp, slot, bid, nblk, smem, s_inv_ready)) return;
             phase_push(A, nnext, base, last, j, dxi, pk, T);
             if (lead) {
                 sc->slices += 1;
@@ -731,16 +762,20 @@ int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *bloc
 }
 
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
-                            int tile_x, int tile_y, int nu) {
+                            int tile_x, int tile_y, int nu, size_t *block_offset,
+                            size_t *tile_offset) {
     int lg = 0;
     while (lg < nlev - 1 && lev_n[lg] > block_level_n) ++lg;
+    const size_t inv = (qsmg::coarse_inv_bytes(lev_n, nlev) + 255) & ~(size_t)255;
     size_t b = precision == QS_FP32_REFINED ? qsmg::block_smem_bytes<float>(lev_n, nlev, lg, 2)
                                             : qsmg::block_smem_bytes<double>(lev_n, nlev, lg, 2);
-    if (precision == QS_FP32_REFINED && tile_x > 0) {
-        const size_t t = qstile::tile_smem_bytes(tile_x, tile_y, nu);
-        if (t > b) b = t;
-    }
-    return b + 256;
+    b = (b + 255) & ~(size_t)255;
+    if (block_offset) *block_offset = inv;
+    if (tile_offset) *tile_offset = b;  // relative to the block part
+    size_t total = inv + b;
+    if (precision == QS_FP32_REFINED && tile_x > 0)
+        total += qstile::tile_smem_bytes(tile_x, tile_y, nu);
+    return total + 256;
 }
 
 cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_blocks,

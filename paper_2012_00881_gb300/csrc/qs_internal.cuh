@@ -14,8 +14,7 @@
 // memory; reset before every launch)
 // ---------------------------------------------------------------------------
 struct DevScalars {
-    unsigned int bar_count;        // grid barrier: arrivals
-    unsigned int bar_gen;          // grid barrier: generation
+    unsigned long long bar_arrive; // grid barrier: total arrivals (monotonic)
     int err;                       // first error status seen on the device
     int err_where;                 // phase id of a timeout
     double rnorm[4][4];            // ||r||^2 (comps 0,1) and ||u||^2 (2,3), ring of 4
@@ -80,6 +79,8 @@ struct EngineArgs {
     // refined form: float32 inner hierarchy (level 0: correction e, residual r)
     int precision;
     int tile_x, tile_y;  // output tile of the staged grid levels (refined form)
+    int block_smem_offset; // byte offset of the coarse part in shared memory
+    int tile_smem_offset;  // byte offset of the staged tile after the coarse part
     float *e32[2], *r32[2], *k32, *d32;
     LevelArrays32 lev32[QS_MAX_LEV];
     // outputs
@@ -188,4 +189,5 @@ cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_bloc
                              size_t smem_bytes);
 int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
-                            int tile_x, int tile_y, int nu);
+                            int tile_x, int tile_y, int nu, size_t *block_offset,
+                            size_t *tile_offset);

@@ -7,7 +7,8 @@
 // average restriction of the residual (and of kappa), bilinear cell-centred
 // prolongation, rediscretised coarse operators, dense elimination on the
 // coarsest level.  Templated on the storage type (double, or float for the
-// inner cycles of the refined form); the coarsest solve is always float64.
+// inner cycles of the refined form) and on the number of components solved
+// together (1 or 2, sharing the operator); the coarsest solve is float64.
 #pragma once
 
 #include "qs_internal.cuh"
@@ -39,12 +40,32 @@ __device__ __forceinline__ int walls(int ix, int iy, int n) {
 }
 
 template <typename T>
-__device__ __forceinline__ T inv_diag(const Lvl<T> &L, int i, int nw) {
-    if (L.d) return L.d[i];
+__device__ __forceinline__ T const_inv_diag(int nw) {
     return nw == 0 ? T(0.25) : (nw == 1 ? T(0.2) : (nw == 2 ? T(1.0 / 6.0) : T(1) / T(4 + nw)));
 }
 
-// (lap_h - kappa) u at (ix, iy), computed in T
+// Walk q = t0, t0 + nt, ... over a row-major index space with `w` columns,
+// keeping (row, col) without a division per step.
+struct Walk {
+    int q, row, col, nt, drow, dcol, w;
+    __device__ __forceinline__ Walk(int t0, int nt_, int w_) : q(t0), nt(nt_), w(w_) {
+        row = t0 / w;
+        col = t0 - row * w;
+        drow = nt / w;
+        dcol = nt - drow * w;
+    }
+    __device__ __forceinline__ void next() {
+        q += nt;
+        row += drow;
+        col += dcol;
+        if (col >= w) {
+            col -= w;
+            ++row;
+        }
+    }
+};
+
+// (lap_h - kappa) u at (ix, iy) of an n x n array, computed in T
 template <typename T>
 __device__ __forceinline__ T apply_op(const T *u, const T *k, int n, T inv_h2, int ix, int iy) {
     const int i = iy * n + ix;
@@ -59,136 +80,181 @@ __device__ __forceinline__ T apply_op(const T *u, const T *k, int n, T inv_h2, i
     return r;
 }
 
+template <typename T, int NC>
+__device__ __forceinline__ void gs_point(T *const u0, T *const u1, const T *const f0,
+                                         const T *const f1, T h2, T di, int n, int ix, int iy) {
+    const int i = iy * n + ix;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        T *u = c ? u1 : u0;
+        T nb = T(0);
+        if (ix > 0) nb += u[i - 1];
+        if (ix < n - 1) nb += u[i + 1];
+        if (iy > 0) nb += u[i - n];
+        if (iy < n - 1) nb += u[i + n];
+        u[i] = (nb - h2 * (c ? f1 : f0)[i]) * di;
+    }
+}
+
 // one red-black half sweep of `color` on every component
-template <typename T>
-__device__ void relax_half(const Lvl<T> &L, int nc, int color, Thr R) {
+template <typename T, int NC>
+__device__ void relax_half(const Lvl<T> L, int color, Thr R) {
     const int n = L.n;
     const T h2 = T(L.h2);
-    const int npts = (n & 1) ? n * n : (n * n) / 2;
-    const int hn = n >> 1;
-    for (int q = R.t0; q < npts; q += R.nt) {
-        int ix, iy;
-        if (n & 1) {
-            iy = q / n;
-            ix = q - iy * n;
+    T *const u0 = L.u[0];
+    T *const u1 = L.u[NC - 1];
+    const T *const f0 = L.f[0];
+    const T *const f1 = L.f[NC - 1];
+    const T *const dd = L.d;
+    if (n & 1) {
+        for (Walk w(R.t0, R.nt, n); w.q < n * n; w.next()) {
+            const int ix = w.col, iy = w.row;
             if (((ix + iy) & 1) != color) continue;
-        } else {
-            iy = q / hn;
-            ix = 2 * (q - iy * hn) + ((iy + color) & 1);
+            const T di = dd ? dd[iy * n + ix] : const_inv_diag<T>(walls(ix, iy, n));
+            gs_point<T, NC>(u0, u1, f0, f1, h2, di, n, ix, iy);
         }
-        const int i = iy * n + ix;
-        const T di = inv_diag(L, i, walls(ix, iy, n));
-        for (int c = 0; c < nc; ++c) {
-            T *u = L.u[c];
-            T nb = T(0);
-            if (ix > 0) nb += u[i - 1];
-            if (ix < n - 1) nb += u[i + 1];
-            if (iy > 0) nb += u[i - n];
-            if (iy < n - 1) nb += u[i + n];
-            u[i] = (nb - h2 * L.f[c][i]) * di;
-        }
+        return;
+    }
+    const int hn = n >> 1;
+    for (Walk w(R.t0, R.nt, hn); w.q < n * hn; w.next()) {
+        const int iy = w.row;
+        const int ix = 2 * w.col + ((iy + color) & 1);
+        const T di = dd ? dd[iy * n + ix] : const_inv_diag<T>(walls(ix, iy, n));
+        gs_point<T, NC>(u0, u1, f0, f1, h2, di, n, ix, iy);
     }
 }
 
 // C.f = 4-cell average of the residual of F; C.u = 0; screened levels also
 // get C.k (4-cell average of F.k) and C.d
-template <typename T>
-__device__ void restrict_res(const Lvl<T> &F, const Lvl<T> &C, int nc, Thr R) {
+template <typename T, int NC>
+__device__ void restrict_res(const Lvl<T> F, const Lvl<T> C, Thr R) {
     const int n = F.n, m = C.n;
     const T inv_h2 = T(1.0 / F.h2);
-    for (int q = R.t0; q < m * m; q += R.nt) {
-        const int J = q / m, I = q - J * m;
+    const T *const k = F.k;
+    const T ch2 = T(C.h2);
+    for (Walk w(R.t0, R.nt, m); w.q < m * m; w.next()) {
+        const int I = w.col, J = w.row;
         const int i0 = (2 * J) * n + 2 * I;
-        for (int c = 0; c < nc; ++c) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
             const T *u = F.u[c];
             const T *f = F.f[c];
-            T s = f[i0] - apply_op(u, (const T *)F.k, n, inv_h2, 2 * I, 2 * J);
-            s += f[i0 + 1] - apply_op(u, (const T *)F.k, n, inv_h2, 2 * I + 1, 2 * J);
-            s += f[i0 + n] - apply_op(u, (const T *)F.k, n, inv_h2, 2 * I, 2 * J + 1);
-            s += f[i0 + n + 1] - apply_op(u, (const T *)F.k, n, inv_h2, 2 * I + 1, 2 * J + 1);
-            C.f[c][q] = T(0.25) * s;
-            C.u[c][q] = T(0);
+            T s = f[i0] - apply_op(u, k, n, inv_h2, 2 * I, 2 * J);
+            s += f[i0 + 1] - apply_op(u, k, n, inv_h2, 2 * I + 1, 2 * J);
+            s += f[i0 + n] - apply_op(u, k, n, inv_h2, 2 * I, 2 * J + 1);
+            s += f[i0 + n + 1] - apply_op(u, k, n, inv_h2, 2 * I + 1, 2 * J + 1);
+            C.f[c][w.q] = T(0.25) * s;
+            C.u[c][w.q] = T(0);
         }
-        if (F.k) {
-            const T kk = T(0.25) * (F.k[i0] + F.k[i0 + 1] + F.k[i0 + n] + F.k[i0 + n + 1]);
-            C.k[q] = kk;
-            C.d[q] = T(1) / (T(4 + walls(I, J, m)) + T(C.h2) * kk);
+        if (k) {
+            const T kk = T(0.25) * (k[i0] + k[i0 + 1] + k[i0 + n] + k[i0 + n + 1]);
+            C.k[w.q] = kk;
+            C.d[w.q] = T(1) / (T(4 + walls(I, J, m)) + ch2 * kk);
         }
     }
 }
 
-// F.u += bilinear interpolation of C.u (odd ghosts on the coarse level)
+// bilinear cell-centred interpolation of the coarse array uc (side m, odd
+// ghosts) at fine cell (ix, iy)
 template <typename T>
-__device__ void prolong_add(const Lvl<T> &F, const Lvl<T> &C, int nc, Thr R) {
+__device__ __forceinline__ T bilinear(const T *uc, int m, int ix, int iy) {
+    const int I = ix >> 1, J = iy >> 1;
+    const int I2 = I + ((ix & 1) ? 1 : -1);
+    const int J2 = J + ((iy & 1) ? 1 : -1);
+    const bool xin = (I2 >= 0 && I2 < m), yin = (J2 >= 0 && J2 < m);
+    const T v00 = uc[J * m + I];
+    const T v10 = xin ? uc[J * m + I2] : -v00;
+    const T v01 = yin ? uc[J2 * m + I] : -v00;
+    T v11;
+    if (xin && yin) v11 = uc[J2 * m + I2];
+    else if (xin) v11 = -uc[J * m + I2];
+    else if (yin) v11 = -uc[J2 * m + I];
+    else v11 = v00;
+    return (T(9) * v00 + T(3) * v10 + T(3) * v01 + v11) * T(0.0625);
+}
+
+// F.u += bilinear interpolation of C.u
+template <typename T, int NC>
+__device__ void prolong_add(const Lvl<T> F, const Lvl<T> C, Thr R) {
     const int n = F.n, m = C.n;
-    for (int q = R.t0; q < n * n; q += R.nt) {
-        const int iy = q / n, ix = q - iy * n;
-        const int I = ix >> 1, J = iy >> 1;
-        const int I2 = I + ((ix & 1) ? 1 : -1);
-        const int J2 = J + ((iy & 1) ? 1 : -1);
-        const bool xin = (I2 >= 0 && I2 < m), yin = (J2 >= 0 && J2 < m);
-        for (int c = 0; c < nc; ++c) {
-            const T *uc = C.u[c];
-            const T v00 = uc[J * m + I];
-            const T v10 = xin ? uc[J * m + I2] : -v00;
-            const T v01 = yin ? uc[J2 * m + I] : -v00;
-            T v11;
-            if (xin && yin) v11 = uc[J2 * m + I2];
-            else if (xin) v11 = -uc[J * m + I2];
-            else if (yin) v11 = -uc[J2 * m + I];
-            else v11 = v00;
-            F.u[c][q] += (T(9) * v00 + T(3) * v10 + T(3) * v01 + v11) * T(0.0625);
-        }
+    for (Walk w(R.t0, R.nt, n); w.q < n * n; w.next()) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) F.u[c][w.q] += bilinear(C.u[c], m, w.col, w.row);
     }
 }
 
-// Dense float64 elimination of -(lap_h - kappa) on the coarsest level by the
-// calling block (no pivoting: the matrix is symmetric positive definite).
-// `mat` needs n^2 * (n^2 + 3) doubles.
-template <typename T>
-__device__ void coarse_solve(const Lvl<T> &L, int nc, double *mat) {
-    const int n = L.n, m = n * n, ld = m + 2;
-    const double inv_h2 = 1.0 / L.h2;
-    double *fac = mat + m * ld;
-    for (int e = threadIdx.x; e < m * ld; e += blockDim.x) mat[e] = 0.0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        const int iy = i / n, ix = i - iy * n;
-        mat[i * ld + i] = (4.0 + walls(ix, iy, n)) * inv_h2 + (L.k ? (double)L.k[i] : 0.0);
-        if (ix > 0) mat[i * ld + i - 1] = -inv_h2;
-        if (ix < n - 1) mat[i * ld + i + 1] = -inv_h2;
-        if (iy > 0) mat[i * ld + i - n] = -inv_h2;
-        if (iy < n - 1) mat[i * ld + i + n] = -inv_h2;
-        for (int c = 0; c < nc; ++c) mat[i * ld + m + c] = -(double)L.f[c][i];
-    }
-    __syncthreads();
-    const int ncol = m + nc;
-    for (int k = 0; k < m - 1; ++k) {
-        const double inv_piv = 1.0 / mat[k * ld + k];
-        for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) fac[i] = mat[i * ld + k] * inv_piv;
-        __syncthreads();
-        const int rows = m - k - 1, cols = ncol - k;
-        for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
-            const int i = k + 1 + e / cols, j = k + e % cols;
-            mat[i * ld + j] -= fac[i] * mat[k * ld + j];
+// Inverse of -(lap_h - kappa) on the coarsest level (float64, row-major m x m
+// with m = n^2), kept in the block's shared memory.  `ready` (shared) says
+// whether `inv` holds the inverse of the current operator; the Poisson
+// operator never changes, the screened one changes with kappa at each solve.
+struct CoarseInv {
+    double *inv;
+    int *ready;
+};
+
+// Solve on the coarsest level by the calling block: x = inv * f with the
+// float64 inverse, computed here by Gauss-Jordan elimination (no pivoting:
+// the matrix is symmetric positive definite) when not ready.  `work` needs
+// m * (2m + 1) doubles.
+template <typename T, int NC>
+__device__ void coarse_solve(const Lvl<T> L, double *work, CoarseInv ci) {
+    const int n = L.n, m = n * n, W = 2 * m;
+    if (!*ci.ready) {
+        const double inv_h2 = 1.0 / L.h2;
+        double *fac = work + m * W;
+        for (int e = threadIdx.x; e < m * W; e += blockDim.x) {
+            const int i = e / W, j = e - i * W;
+            work[e] = (j == m + i) ? 1.0 : 0.0;
         }
         __syncthreads();
-    }
-    if ((int)threadIdx.x < nc) {  // back substitution; x overwrites column m + c
-        const int c = threadIdx.x;
-        for (int i = m - 1; i >= 0; --i) {
-            double s = mat[i * ld + m + c];
-            for (int j = i + 1; j < m; ++j) s -= mat[i * ld + j] * mat[j * ld + m + c];
-            mat[i * ld + m + c] = s / mat[i * ld + i];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const int iy = i / n, ix = i - iy * n;
+            work[i * W + i] = (4.0 + walls(ix, iy, n)) * inv_h2 + (L.k ? (double)L.k[i] : 0.0);
+            if (ix > 0) work[i * W + i - 1] = -inv_h2;
+            if (ix < n - 1) work[i * W + i + 1] = -inv_h2;
+            if (iy > 0) work[i * W + i - n] = -inv_h2;
+            if (iy < n - 1) work[i * W + i + n] = -inv_h2;
         }
+        __syncthreads();
+        for (int k = 0; k < m; ++k) {
+            const double inv_piv = 1.0 / work[k * W + k];
+            for (int i = threadIdx.x; i < m; i += blockDim.x)
+                fac[i] = (i == k) ? 0.0 : work[i * W + k] * inv_piv;
+            __syncthreads();
+            for (int e = threadIdx.x; e < m * (W - k); e += blockDim.x) {
+                const int i = e / (W - k), j = k + (e - i * (W - k));
+                if (i != k) work[i * W + j] -= fac[i] * work[k * W + j];
+            }
+            __syncthreads();
+            for (int j = k + threadIdx.x; j < W; j += blockDim.x) work[k * W + j] *= inv_piv;
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = e / m, j = e - i * m;
+            ci.inv[e] = work[i * W + m + j];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *ci.ready = 1;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x)
-        for (int c = 0; c < nc; ++c) L.u[c][i] = (T)mat[i * ld + m + c];
+    // -(lap - kappa) u = -f  =>  u = inv * (-f)
+    for (int e = threadIdx.x; e < NC * m; e += blockDim.x) {
+        const int c = e / m, i = e - c * m;
+        const T *f = L.f[c];
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s -= ci.inv[i * m + j] * (double)f[j];
+        work[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NC * m; e += blockDim.x) {
+        const int c = e / m, i = e - c * m;
+        L.u[c][i] = (T)work[e];
+    }
     __syncthreads();
 }
 
-// Shared-memory bytes that block_vcycle needs from level lg down.
+// Shared-memory bytes that block_vcycle needs from level lg down (levels and
+// the coarse-solve work area; the CoarseInv storage is separate).
 template <typename T>
 __host__ __device__ inline size_t block_smem_bytes(const int *lev_n, int L, int lg, int nc_max) {
     size_t pts = 0;
@@ -196,18 +262,50 @@ __host__ __device__ inline size_t block_smem_bytes(const int *lev_n, int L, int 
     const int mc = lev_n[L - 1] * lev_n[L - 1];
     size_t b = pts * (2 * nc_max + 2) * sizeof(T);
     b = (b + 15) & ~(size_t)15;
-    return b + (size_t)mc * (mc + 3) * sizeof(double);
+    return b + (size_t)mc * (2 * mc + 1) * sizeof(double);
+}
+
+// Bytes of the two coarsest-level inverses (Poisson, screened).
+__host__ __device__ inline size_t coarse_inv_bytes(const int *lev_n, int L) {
+    const size_t mc = (size_t)lev_n[L - 1] * lev_n[L - 1];
+    return 2 * mc * mc * sizeof(double);
 }
 
 // The rest of a V-cycle from level lg down, entirely in the calling block's
 // shared memory.  Level lg's right-hand side (and kappa) come from global
 // memory; its initial iterate is zero unless lg == 0 (then the global u is
 // the warm start).  Level lg's result is written back to global memory.
-template <typename T>
-__device__ void block_vcycle(const Hier<T> &H, int lg, int nc, int nu1, int nu2, void *smem) {
+//
+// With writeback == false the result stays in shared memory only: it is
+// component c of level lg at ((T *)smem) + 2 * c * n_lg^2 (every block can
+// then run this part redundantly and read its own copy).
+// Optional sub-phase timestamps (block 0, thread 0): trace[2k] = id,
+// trace[2k+1] = %globaltimer; *count is the next free entry.
+struct Marks {
+    int64_t *trace;
+    unsigned long long *count;
+    int cap;
+    __device__ __forceinline__ void operator()(int id) const {
+        if (!trace || blockIdx.x != 0 || threadIdx.x != 0) return;
+        const unsigned long long k = *count;
+        if (k < (unsigned long long)cap) {
+            int64_t t;
+            asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+            trace[2 * k] = id;
+            trace[2 * k + 1] = t;
+            *count = k + 1;
+        }
+    }
+};
+
+template <typename T, int NC>
+__device__ void block_vcycle(const Hier<T> &H, int lg, int nu1, int nu2, void *smem,
+                             CoarseInv ci, bool writeback = true,
+                             Marks mark = Marks{nullptr, nullptr, 0}) {
     const int L = H.L;
     Lvl<T> S[QS_MAX_LEV];
     T *p = (T *)smem;
+    const bool scr = H.lv[lg].k != nullptr;
     for (int l = lg; l < L; ++l) {
         const int m = H.lv[l].n * H.lv[l].n;
         S[l].n = H.lv[l].n;
@@ -218,56 +316,62 @@ __device__ void block_vcycle(const Hier<T> &H, int lg, int nc, int nu1, int nu2,
             S[l].f[c] = p;
             p += m;
         }
-        if (H.lv[lg].k) {
-            S[l].k = p;
-            p += m;
-            S[l].d = p;
-            p += m;
-        } else {
-            S[l].k = S[l].d = nullptr;
-            p += 2 * m;
-        }
+        S[l].k = scr ? p : nullptr;
+        S[l].d = scr ? p + m : nullptr;
+        p += 2 * m;
     }
     size_t off = ((size_t)((char *)p - (char *)smem) + 15) & ~(size_t)15;
     double *mat = (double *)((char *)smem + off);
-    const Lvl<T> &G = H.lv[lg];
+    const Lvl<T> G = H.lv[lg];
+    const Lvl<T> S0 = S[lg];
     const int m0 = G.n * G.n;
     for (int i = threadIdx.x; i < m0; i += blockDim.x) {
-        for (int c = 0; c < nc; ++c) {
-            S[lg].u[c][i] = (lg == 0) ? G.u[c][i] : T(0);
-            S[lg].f[c][i] = G.f[c][i];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            S0.u[c][i] = (lg == 0) ? G.u[c][i] : T(0);
+            S0.f[c][i] = G.f[c][i];
         }
-        if (G.k) {
-            S[lg].k[i] = G.k[i];
-            S[lg].d[i] = G.d[i];
+        if (scr) {
+            S0.k[i] = G.k[i];
+            S0.d[i] = G.d[i];
         }
     }
     __syncthreads();
+    mark(40);
     const Thr B{(int)threadIdx.x, (int)blockDim.x};
     for (int l = lg; l < L - 1; ++l) {
+        const Lvl<T> Sl = S[l], Sc = S[l + 1];
         for (int s = 0; s < nu1; ++s) {
-            relax_half(S[l], nc, 0, B);
+            relax_half<T, NC>(Sl, 0, B);
             __syncthreads();
-            relax_half(S[l], nc, 1, B);
+            relax_half<T, NC>(Sl, 1, B);
             __syncthreads();
         }
-        restrict_res(S[l], S[l + 1], nc, B);
+        restrict_res<T, NC>(Sl, Sc, B);
         __syncthreads();
+        mark(41 + l - lg);
     }
-    coarse_solve(S[L - 1], nc, mat);
+    coarse_solve<T, NC>(S[L - 1], mat, ci);
+    mark(50);
     for (int l = L - 2; l >= lg; --l) {
-        prolong_add(S[l], S[l + 1], nc, B);
+        const Lvl<T> Sl = S[l], Sc = S[l + 1];
+        prolong_add<T, NC>(Sl, Sc, B);
         __syncthreads();
         for (int s = 0; s < nu2; ++s) {
-            relax_half(S[l], nc, 0, B);
+            relax_half<T, NC>(Sl, 0, B);
             __syncthreads();
-            relax_half(S[l], nc, 1, B);
+            relax_half<T, NC>(Sl, 1, B);
             __syncthreads();
         }
+        mark(51 + l - lg);
     }
-    for (int i = threadIdx.x; i < m0; i += blockDim.x)
-        for (int c = 0; c < nc; ++c) G.u[c][i] = S[lg].u[c][i];
-    __syncthreads();
+    if (writeback) {
+        for (int i = threadIdx.x; i < m0; i += blockDim.x) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) G.u[c][i] = S0.u[c][i];
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace qsmg
