@@ -38,7 +38,7 @@ def _args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--form", default="fp64", choices=["fp64", "fp32r", "both"])
+    p.add_argument("--form", default="both", choices=["fp64", "fp32r", "both"])
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target CPU time of the oracle baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -48,8 +48,13 @@ def _args():
     return p.parse_args()
 
 
+SCAN = "scan48"
+
+
 def _load_workload(args):
     import workloads as W
+    if args.workload == SCAN:
+        return None
     wl = W.workload(args.workload)
     if args.slices > 0:
         wl = wl.with_(n_xi=args.slices, xi_len=wl.xi_len * args.slices / wl.n_xi)
@@ -70,6 +75,45 @@ def _workload_desc(wl):
             f"{wl.n_xi} base xi-slices over {wl.xi_len:g}, {wl.ppc} ppc "
             f"({wl.n_plasma} plasma macroparticles), beams [{beams}], refine_k={wl.refine_k}, "
             f"mg_tol={wl.mg_tol:g}, dt={wl.dt:g}")
+
+
+# ---------------------------------------------------------------- ncu traffic
+ENGINE_SOURCES = ("qs_engine.cu", "qs_mg.cuh", "qs_tile.cuh", "qs_internal.cuh")
+
+
+def engine_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ENGINE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2012_00881_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str, form: str):
+    """DRAM bytes per launch from the committed ncu summary of this kernel and
+    workload, if it was captured on the current engine source; else None."""
+    d = os.path.join(ROOT, "profiles")
+    want = engine_source_hash()
+    if not os.path.isdir(d):
+        return None
+    for fn in sorted(os.listdir(d)):
+        if not fn.endswith(".md"):
+            continue
+        meta = {}
+        with open(os.path.join(d, fn)) as f:
+            for line in f:
+                if line.startswith("<!-- traffic "):
+                    for kv in line[len("<!-- traffic "):].replace("-->", "").split():
+                        k, _, v = kv.partition("=")
+                        meta[k] = v
+        if (meta.get("kernel") == kernel and meta.get("workload") == workload
+                and meta.get("form") == form and meta.get("source_sha256") == want):
+            try:
+                return float(meta["bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
 
 
 # ---------------------------------------------------------------- roofline model
@@ -250,7 +294,8 @@ def run_native(args):
             max_m=max_m,
             engine_ms_per_step=eng_s * 1e3 / args.steps,
             roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                      "frac": achieved / hbm_peak, "traffic": None,
+                      "frac": achieved / hbm_peak,
+                      "traffic": measured_traffic("slice_engine", wl.name, form),
                       "kernel": "slice_engine", "peak_source": peak_src,
                       "bytes_per_launch": bytes_alg / args.steps},
             e2e={"value": e2e_slices * world / e2e_s, "unit": UNIT,
@@ -293,6 +338,145 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batched scan
+def run_batched(args):
+    """The 48-instance parameter scan (16 each of 128^2, 192^2, 256^2 over
+    [-8,8]^2, 512 base slices, 4 ppc, n_b in [0.5, 8], sigma_r in [0.3, 0.8])
+    as one batched launch per 3D step, refined form, settings per size from the
+    autotuner (tuned untimed on 16-slice windows before the timed steps)."""
+    import torch
+
+    import paper_2012_00881_gb300 as qs
+    import workloads as W
+    from paper_2012_00881_gb300 import autotune as AT
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    insts = W.scan_instances()
+    if args.slices > 0:
+        insts = [wl.with_(n_xi=args.slices, xi_len=wl.xi_len * args.slices / wl.n_xi)
+                 for wl in insts]
+    t0 = time.perf_counter()
+    tuned = AT.tune(insts, precision="fp32r", n_slices=16,
+                    cands=AT.candidates(tiles=((32, 16), (64, 32)), sweeps=((2, 2),),
+                                        coarse=(16, 32)))
+    tune_s = time.perf_counter() - t0
+    beams_np = [[W.sample_beam(b) for b in wl.beams] for wl in insts]
+    ctxs, beams, master = [], [], []
+    for wl, bn in zip(insts, beams_np):
+        c = qs.Context(qs.config_from_workload(wl, precision="fp32r", **AT.apply(wl, tuned)))
+        c.init_plasma(wl.ppc)
+        ctxs.append(c)
+        master.append([qs.Beam(b, device=dev) for b in bn])
+        beams.append([qs.Beam(b, device=dev) for b in bn])
+
+    def reset():
+        for ms, bs in zip(master, beams):
+            for a, b in zip(ms, bs):
+                for k in qs.Beam.KEYS:
+                    b.t[k].copy_(a.t[k])
+
+    def one_step():
+        st = qs.step3d_batched(ctxs, beams)
+        for c, b, wl in zip(ctxs, beams, insts):
+            c.push_beam(b, wl.dt)
+        return st
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        reset()
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times, slices, pushes, eng_ms, bytes_alg = [], 0, 0, 0.0, 0.0
+    for _ in range(args.steps):
+        reset()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = one_step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        eng_ms += st[0]["gpu_ms"]
+        for s_, wl in zip(st, insts):
+            slices += s_["slices"]
+            pushes += s_["pushes"]
+            bytes_alg += algorithmic_bytes(s_, wl, 4, wl.n_xi)
+    clocks = sampler.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # end to end: beams from pinned host memory each step, read back after
+    host = [[{k: torch.as_tensor(b[k]).pin_memory() for k in qs.Beam.KEYS} for b in bn]
+            for bn in beams_np]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_slices = 0
+    for _ in range(args.steps):
+        for hs, bs in zip(host, beams):
+            for h, b in zip(hs, bs):
+                for k in qs.Beam.KEYS:
+                    b.t[k].copy_(h[k], non_blocking=True)
+        st = one_step()
+        e2e_slices += sum(s_["slices"] for s_ in st)
+        out = [b.t["pz"].to("cpu", non_blocking=True) for bs in beams for b in bs]
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    bbytes = sum(7 * 8 * len(b["x"]) for bn in beams_np for b in bn)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_alg / (eng_ms / 1e3) / 1e9
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    out = {
+        "metric": METRIC, "value": slices * world / (total_ms / 1e3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "scan48: 48 independent instances (16 each of 128^2, 192^2, 256^2 "
+                               f"over [-8,8]^2), {insts[0].n_xi} base slices over "
+                               f"{insts[0].xi_len:g}, 4 ppc, one driver each (n_b 0.5..8, "
+                               "sigma_r 0.3..0.8, sigma_z 0.7, 100k), refined form, one batched "
+                               "launch per 3D step",
+                   "form": "fp32r-batched", "tuned": {str(k): v for k, v in tuned.items()},
+                   "tune_seconds": tune_s,
+                   "l2": "history and beam grids larger than L2; 256 MB write between steps"},
+        "pushes_per_s": pushes * world / (total_ms / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "kernel": "slice_engine_batched", "peak_source": "measured",
+                     "bytes_per_launch": bytes_alg / args.steps},
+        "e2e": {"value": e2e_slices * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": bbytes,
+                "d2h_bytes_per_step": sum(8 * len(b["x"]) for bn in beams_np for b in bn)},
+        "gpu_launches": args.steps * (1 + 2 * sum(len(b) for b in beams)),
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    for c in ctxs:
+        c.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 # ---------------------------------------------------------------- oracle timing
 def _oracle_sample(wl, seconds: float):
     """Time the FP64 oracle on the first base slices of one 3D step of the
@@ -331,6 +515,9 @@ def run_reference(args):
     if rank != 0:
         return
     wl = _load_workload(args)
+    if wl is None:  # the scan: time the oracle on its 256^2 instances
+        import workloads as W
+        wl = [w for w in W.scan_instances() if w.n == 256][0]
     per_step = max(2.0, args.cpu_seconds / 2)
     vals, slices, secs = [], 0, 0.0
     for i in range(args.warmup + args.steps):
@@ -356,5 +543,7 @@ if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == SCAN:
+        run_batched(a)
     else:
         run_native(a)

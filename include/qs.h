@@ -87,10 +87,16 @@ typedef struct {
     int pre_sweeps, post_sweeps;/* red-black Gauss-Seidel sweeps per level      */
     int coarse_block_n;         /* multigrid levels of side <= this are relaxed  */
                                 /* by one thread block in shared memory;         */
-                                /* 0 = default (16 for QS_FP64, 64 for refined) */
+                                /* 0 = default (16 for QS_FP64, 32 for refined) */
     int trace_capacity;         /* > 0: record up to this many phase timestamps */
                                 /* per step (see qs_phase_trace); 0 = off        */
-    int reserved[6];            /* must be zero                                  */
+    int warm_start_order;       /* initial guess of each solve: 0 = previous    */
+                                /* slice's solution (Sec. 7.1); 1, 2 = that     */
+                                /* history extrapolated in xi, linear/quadratic */
+    int tile_x, tile_y;         /* refined form: output tile of the grid-wide   */
+                                /* multigrid levels staged in shared memory;    */
+                                /* even, 0 = default 32 x 16                     */
+    int reserved[3];            /* must be zero                                  */
 } qs_config;
 
 /* Driver-beam macroparticles: structure of arrays of float64, n entries each.
@@ -122,7 +128,7 @@ typedef struct {
 
 /* Defaults: N = 64 on [-6,6]^2, 128 slices on [0,12], refine_k = 8,
  * QS_FP64, mg_tol = 1e-10, 60 V-cycles, psi_floor = 1e-3, unlimited guard
- * hits, sort_every = 16, V(2,2). */
+ * hits, sort_every = 16, V(2,2), warm_start_order = 2. */
 void qs_config_default(qs_config *cfg);
 
 /* Create a context on the current CUDA device; `cuda_stream` is a
@@ -170,6 +176,21 @@ int qs_step3d(qs_ctx *ctx, const qs_beam *beams, int n_beams, qs_step_stats *sta
  * adaptive rule; used to replay a schedule. */
 int qs_step3d_schedule(qs_ctx *ctx, const qs_beam *beams, int n_beams,
                        const int32_t *m_schedule, qs_step_stats *stats);
+
+/* Batched form: one 3D step (as qs_step3d) of each of n independent
+ * contexts, which may differ in size, window, drivers, tiles and sweeps, in a
+ * single persistent launch.  The launch is split into teams of `team_blocks`
+ * thread blocks (0 = as many blocks per team as leave every instance its own
+ * team); each team takes the next context from a device-side queue and runs
+ * its whole slice loop behind the team's own barrier.  All contexts must use
+ * one precision and one device; the launch is queued on the first context's
+ * stream and the call synchronises it.  beams[i] / n_beams[i] give context
+ * i's drivers (DEVICE arrays; both lists may be NULL for no drivers).
+ * stats (may be NULL) receives n entries; gpu_ms is the whole launch.
+ * Returns the first failing status of any context (QS_ERR_ARG for repeated
+ * contexts or mixed precisions). */
+int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const int *n_beams,
+                      int team_blocks, qs_step_stats *stats);
 
 /* Push_Driver of Algorithm 1: advance every beam macroparticle by one
  * relativistic Boris step of length dt (Eqs. EoM_beam_1/2) in the wake stored

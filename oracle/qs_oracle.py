@@ -450,8 +450,9 @@ class Config:
         return (self.xi_max - self.xi_min) / self.n_xi
 
 
-def deposit_beam(cfg: Config, beams: Sequence[dict]) -> np.ndarray:
-    """j_z of the drivers on the base slices, shape (n_xi, N, N).
+def deposit_beam(cfg: Config, beams: Sequence[dict], n_slices: Optional[int] = None) -> np.ndarray:
+    """j_z of the drivers on the base slices, shape (n_xi, N, N), or on the
+    first `n_slices` base slices only (the rest of the window is not stored).
 
     CIC in x, y (folded at the walls like the plasma deposit) and linear in xi
     between base slices; particles outside the transverse box, and weight that
@@ -460,7 +461,8 @@ def deposit_beam(cfg: Config, beams: Sequence[dict]) -> np.ndarray:
     """
     g = cfg.grid
     n = g.n
-    out = np.zeros(cfg.n_xi * n * n)
+    ns = cfg.n_xi if n_slices is None else min(cfg.n_xi, n_slices)
+    out = np.zeros(ns * n * n)
     for b in beams:
         x, y, xi = b["x"], b["y"], b["xi"]
         gam = np.sqrt(1.0 + b["px"] ** 2 + b["py"] ** 2 + b["pz"] ** 2)
@@ -472,11 +474,11 @@ def deposit_beam(cfg: Config, beams: Sequence[dict]) -> np.ndarray:
         j0 = j0.astype(np.int64)
         idx, wts = cic_stencil(x, y, g)
         for jj, wj in ((j0, 1.0 - f), (j0 + 1, f)):
-            ok = inside & (jj >= 0) & (jj < cfg.n_xi)
+            ok = inside & (jj >= 0) & (jj < ns)
             for i, wgt in zip(idx, wts):
                 out += np.bincount((jj[ok] * n * n + i[ok]), weights=(q * wj * wgt)[ok],
-                                   minlength=cfg.n_xi * n * n)
-    return (out / (g.h * g.h * cfg.dxi0)).reshape(cfg.n_xi, n, n)
+                                   minlength=ns * n * n)
+    return (out / (g.h * g.h * cfg.dxi0)).reshape(ns, n, n)
 
 
 @dataclasses.dataclass
@@ -502,9 +504,9 @@ def step3d(cfg: Config, plasma0: Plasma, n_ion: np.ndarray, beams: Sequence[dict
     adaptive rule (used to freeze the schedule of a previous run).
     """
     g = cfg.grid
-    if jzb is None:
-        jzb = deposit_beam(cfg, beams)
     nb = cfg.n_xi if n_slices is None else n_slices
+    if jzb is None:
+        jzb = deposit_beam(cfg, beams, n_slices=min(cfg.n_xi, nb + 1))
     v0 = g.h / cfg.dxi0
     hist = np.zeros((5, nb, g.n, g.n))
     ms = np.ones(nb, dtype=np.int64)
@@ -516,7 +518,7 @@ def step3d(cfg: Config, plasma0: Plasma, n_ion: np.ndarray, beams: Sequence[dict
     zero = np.zeros((g.n, g.n))
     for j in range(nb):
         ms[j] = m
-        nxt = jzb[j + 1] if j + 1 < cfg.n_xi else zero
+        nxt = jzb[j + 1] if j + 1 < min(cfg.n_xi, jzb.shape[0]) else zero
         for q in range(m):
             frac = q / m
             jz_here = jzb[j] if q == 0 else (1.0 - frac) * jzb[j] + frac * nxt

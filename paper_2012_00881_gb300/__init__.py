@@ -8,10 +8,12 @@ from ._binding import (FIELD_ALL, FIELD_BX, FIELD_BY, FIELD_BZ, FIELD_EZ, FIELD_
                        FIELD_NAMES, FIELD_PSI, PROTOTYPES, QS_ERR_ARG, QS_ERR_CUDA,
                        QS_ERR_NOT_CONVERGED, QS_ERR_OOM, QS_ERR_PSI_FLOOR, QS_ERR_STATE,
                        QS_ERR_TIMEOUT, QS_FP32_REFINED, QS_FP64, QS_OK, Beam, Context, QsConfig,
-                       QsError, config_from_workload, default_config, load_library)
+                       QsError, config_from_workload, default_config, load_library,
+                       step3d_batched, cell_sort_noalloc)
 
 __all__ = [
     "Beam", "Context", "QsConfig", "QsError", "config_from_workload", "default_config",
+    "step3d_batched", "cell_sort_noalloc",
     "load_library", "PROTOTYPES", "FIELD_ALL", "FIELD_PSI", "FIELD_EZ", "FIELD_BZ", "FIELD_BX",
     "FIELD_BY", "FIELD_JZB", "FIELD_NAMES", "QS_FP64", "QS_FP32_REFINED",
 ]

@@ -45,7 +45,9 @@ class QsConfig(ctypes.Structure):
         ("pre_sweeps", ctypes.c_int), ("post_sweeps", ctypes.c_int),
         ("coarse_block_n", ctypes.c_int),
         ("trace_capacity", ctypes.c_int),
-        ("reserved", ctypes.c_int * 6),
+        ("warm_start_order", ctypes.c_int),
+        ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -82,6 +84,7 @@ PROTOTYPES = {
     "qs_step3d": (_I, [_P, _P, _I, ctypes.POINTER(QsStepStats)]),
     "qs_step3d_schedule": (_I, [_P, _P, _I, _P, ctypes.POINTER(QsStepStats)]),
     "qs_push_beam": (_I, [_P, _P, _I, _D]),
+    "qs_step3d_batched": (_I, [_P, _I, _P, _P, _I, _P]),
     "qs_fields": (_I, [_P, _I, _I, _I, _P, _I]),
     "qs_slice_diagnostics": (_I, [_P, _P, _P, _P]),
     "qs_get_plasma": (_I, [_P, _P, _P, _P, _P, _P, _P]),
@@ -337,3 +340,33 @@ def cell_sort_noalloc(n: int, x_min: float, y_min: float, h: float, x, y, pid, o
         raise QsError(rc, "qs_cell_sort_noalloc: " + lib.qs_strerror(rc).decode())
     st.synchronize()
     return cell, count, offset, perm
+
+
+def step3d_batched(contexts: Sequence["Context"], beams: Sequence[Sequence[Beam]] = None,
+                   team_blocks: int = 0, raise_on_error: bool = True) -> List[Dict]:
+    """qs_step3d_batched over several contexts; returns one stats dict each."""
+    lib = load_library()
+    n = len(contexts)
+    handles = (_P * n)(*[c.h for c in contexts])
+    arrays = []
+    ptrs = (_P * n)()
+    counts = (ctypes.c_int * n)()
+    for i in range(n):
+        bl = list(beams[i]) if beams is not None else []
+        arr = _beam_array(bl)
+        arrays.append(arr)
+        ptrs[i] = ctypes.cast(arr, _P)
+        counts[i] = len(bl)
+    stats = (QsStepStats * n)()
+    st = lib.qs_step3d_batched(ctypes.cast(handles, _P), n, ctypes.cast(ptrs, _P),
+                               ctypes.cast(counts, _P), int(team_blocks), ctypes.cast(stats, _P))
+    if raise_on_error and st != QS_OK:
+        msg = lib.qs_last_error(contexts[0].h).decode()
+        raise QsError(st, f"qs_step3d_batched: {lib.qs_strerror(st).decode()}: {msg}")
+    out = []
+    for s_ in stats:
+        out.append(dict(status=s_.status, slices=s_.slices, substeps=s_.substeps,
+                        pushes=s_.pushes, vcycles=list(s_.vcycles),
+                        psi_guard_hits=s_.psi_guard_hits, max_relres=s_.max_relres,
+                        vmax=s_.vmax, max_m=s_.max_m, gpu_ms=s_.gpu_ms))
+    return out

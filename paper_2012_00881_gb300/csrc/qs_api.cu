@@ -25,6 +25,7 @@ struct qs_ctx {
     double *psi = nullptr, *ez = nullptr, *bz = nullptr, *bx = nullptr, *by = nullptr;
     double *f_psi = nullptr, *f_ez = nullptr, *f_bz = nullptr, *f_bx = nullptr, *f_by = nullptr;
     double *dpx = nullptr, *dpy = nullptr, *jz = nullptr, *kap = nullptr, *invd0 = nullptr;
+    double *hist1[5] = {}, *hist2[5] = {};
     LevelArrays lev[QS_MAX_LEV] = {};
     float *e32[2] = {nullptr, nullptr}, *r32[2] = {nullptr, nullptr};
     float *k32 = nullptr, *d32 = nullptr;
@@ -46,6 +47,8 @@ struct qs_ctx {
     int32_t *t_id = nullptr;
     double *x = nullptr, *y = nullptr, *px = nullptr, *py = nullptr, *w = nullptr;
     int32_t *id = nullptr;
+    float *px32 = nullptr, *py32 = nullptr, *w32 = nullptr;
+    float *g32[6] = {};  // refined form: jx, jy, txx, txy, tyy, G
     std::vector<void *> plasma_allocs;
     bool have_plasma = false, have_step = false;
     int engine_blocks = 0;
@@ -149,7 +152,16 @@ int validate(const qs_config *cfg, char *why, size_t nwhy) {
         snprintf(why, nwhy, "trace_capacity must be in [0, 2^26]");
         return QS_ERR_ARG;
     }
-    for (int i = 0; i < 6; ++i)
+    if (cfg->warm_start_order < 0 || cfg->warm_start_order > 2) {
+        snprintf(why, nwhy, "warm_start_order must be 0, 1 or 2");
+        return QS_ERR_ARG;
+    }
+    if (cfg->tile_x < 0 || cfg->tile_y < 0 || (cfg->tile_x & 1) || (cfg->tile_y & 1) ||
+        cfg->tile_x > 256 || cfg->tile_y > 256 || ((cfg->tile_x == 0) != (cfg->tile_y == 0))) {
+        snprintf(why, nwhy, "tile_x, tile_y must both be 0 or even in [2, 256]");
+        return QS_ERR_ARG;
+    }
+    for (int i = 0; i < 3; ++i)
         if (cfg->reserved[i] != 0) {
             snprintf(why, nwhy, "reserved fields must be zero");
             return QS_ERR_ARG;
@@ -174,7 +186,9 @@ int create_impl(qs_ctx *c) {
     double **grids[] = {&c->n_a, &c->n_b, &c->n_ion, &c->jx,  &c->jy,   &c->txx, &c->txy,
                         &c->tyy, &c->G,   &c->psi,   &c->ez,  &c->bz,   &c->bx,  &c->by,
                         &c->f_psi, &c->f_ez, &c->f_bz, &c->f_bx, &c->f_by, &c->dpx, &c->dpy,
-                        &c->jz,  &c->kap, &c->invd0};
+                        &c->jz,  &c->kap, &c->invd0, &c->hist1[0], &c->hist1[1],
+                        &c->hist1[2], &c->hist1[3], &c->hist1[4], &c->hist2[0], &c->hist2[1],
+                        &c->hist2[2], &c->hist2[3], &c->hist2[4]};
     for (double **p : grids) AL(L, *p, nn);
     const bool ref = g.precision == QS_FP32_REFINED;
     for (int l = 1; l < c->nlev; ++l) {
@@ -198,7 +212,9 @@ int create_impl(qs_ctx *c) {
         }
     }
     if (ref) {
-        float **g32[] = {&c->e32[0], &c->e32[1], &c->r32[0], &c->r32[1], &c->k32, &c->d32};
+        float **g32[] = {&c->e32[0], &c->e32[1], &c->r32[0], &c->r32[1], &c->k32, &c->d32,
+                         &c->g32[0], &c->g32[1], &c->g32[2], &c->g32[3], &c->g32[4],
+                         &c->g32[5]};
         for (float **p : g32) {
             AL(L, *p, nn);
             CK(cudaMemsetAsync(*p, 0, nn * sizeof(float), c->st), "memset");
@@ -217,16 +233,17 @@ int create_impl(qs_ctx *c) {
     for (double **p : grids) CK(cudaMemsetAsync(*p, 0, nn * sizeof(double), c->st), "memset");
     CK(cudaMemsetAsync(c->hist, 0, 5 * (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
     CK(cudaMemsetAsync(c->jzb, 0, (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
-    c->block_level_n = g.coarse_block_n > 0 ? g.coarse_block_n : (ref ? 64 : 16);
-    c->tile_x = ref ? 32 : 0;
-    c->tile_y = ref ? 16 : 0;
+    c->block_level_n = g.coarse_block_n > 0 ? g.coarse_block_n : (ref ? 32 : 16);
+    c->tile_x = ref ? (g.tile_x > 0 ? g.tile_x : 32) : 0;
+    c->tile_y = ref ? (g.tile_y > 0 ? g.tile_y : 16) : 0;
     const int nu = g.pre_sweeps > g.post_sweeps ? g.pre_sweeps : g.post_sweeps;
     c->engine_smem = qs_engine_smem_bytes(c->lev_n, c->nlev, c->block_level_n, g.precision,
                                           c->tile_x, c->tile_y, nu, &c->block_offset,
                                           &c->tile_offset);
-    if (c->engine_smem > 200 * 1024)
-        return fail(c, QS_ERR_ARG, "coarse_block_n = %d needs %zu bytes of shared memory",
-                    c->block_level_n, c->engine_smem);
+    if (c->engine_smem > 220 * 1024)
+        return fail(c, QS_ERR_ARG,
+                    "coarse_block_n = %d with %d x %d tiles needs %zu bytes of shared memory",
+                    c->block_level_n, c->tile_x, c->tile_y, c->engine_smem);
     int blocks = 0;
     if (qs_engine_max_blocks(c->dev, g.precision, c->engine_smem, &blocks) != 0 || blocks < 1)
         return fail(c, QS_ERR_CUDA, "slice engine cannot be made resident");
@@ -268,6 +285,7 @@ void qs_config_default(qs_config *cfg) {
     cfg->sort_every = 16;
     cfg->pre_sweeps = 2;
     cfg->post_sweeps = 2;
+    cfg->warm_start_order = 2;
 }
 
 int qs_create(const qs_config *cfg, void *cuda_stream, qs_ctx **out) {
@@ -329,6 +347,11 @@ int qs_init_plasma(qs_ctx *c, int ppc, const double *profile, int n_coef, double
     AL(L, c->py, np);
     AL(L, c->w, np);
     AL(L, c->id, np);
+    if (c->cfg.precision == QS_FP32_REFINED) {
+        AL(L, c->px32, np);
+        AL(L, c->py32, np);
+        AL(L, c->w32, np);
+    }
     double *d_table = nullptr;
     if (profile) {
         AL(L, d_table, (size_t)n_coef);
@@ -359,8 +382,11 @@ int qs_init_plasma(qs_ctx *c, int ppc, const double *profile, int n_coef, double
     return QS_OK;
 }
 
-static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t *sched,
-                     qs_step_stats *stats) {
+// Everything of a 3D step before the slice engine: validation, fresh plasma,
+// zeroed fields, the driver current on the base slices, reset diagnostics;
+// fills the engine arguments.  Work is queued on `st`.
+static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t *sched,
+                        cudaStream_t st, EngineArgs &a) {
     if (check_ctx(c)) return QS_ERR_ARG;
     if (!c->have_plasma) return fail(c, QS_ERR_STATE, "qs_init_plasma has not been called");
     if (n_beams < 0 || (n_beams > 0 && !beams)) return fail(c, QS_ERR_ARG, "bad beam list");
@@ -381,30 +407,38 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
     const double dxi0 = (g.xi_max - g.xi_min) / g.n_xi;
     // fresh plasma at the head of the window
     const size_t bd = c->np * sizeof(double);
-    CK(cudaMemcpyAsync(c->x, c->t_x, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
-    CK(cudaMemcpyAsync(c->y, c->t_y, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
-    CK(cudaMemcpyAsync(c->px, c->t_px, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
-    CK(cudaMemcpyAsync(c->py, c->t_py, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
-    CK(cudaMemcpyAsync(c->w, c->t_w, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
-    CK(cudaMemcpyAsync(c->id, c->t_id, c->np * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->st),
+    CK(cudaMemcpyAsync(c->x, c->t_x, bd, cudaMemcpyDeviceToDevice, st), "copy");
+    CK(cudaMemcpyAsync(c->y, c->t_y, bd, cudaMemcpyDeviceToDevice, st), "copy");
+    CK(cudaMemcpyAsync(c->px, c->t_px, bd, cudaMemcpyDeviceToDevice, st), "copy");
+    CK(cudaMemcpyAsync(c->py, c->t_py, bd, cudaMemcpyDeviceToDevice, st), "copy");
+    CK(cudaMemcpyAsync(c->w, c->t_w, bd, cudaMemcpyDeviceToDevice, st), "copy");
+    CK(cudaMemcpyAsync(c->id, c->t_id, c->np * sizeof(int32_t), cudaMemcpyDeviceToDevice, st),
        "copy");
-    CK(cudaMemsetAsync(c->n_a, 0, nn * sizeof(double), c->st), "memset");
+    CK(cudaMemsetAsync(c->n_a, 0, nn * sizeof(double), st), "memset");
+    if (g.precision == QS_FP32_REFINED) {  // float32 momenta and weights of the refined form
+        CK(qs_launch_convert(st, c->t_px, c->px32, c->np), "convert");
+        CK(qs_launch_convert(st, c->t_py, c->py32, c->np), "convert");
+        CK(qs_launch_convert(st, c->t_w, c->w32, c->np), "convert");
+    }
+    // the wake ahead of the driver is zero: every solve of the first slice
+    // starts from zero
+    for (double *f : {c->psi, c->ez, c->bz, c->bx, c->by})
+        CK(cudaMemsetAsync(f, 0, nn * sizeof(double), st), "memset");
     // driver current on the base slices
-    CK(cudaMemsetAsync(c->jzb, 0, (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
+    CK(cudaMemsetAsync(c->jzb, 0, (size_t)g.n_xi * nn * sizeof(double), st), "memset");
     for (int b = 0; b < n_beams; ++b)
-        CK(qs_launch_beam_deposit(c->st, beams[b], c->N, g.x_min, g.x_max, g.y_min, g.y_max,
+        CK(qs_launch_beam_deposit(st, beams[b], c->N, g.x_min, g.x_max, g.y_min, g.y_max,
                                   c->h, g.n_xi, g.xi_min, dxi0, c->jzb),
            "beam deposit");
-    CK(cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->st), "memset");
-    CK(cudaMemsetAsync(c->diag_m, 0, g.n_xi * sizeof(int32_t), c->st), "memset");
-    CK(cudaMemsetAsync(c->diag_vmax, 0, g.n_xi * sizeof(double), c->st), "memset");
-    CK(cudaMemsetAsync(c->diag_charge, 0, g.n_xi * sizeof(double), c->st), "memset");
+    CK(cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), st), "memset");
+    CK(cudaMemsetAsync(c->diag_m, 0, g.n_xi * sizeof(int32_t), st), "memset");
+    CK(cudaMemsetAsync(c->diag_vmax, 0, g.n_xi * sizeof(double), st), "memset");
+    CK(cudaMemsetAsync(c->diag_charge, 0, g.n_xi * sizeof(double), st), "memset");
     if (sched)
         CK(cudaMemcpyAsync(c->d_sched, sched, g.n_xi * sizeof(int32_t), cudaMemcpyHostToDevice,
-                           c->st),
+                           st),
            "copy schedule");
 
-    EngineArgs a;
     std::memset(&a, 0, sizeof(a));
     a.N = c->N;
     a.h = c->h;
@@ -430,6 +464,15 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
     a.px = c->px;
     a.py = c->py;
     a.w = c->w;
+    a.px32 = c->px32;
+    a.py32 = c->py32;
+    a.w32 = c->w32;
+    a.jx32 = c->g32[0];
+    a.jy32 = c->g32[1];
+    a.txx32 = c->g32[2];
+    a.txy32 = c->g32[3];
+    a.tyy32 = c->g32[4];
+    a.G32 = c->g32[5];
     a.n_a = c->n_a;
     a.n_b = c->n_b;
     a.n_ion = c->n_ion;
@@ -454,6 +497,11 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
     a.jz = c->jz;
     a.kap = c->kap;
     a.invd0 = c->invd0;
+    for (int f = 0; f < 5; ++f) {
+        a.hist1[f] = c->hist1[f];
+        a.hist2[f] = c->hist2[f];
+    }
+    a.ws_order = g.warm_start_order;
     a.nlev = c->nlev;
     for (int l = 0; l < c->nlev; ++l) {
         a.lev_n[l] = c->lev_n[l];
@@ -483,10 +531,12 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
     a.sc = c->sc;
     a.trace = c->trace;
     a.trace_cap = g.trace_capacity;
-    CK(cudaEventRecord(c->ev0, c->st), "event");
-    CK(qs_launch_engine(c->st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
-    CK(cudaEventRecord(c->ev1, c->st), "event");
-    CK(cudaStreamSynchronize(c->st), "slice engine");
+    return QS_OK;
+}
+
+// After the slice engine: read the device scalars, set the status, fill stats.
+static int step_finish(qs_ctx *c, qs_step_stats *stats, double gpu_ms) {
+    const qs_config &g = c->cfg;
     DevScalars hs;
     CK(cudaMemcpy(&hs, c->sc, sizeof(hs), cudaMemcpyDeviceToHost), "copy scalars");
     c->have_step = true;
@@ -515,11 +565,24 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
         stats->vmax = vm;
         stats->max_m = hs.max_m;
         stats->status = status;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-        stats->gpu_ms = ms;
+        stats->gpu_ms = gpu_ms;
     }
     return status;
+}
+
+static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t *sched,
+                     qs_step_stats *stats) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    EngineArgs a;
+    int r = step_prepare(c, beams, n_beams, sched, c->st, a);
+    if (r != QS_OK) return r;
+    CK(cudaEventRecord(c->ev0, c->st), "event");
+    CK(qs_launch_engine(c->st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
+    CK(cudaEventRecord(c->ev1, c->st), "event");
+    CK(cudaStreamSynchronize(c->st), "slice engine");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    return step_finish(c, stats, ms);
 }
 
 int qs_step3d(qs_ctx *c, const qs_beam *beams, int n_beams, qs_step_stats *stats) {
@@ -530,6 +593,69 @@ int qs_step3d_schedule(qs_ctx *c, const qs_beam *beams, int n_beams, const int32
                        qs_step_stats *stats) {
     if (!m_schedule) return fail(c, QS_ERR_ARG, "m_schedule is NULL");
     return step_impl(c, beams, n_beams, m_schedule, stats);
+}
+
+int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const int *n_beams,
+                      int team_blocks, qs_step_stats *stats) {
+    if (n < 1 || !ctxs) return QS_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return QS_ERR_ARG;
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) return fail(ctxs[0], QS_ERR_ARG, "context %d repeated", i);
+        if (ctxs[i]->cfg.precision != ctxs[0]->cfg.precision || ctxs[i]->dev != ctxs[0]->dev)
+            return fail(ctxs[0], QS_ERR_ARG, "batched contexts need one precision and device");
+    }
+    qs_ctx *c = ctxs[0];
+    if (team_blocks < 0) return fail(c, QS_ERR_ARG, "team_blocks must be >= 0");
+    cudaStream_t st = c->st;
+    std::vector<EngineArgs> list(n);
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        const int r = step_prepare(ctxs[i], beams ? beams[i] : nullptr, n_beams ? n_beams[i] : 0,
+                                   nullptr, st, list[i]);
+        if (r != QS_OK) {
+            if (i > 0) fail(c, r, "context %d: %s", i, ctxs[i]->msg);
+            return r;
+        }
+        list[i].trace = nullptr;
+        list[i].trace_cap = 0;
+        if (ctxs[i]->engine_smem > smem) smem = ctxs[i]->engine_smem;
+    }
+    int total = 0;
+    if (qs_engine_batched_max_blocks(c->dev, c->cfg.precision, smem, &total) != 0 || total < 1)
+        return fail(c, QS_ERR_CUDA, "batched slice engine cannot be made resident");
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev), "attr");
+    if (total > sms) total = sms;
+    int team = team_blocks > 0 ? team_blocks : total / n;
+    if (team < 1) team = 1;
+    if (team > total) team = total;
+    int teams = total / team;
+    if (teams > QS_MAX_TEAMS) teams = QS_MAX_TEAMS;
+    void *dbuf = nullptr;
+    const size_t list_bytes = (n * sizeof(EngineArgs) + 255) & ~(size_t)255;
+    CK(cudaMallocAsync(&dbuf, list_bytes + sizeof(BatchState), st), "cudaMallocAsync");
+    EngineArgs *dlist = static_cast<EngineArgs *>(dbuf);
+    BatchState *bs = reinterpret_cast<BatchState *>(static_cast<char *>(dbuf) + list_bytes);
+    cudaError_t e = cudaMemcpyAsync(dlist, list.data(), n * sizeof(EngineArgs),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bs, 0, sizeof(BatchState), st);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev0, st);
+    if (e == cudaSuccess)
+        e = qs_launch_engine_batched(st, dlist, n, c->cfg.precision, team, teams, bs, smem);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev1, st);
+    cudaFreeAsync(dbuf, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched slice engine");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "batched slice engine");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    int status = QS_OK;
+    for (int i = 0; i < n; ++i) {
+        const int r = step_finish(ctxs[i], stats ? &stats[i] : nullptr, ms);
+        if (r != QS_OK && status == QS_OK) status = r;
+    }
+    return status;
 }
 
 int qs_push_beam(qs_ctx *c, qs_beam *beams, int n_beams, double dt) {
@@ -592,6 +718,11 @@ int qs_get_plasma(qs_ctx *c, double *x, double *y, double *px, double *py, doubl
     if (!c->have_plasma) return fail(c, QS_ERR_STATE, "qs_init_plasma has not been called");
     const size_t bd = c->np * sizeof(double);
     const cudaMemcpyKind k = cudaMemcpyDeviceToHost;
+    if (c->have_step && c->cfg.precision == QS_FP32_REFINED) {  // float32 working copy
+        CK(qs_launch_widen(c->st, c->px32, c->px, c->np), "widen");
+        CK(qs_launch_widen(c->st, c->py32, c->py, c->np), "widen");
+        CK(qs_launch_widen(c->st, c->w32, c->w, c->np), "widen");
+    }
     if (x) CK(cudaMemcpyAsync(x, c->x, bd, k, c->st), "copy");
     if (y) CK(cudaMemcpyAsync(y, c->y, bd, k, c->st), "copy");
     if (px) CK(cudaMemcpyAsync(px, c->px, bd, k, c->st), "copy");

@@ -167,6 +167,18 @@ __global__ void k_beam_push(double *x, double *y, double *xi, double *px, double
     }
 }
 
+__global__ void k_convert(const double *src, float *dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+__global__ void k_widen(const float *src, double *dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
 // ---- stable counting sort by cell ----
 __global__ void k_sort_count(const double *x, const double *y, int64_t np, int n, double x_min,
                              double y_min, double h, int32_t *cell, int32_t *count) {
@@ -271,6 +283,18 @@ cudaError_t qs_launch_beam_push(cudaStream_t st, const qs_beam &b, int n, double
     k_beam_push<<<blocks_for(b.n), kThreads, 0, st>>>(b.x, b.y, b.xi, b.px, b.py, b.pz, b.n,
                                                       b.q_over_m, n, x_min, x_max, y_min, y_max,
                                                       h, n_xi, xi_min, dxi0, hist, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t qs_launch_convert(cudaStream_t st, const double *src, float *dst, int64_t n) {
+    if (n <= 0) return cudaSuccess;
+    k_convert<<<blocks_for(n), kThreads, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t qs_launch_widen(cudaStream_t st, const float *src, double *dst, int64_t n) {
+    if (n <= 0) return cudaSuccess;
+    k_widen<<<blocks_for(n), kThreads, 0, st>>>(src, dst, n);
     return cudaGetLastError();
 }
 

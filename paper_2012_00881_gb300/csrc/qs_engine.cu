@@ -11,6 +11,8 @@
 // is at most block_level_n are relaxed by block 0 alone.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "qs_tile.cuh"
 
 namespace {
@@ -46,12 +48,14 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsig
 // 0 adds 1 to a monotonic counter with a release reduction (no round trip)
 // and polls with acquire loads until the counter reaches epoch * nblk.
 struct Sync {
-    DevScalars *sc;
-    unsigned nblk;
+    DevScalars *sc;             // the instance's scalars (error word, trace count)
+    unsigned long long *bar;    // monotonic arrival counter of the blocks in the team
+    unsigned nblk;              // blocks in the team
     long long limit;
     int64_t *trace;
     int trace_cap;
     unsigned long long *epoch;  // this block's barrier count (shared memory)
+    bool tracer;                // this block records the phase trace
     __device__ bool operator()(int where) const {
         __shared__ int s_ok;
         __syncthreads();
@@ -62,10 +66,10 @@ struct Sync {
             } else {
                 const unsigned long long target = (*epoch + 1) * nblk;
                 *epoch += 1;
-                red_release_add_u64(&sc->bar_arrive, 1ull);
-                if (ld_acquire_u64(&sc->bar_arrive) < target) {
+                red_release_add_u64(bar, 1ull);
+                if (ld_acquire_u64(bar) < target) {
                     const long long t0 = clock64();
-                    while (ld_acquire_u64(&sc->bar_arrive) < target) {
+                    while (ld_acquire_u64(bar) < target) {
                         if (vload(&sc->err) != 0) {
                             ok = 0;
                             break;
@@ -79,7 +83,7 @@ struct Sync {
                 }
             }
             s_ok = ok;
-            if (trace && blockIdx.x == 0) {
+            if (trace && tracer) {
                 const unsigned long long k = sc->trace_n;
                 if (k < (unsigned long long)trace_cap) {
                     trace[2 * k] = where;
@@ -282,7 +286,8 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
         SYNC(30);
     }
     qsmg::block_vcycle<float, NC>(H, lg, A.nu1, A.nu2, smem, ci, false,
-                                  qsmg::Marks{A.trace, &A.sc->trace_n, A.trace_cap});
+                                  qsmg::Marks{bid == 0 ? A.trace : nullptr, &A.sc->trace_n,
+                                              A.trace_cap});
     const int mg2 = H.lv[lg].n * H.lv[lg].n;
     for (int l = lg - 1; l >= 0; --l) {
         const float *cu0 = (l + 1 == lg) ? (const float *)smem : A.lev32[l + 1].up[0];
@@ -441,33 +446,118 @@ __device__ void add_hits(DevScalars *sc, unsigned hits) {
     if (threadIdx.x == 0 && t > 0.0) atomicAdd(&sc->guard_hits, (unsigned long long)t);
 }
 
+// Plasma macroparticles and the grids they deposit into.  Positions and
+// n_* are float64 in both forms (the density source n_* - n_ion and the
+// sources built on it are small differences of O(1) numbers); momenta,
+// weights and the other six moments are in the particle precision P (float64
+// form: double; refined form: float).  In the refined form the gamma moment
+// holds n_* <gamma - 1>, which has no cancellation.
+template <typename P>
+struct PS {
+    double *x, *y;
+    P *px, *py, *w;
+    const double *wd;  // float64 weights: n_* must cancel n_ion to rounding
+    double *na, *nb;   // n_* of this slice and of the next one
+    P *jx, *jy, *txx, *txy, *tyy, *G;
+};
+
+// n_* <gamma> from the gamma moment of either form
+template <typename P>
+__device__ __forceinline__ double g_total(const P *G, const double *n, int i) {
+    if constexpr (sizeof(P) == 8) return G[i];
+    else return n[i] + (double)G[i];
+}
+
+template <typename P>
+struct CicP {
+    int i00, i01, i10, i11;
+    P w00, w01, w10, w11;
+};
+
+// CIC weights of a float64 stencil in the particle precision
+template <typename P>
+__device__ __forceinline__ CicP<P> cic_p(const Cic &c) {
+    CicP<P> r;
+    r.i00 = c.i00; r.i01 = c.i01; r.i10 = c.i10; r.i11 = c.i11;
+    r.w00 = (P)c.w00; r.w01 = (P)c.w01; r.w10 = (P)c.w10; r.w11 = (P)c.w11;
+    return r;
+}
+
+template <typename P, typename G>
+__device__ __forceinline__ P gat(const G *u, const CicP<P> &c) {
+    return (P)u[c.i00] * c.w00 + (P)u[c.i01] * c.w01 + (P)u[c.i10] * c.w10 + (P)u[c.i11] * c.w11;
+}
+
+template <typename P>
+__device__ __forceinline__ void dep(P *g, const CicP<P> &c, P q) {
+    atomicAdd(g + c.i00, q * c.w00);
+    atomicAdd(g + c.i01, q * c.w01);
+    atomicAdd(g + c.i10, q * c.w10);
+    atomicAdd(g + c.i11, q * c.w11);
+}
+
 // n_* of the initial particles
-__device__ void phase_deposit_n(const EngineArgs &A, double *ng, Thr T) {
+template <typename P>
+__device__ void phase_deposit_n(const EngineArgs &A, const PS<P> &Q, double *ng, Thr T) {
     const double s = A.inv_h * A.inv_h;
     for (int64_t p = T.t0; p < A.np; p += T.nt) {
-        Cic c = cic_stencil(A.x[p], A.y[p], A.x_min, A.y_min, A.h, A.N);
-        cic_deposit(ng, c, A.w[p] * s);
+        const Cic c = cic_stencil(Q.x[p], Q.y[p], A.x_min, A.y_min, A.h, A.N);
+        cic_deposit(ng, c, Q.wd[p] * s);
     }
+}
+
+// Initial guess of a solve: the solutions of the last (up to three) slices
+// extrapolated in xi to the new slice (order 0 is the plain warm start from
+// the previous slice, Sec. 7.1).  w[k] multiplies the solution k slices back;
+// the history of each field shifts by one as the guess replaces it.
+struct Guess {
+    double w0, w1, w2;
+    bool active;
+};
+
+__device__ __forceinline__ Guess make_guess(int order, int have, double xt, double x0, double x1,
+                                            double x2) {
+    Guess g{1.0, 0.0, 0.0, order > 0 || have > 0};
+    const int o = min(order, have - 1);
+    if (o == 1) {
+        g.w0 = (xt - x1) / (x0 - x1);
+        g.w1 = (xt - x0) / (x1 - x0);
+    } else if (o >= 2) {
+        g.w0 = (xt - x1) * (xt - x2) / ((x0 - x1) * (x0 - x2));
+        g.w1 = (xt - x0) * (xt - x2) / ((x1 - x0) * (x1 - x2));
+        g.w2 = (xt - x0) * (xt - x1) / ((x2 - x0) * (x2 - x1));
+    }
+    return g;
+}
+
+__device__ __forceinline__ void apply_guess(double *u, double *h1, double *h2, int i,
+                                            const Guess &g) {
+    const double u0 = u[i], p1 = h1[i], p2 = h2[i];
+    h2[i] = p1;
+    h1[i] = u0;
+    u[i] = g.w0 * u0 + g.w1 * p1 + g.w2 * p2;
 }
 
 // f_psi = n_* - n_ion (Eq. EqM_N8_AA) and its norm; charge sum; clear the
 // moment accumulators and the next-slice density buffer
-__device__ void phase_psi_rhs(const EngineArgs &A, const double *ncur, double *nnext, bool base,
-                              int j, Thr T) {
+template <typename P>
+__device__ void phase_psi_rhs(const EngineArgs &A, const PS<P> &Q, const double *ncur,
+                              double *nnext, bool base, int j, Thr T, const Guess &g) {
     const int nn = A.N * A.N;
     double s = 0.0, cs = 0.0;
     for (int i = T.t0; i < nn; i += T.nt) {
-        double nv = ncur[i];
-        double f = nv - A.n_ion[i];
+        if (g.active) apply_guess(A.psi, A.hist1[0], A.hist2[0], i, g);
+        const double nv = (double)ncur[i];
+        const double f = nv - A.n_ion[i];
         A.f_psi[i] = f;
         s += f * f;
         cs += nv;
-        A.jx[i] = 0.0;
-        A.jy[i] = 0.0;
-        A.txx[i] = 0.0;
-        A.txy[i] = 0.0;
-        A.tyy[i] = 0.0;
-        A.G[i] = 0.0;
+        Q.jx[i] = P(0);
+        Q.jy[i] = P(0);
+        Q.txx[i] = P(0);
+        Q.txy[i] = P(0);
+        Q.tyy[i] = P(0);
+        Q.G[i] = P(0);
         nnext[i] = 0.0;
     }
     s = block_sum(s);
@@ -478,36 +568,47 @@ __device__ void phase_psi_rhs(const EngineArgs &A, const double *ncur, double *n
     }
 }
 
-// gather psi at every particle; deposit j_perp, T, G (Eqs. Jr, FluxPres)
-__device__ void phase_moments(const EngineArgs &A, Thr T) {
-    const double s = A.inv_h * A.inv_h;
+// gather psi at every particle; deposit j_perp, T, G (Eqs. Jr, FluxPres);
+// gamma from the constant of motion is always evaluated in float64
+template <typename P>
+__device__ void phase_moments(const EngineArgs &A, const PS<P> &Q, Thr T) {
+    const P s = (P)(A.inv_h * A.inv_h);
     unsigned hits = 0;
     for (int64_t p = T.t0; p < A.np; p += T.nt) {
-        Cic c = cic_stencil(A.x[p], A.y[p], A.x_min, A.y_min, A.h, A.N);
-        double a = guard(1.0 + cic_gather(A.psi, c), A.psi_floor, hits);
-        double px = A.px[p], py = A.py[p];
-        double gam = (1.0 + px * px + py * py + a * a) / (2.0 * a);
-        double vx = px / a, vy = py / a;
-        double wq = A.w[p] * s;
-        cic_deposit(A.jx, c, wq * vx);
-        cic_deposit(A.jy, c, wq * vy);
-        cic_deposit(A.txx, c, wq * vx * vx);
-        cic_deposit(A.txy, c, wq * vx * vy);
-        cic_deposit(A.tyy, c, wq * vy * vy);
-        cic_deposit(A.G, c, wq * gam);
+        const Cic cd = cic_stencil(Q.x[p], Q.y[p], A.x_min, A.y_min, A.h, A.N);
+        const CicP<P> c = cic_p<P>(cd);
+        const double a = guard(1.0 + cic_gather(A.psi, cd), A.psi_floor, hits);
+        const P px = Q.px[p], py = Q.py[p];
+        const double p2 = (double)px * px + (double)py * py;
+        const P ap = (P)a;
+        const P vx = px / ap, vy = py / ap;
+        const P wq = Q.w[p] * s;
+        dep(Q.jx, c, wq * vx);
+        dep(Q.jy, c, wq * vy);
+        dep(Q.txx, c, wq * vx * vx);
+        dep(Q.txy, c, wq * vx * vy);
+        dep(Q.tyy, c, wq * vy * vy);
+        if constexpr (sizeof(P) == 8) {
+            dep(Q.G, c, wq * ((1.0 + p2 + a * a) / (2.0 * a)));  // gamma
+        } else {
+            const double am1 = a - 1.0;  // gamma - 1 = (p^2 + psi^2) / (2 (1 + psi))
+            dep(Q.G, c, wq * (P)((p2 + am1 * am1) / (2.0 * a)));
+        }
     }
     add_hits(A.sc, hits);
 }
 
 // central differences: zero ghosts (moments) and odd ghosts (fields)
-__device__ __forceinline__ double dx0(const double *u, int n, int ix, int i, double inv2h) {
-    double e = ix < n - 1 ? u[i + 1] : 0.0;
-    double w = ix > 0 ? u[i - 1] : 0.0;
+template <typename G>
+__device__ __forceinline__ double dx0(const G *u, int n, int ix, int i, double inv2h) {
+    const double e = ix < n - 1 ? (double)u[i + 1] : 0.0;
+    const double w = ix > 0 ? (double)u[i - 1] : 0.0;
     return (e - w) * inv2h;
 }
-__device__ __forceinline__ double dy0(const double *u, int n, int iy, int i, double inv2h) {
-    double s = iy < n - 1 ? u[i + n] : 0.0;
-    double q = iy > 0 ? u[i - n] : 0.0;
+template <typename G>
+__device__ __forceinline__ double dy0(const G *u, int n, int iy, int i, double inv2h) {
+    const double s = iy < n - 1 ? (double)u[i + n] : 0.0;
+    const double q = iy > 0 ? (double)u[i - n] : 0.0;
     return (s - q) * inv2h;
 }
 __device__ __forceinline__ double dxo(const double *u, int n, int ix, int i, double inv2h) {
@@ -523,8 +624,9 @@ __device__ __forceinline__ double dyo(const double *u, int n, int iy, int i, dou
 
 // sources of E_z, B_z (Eqs. EqM_N8_A, Mag_z_A); j_z (Eq. Jr plus the
 // driver), kappa = n_* / (1+psi) with the smoother's inverse diagonal, grad psi
-__device__ void phase_assemble1(const EngineArgs &A, const double *ncur, int j, int q, int m,
-                                Thr T) {
+template <typename P>
+__device__ void phase_assemble1(const EngineArgs &A, const PS<P> &Q, const double *ncur, int j,
+                                int q, int m, Thr T, const Guess &g) {
     const int n = A.N, nn = n * n;
     const double inv2h = 0.5 * A.inv_h;
     const double frac = (double)q / (double)m;
@@ -534,16 +636,20 @@ __device__ void phase_assemble1(const EngineArgs &A, const double *ncur, int j, 
     double sez = 0.0, sbz = 0.0;
     for (int i = T.t0; i < nn; i += T.nt) {
         const int iy = i / n, ix = i - iy * n;
-        double fez = -(dx0(A.jx, n, ix, i, inv2h) + dy0(A.jy, n, iy, i, inv2h));
-        double fbz = dx0(A.jy, n, ix, i, inv2h) - dy0(A.jx, n, iy, i, inv2h);
+        if (g.active) {
+            apply_guess(A.ez, A.hist1[1], A.hist2[1], i, g);
+            apply_guess(A.bz, A.hist1[2], A.hist2[2], i, g);
+        }
+        double fez = -(dx0(Q.jx, n, ix, i, inv2h) + dy0(Q.jy, n, iy, i, inv2h));
+        double fbz = dx0(Q.jy, n, ix, i, inv2h) - dy0(Q.jx, n, iy, i, inv2h);
         A.f_ez[i] = fez;
         A.f_bz[i] = fbz;
         sez += fez * fez;
         sbz += fbz * fbz;
         double a = guard(1.0 + A.psi[i], A.psi_floor, hits);
         double jzb = q == 0 ? J0[i] : (1.0 - frac) * J0[i] + frac * (J1 ? J1[i] : 0.0);
-        double nv = ncur[i];
-        A.jz[i] = A.G[i] / a - nv + jzb;
+        const double nv = ncur[i];
+        A.jz[i] = g_total(Q.G, ncur, i) / a - nv + jzb;
         const double kap = nv / a;
         A.kap[i] = kap;
         const int nw = qsmg::walls(ix, iy, n);
@@ -566,22 +672,28 @@ __device__ void phase_assemble1(const EngineArgs &A, const double *ncur, int j, 
 
 // explicit source S of Eq. FluxCurr1_A; rhs of Eq. Main_Eq_A is -e_z x S =
 // (S_y, -S_x)
-__device__ void phase_assemble2(const EngineArgs &A, Thr T) {
+template <typename P>
+__device__ void phase_assemble2(const EngineArgs &A, const PS<P> &Q, const double *ncur, Thr T,
+                                const Guess &g) {
     const int n = A.N, nn = n * n;
     const double inv2h = 0.5 * A.inv_h;
     double sbx = 0.0, sby = 0.0;
     for (int i = T.t0; i < nn; i += T.nt) {
         const int iy = i / n, ix = i - iy * n;
+        if (g.active) {
+            apply_guess(A.bx, A.hist1[3], A.hist2[3], i, g);
+            apply_guess(A.by, A.hist1[4], A.hist2[4], i, g);
+        }
         double a = 1.0 + A.psi[i];
         if (a < A.psi_floor) a = A.psi_floor;
-        const double jx = A.jx[i], jy = A.jy[i], txx = A.txx[i], txy = A.txy[i],
-                     tyy = A.tyy[i], G = A.G[i], ez = A.ez[i], bz = A.bz[i];
+        const double jx = Q.jx[i], jy = Q.jy[i], txx = Q.txx[i], txy = Q.txy[i],
+                     tyy = Q.tyy[i], G = g_total(Q.G, ncur, i), ez = A.ez[i], bz = A.bz[i];
         const double gx = A.dpx[i], gy = A.dpy[i];
-        double sx = dx0(A.jz, n, ix, i, inv2h) - dx0(A.txx, n, ix, i, inv2h) -
-                    dy0(A.txy, n, iy, i, inv2h) - jy * bz / a + G * gx / (a * a) - jx * ez / a -
+        double sx = dx0(A.jz, n, ix, i, inv2h) - dx0(Q.txx, n, ix, i, inv2h) -
+                    dy0(Q.txy, n, iy, i, inv2h) - jy * bz / a + G * gx / (a * a) - jx * ez / a -
                     (txx * gx + txy * gy) / a;
-        double sy = dy0(A.jz, n, iy, i, inv2h) - dx0(A.txy, n, ix, i, inv2h) -
-                    dy0(A.tyy, n, iy, i, inv2h) + jx * bz / a + G * gy / (a * a) - jy * ez / a -
+        double sy = dy0(A.jz, n, iy, i, inv2h) - dx0(Q.txy, n, ix, i, inv2h) -
+                    dy0(Q.tyy, n, iy, i, inv2h) + jx * bz / a + G * gy / (a * a) - jy * ez / a -
                     (txy * gx + tyy * gy) / a;
         A.f_bx[i] = sy;
         A.f_by[i] = -sx;
@@ -595,9 +707,10 @@ __device__ void phase_assemble2(const EngineArgs &A, Thr T) {
 }
 
 // store the base slice; push every trajectory (Eqs. EoM_112_A, EoM_111);
-// deposit n_* of the next slice; V_max
-__device__ void phase_push(const EngineArgs &A, double *nnext, bool base, bool last, int j,
-                           double dxi, int pk, Thr T) {
+// deposit n_* of the next slice; V_max.  gamma is evaluated in float64.
+template <typename P>
+__device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, bool base,
+                           bool last, int j, double dxi, int pk, Thr T) {
     const int nn = A.N * A.N;
     if (base) {
         double *h0 = A.hist + (size_t)j * nn;
@@ -612,44 +725,45 @@ __device__ void phase_push(const EngineArgs &A, double *nnext, bool base, bool l
     }
     if (last) return;
     const double s = A.inv_h * A.inv_h;
-    const double half = 0.5 * dxi;
+    const P half = (P)(0.5 * dxi), dxp = (P)dxi;
     unsigned hits = 0;
     double vmax = 0.0;
     for (int64_t p = T.t0; p < A.np; p += T.nt) {
-        const double x = A.x[p], y = A.y[p];
-        Cic c = cic_stencil(x, y, A.x_min, A.y_min, A.h, A.N);
-        double a = guard(1.0 + cic_gather(A.psi, c), A.psi_floor, hits);
-        const double gx = cic_gather(A.dpx, c), gy = cic_gather(A.dpy, c);
-        const double bx = cic_gather(A.bx, c), by = cic_gather(A.by, c),
-                     bz = cic_gather(A.bz, c);
-        double px = A.px[p], py = A.py[p];
+        const double x = Q.x[p], y = Q.y[p];
+        const Cic cd = cic_stencil(x, y, A.x_min, A.y_min, A.h, A.N);
+        const CicP<P> c = cic_p<P>(cd);
+        const double a = guard(1.0 + cic_gather(A.psi, cd), A.psi_floor, hits);
+        const P ap = (P)a;
+        const P gx = gat<P>(A.dpx, c), gy = gat<P>(A.dpy, c);
+        const P bx = gat<P>(A.bx, c), by = gat<P>(A.by, c), bz = gat<P>(A.bz, c);
+        P px = Q.px[p], py = Q.py[p];
         // half kick: gamma grad psi / (1+psi) + e_z x B_perp
-        double gam = (1.0 + px * px + py * py + a * a) / (2.0 * a);
-        double pxm = px + half * (gam * gx / a - by);
-        double pym = py + half * (gam * gy / a + bx);
+        const double gam = (1.0 + (double)px * px + (double)py * py + a * a) / (2.0 * a);
+        const P pxm = px + half * ((P)gam * gx / ap - by);
+        const P pym = py + half * ((P)gam * gy / ap + bx);
         // rotation by the B_z term (e_z x p) B_z / (1+psi)
-        double tau = half * bz / a;
-        double pxp = pxm - tau * pym;
-        double pyp = pym + tau * pxm;
-        double sr = 2.0 * tau / (1.0 + tau * tau);
-        double pxr = pxm - sr * pyp;
-        double pyr = pym + sr * pxp;
-        double gam2 = (1.0 + pxr * pxr + pyr * pyr + a * a) / (2.0 * a);
-        px = pxr + half * (gam2 * gx / a - by);
-        py = pyr + half * (gam2 * gy / a + bx);
-        double nx = x + dxi * px / a;
-        double ny = y + dxi * py / a;
+        const P tau = half * bz / ap;
+        const P pxp = pxm - tau * pym;
+        const P pyp = pym + tau * pxm;
+        const P sr = P(2) * tau / (P(1) + tau * tau);
+        const P pxr = pxm - sr * pyp;
+        const P pyr = pym + sr * pxp;
+        const double gam2 = (1.0 + (double)pxr * pxr + (double)pyr * pyr + a * a) / (2.0 * a);
+        px = pxr + half * ((P)gam2 * gx / ap - by);
+        py = pyr + half * ((P)gam2 * gy / ap + bx);
+        double nx = x + (double)(dxp * px / ap);
+        double ny = y + (double)(dxp * py / ap);
         if (nx > A.x_max) { nx = 2.0 * A.x_max - nx; px = -px; }
         if (nx < A.x_min) { nx = 2.0 * A.x_min - nx; px = -px; }
         if (ny > A.y_max) { ny = 2.0 * A.y_max - ny; py = -py; }
         if (ny < A.y_min) { ny = 2.0 * A.y_min - ny; py = -py; }
-        A.x[p] = nx;
-        A.y[p] = ny;
-        A.px[p] = px;
-        A.py[p] = py;
-        vmax = fmax(vmax, sqrt(px * px + py * py) / a);
-        Cic c2 = cic_stencil(nx, ny, A.x_min, A.y_min, A.h, A.N);
-        cic_deposit(nnext, c2, A.w[p] * s);
+        Q.x[p] = nx;
+        Q.y[p] = ny;
+        Q.px[p] = px;
+        Q.py[p] = py;
+        vmax = fmax(vmax, sqrt((double)px * px + (double)py * py) / a);
+        const Cic c2 = cic_stencil(nx, ny, A.x_min, A.y_min, A.h, A.N);
+        cic_deposit(nnext, c2, Q.wd[p] * s);
     }
     add_hits(A.sc, hits);
     vmax = block_max(vmax);
@@ -659,18 +773,12 @@ __device__ void phase_push(const EngineArgs &A, double *nnext, bool base, bool l
     }
 }
 
+// One 3D step of one instance on `nblk` blocks (this one is `bid`): the xi
+// loop of Algorithm 1.  Returns false if a barrier failed (the error word of
+// the instance says why).
 template <bool REF>
-__global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs A) {
-    extern __shared__ double smem[];
-    const int bid = blockIdx.x, nblk = gridDim.x;
-    __shared__ unsigned long long s_epoch;
-    __shared__ int s_inv_ready[2];
-    if (threadIdx.x == 0) {
-        s_epoch = 0ull;
-        s_inv_ready[0] = s_inv_ready[1] = 0;
-    }
-    __syncthreads();
-    const Sync S{A.sc, (unsigned)nblk, A.spin_cycles, A.trace, A.trace_cap, &s_epoch};
+__device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, void *smem,
+                         int *s_inv_ready) {
     if (A.trace && bid == 0 && threadIdx.x == 0) {
         A.trace[0] = 0;
         A.trace[1] = global_ns();
@@ -680,9 +788,18 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs 
     const Thr T = grid_thr(bid, nblk);
     const bool lead = (bid == 0 && threadIdx.x == 0);
 
-    double *ncur = A.n_a, *nnext = A.n_b;
-    phase_deposit_n(A, ncur, T);
-    if (!S(1)) return;
+    using P = typename std::conditional<REF, float, double>::type;
+    PS<P> Q;
+    if constexpr (REF) {
+        Q = PS<P>{A.x, A.y, A.px32, A.py32, A.w32, A.w, A.n_a, A.n_b,
+                  A.jx32, A.jy32, A.txx32, A.txy32, A.tyy32, A.G32};
+    } else {
+        Q = PS<P>{A.x, A.y, A.px, A.py, A.w, A.w, A.n_a, A.n_b,
+                  A.jx, A.jy, A.txx, A.txy, A.tyy, A.G};
+    }
+    double *ncur = Q.na, *nnext = Q.nb;
+    phase_deposit_n<P>(A, Q, ncur, T);
+    if (!S(1)) return false;
 
     const SolveSpec Vpsi{1, 0, {A.psi, nullptr}, {A.f_psi, nullptr}, false};
     const SolveSpec Veb{2, 1, {A.ez, A.bz}, {A.f_ez, A.f_bz}, false};
@@ -690,6 +807,8 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs 
 
     int m = A.m_sched ? A.m_sched[0] : 1;
     int slot = 0, pk = 0;
+    int have = 0;                        // previous solutions available for the guess
+    double gx0 = 0.0, gx1 = 0.0, gx2 = 0.0;  // their xi
     for (int j = 0; j < A.n_xi; ++j) {
         if (lead) {
             A.diag_m[j] = m;
@@ -699,18 +818,20 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs 
         const double dxi = A.dxi0 / m;
         for (int q = 0; q < m; ++q) {
             const bool base = (q == 0);
-            phase_psi_rhs(A, ncur, nnext, base, j, T);
-            if (!S(2)) return;
-            if (!mg_solve<REF>(A, S, Vpsi, slot, bid, nblk, smem, s_inv_ready)) return;
-            phase_moments(A, T);
-            if (!S(3)) return;
-            phase_assemble1(A, ncur, j, q, m, T);
-            if (!S(4)) return;
-            if (!mg_solve<REF>(A, S, Veb, slot, bid, nblk, smem, s_inv_ready)) return;
-            phase_assemble2(A, T);
-            if (!S(5)) return;
-            if (!mg_solve<REF>(A, S, Vbp, slot, bid, nblk, smem, s_inv_ready)) return;
-            phase_push(A, nnext, base, last, j, dxi, pk, T);
+            const double xs = j * A.dxi0 + q * dxi;  // xi of this slice (from xi_min)
+            const Guess g = make_guess(A.ws_order, have, xs, gx0, gx1, gx2);
+            phase_psi_rhs<P>(A, Q, ncur, nnext, base, j, T, g);
+            if (!S(2)) return false;
+            if (!mg_solve<REF>(A, S, Vpsi, slot, bid, nblk, smem, s_inv_ready)) return false;
+            phase_moments<P>(A, Q, T);
+            if (!S(3)) return false;
+            phase_assemble1<P>(A, Q, ncur, j, q, m, T, g);
+            if (!S(4)) return false;
+            if (!mg_solve<REF>(A, S, Veb, slot, bid, nblk, smem, s_inv_ready)) return false;
+            phase_assemble2<P>(A, Q, ncur, T, g);
+            if (!S(5)) return false;
+            if (!mg_solve<REF>(A, S, Vbp, slot, bid, nblk, smem, s_inv_ready)) return false;
+            phase_push<P>(A, Q, nnext, base, last, j, dxi, pk, T);
             if (lead) {
                 sc->slices += 1;
                 if (!last) {
@@ -721,7 +842,11 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs 
                 sc->fnorm[1][0] = sc->fnorm[1][1] = 0.0;
                 sc->fnorm[2][0] = sc->fnorm[2][1] = 0.0;
             }
-            if (!S(6)) return;
+            if (!S(6)) return false;
+            gx2 = gx1;
+            gx1 = gx0;
+            gx0 = xs;
+            have = min(have + 1, 3);
             if (last) break;
             double *t = ncur;
             ncur = nnext;
@@ -739,6 +864,62 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs 
             double r = ceil(vm / A.V0);
             m = r > (double)A.refine_k ? A.refine_k : (int)r;
             if (m < 1) m = 1;
+        }
+    }
+    return true;
+}
+
+template <bool REF>
+__global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(EngineArgs A) {
+    extern __shared__ double smem[];
+    __shared__ unsigned long long s_epoch;
+    __shared__ int s_inv_ready[2];
+    if (threadIdx.x == 0) {
+        s_epoch = 0ull;
+        s_inv_ready[0] = s_inv_ready[1] = 0;
+    }
+    __syncthreads();
+    const Sync S{A.sc, &A.sc->bar_arrive, gridDim.x, A.spin_cycles, A.trace, A.trace_cap,
+                 &s_epoch, blockIdx.x == 0};
+    run_step<REF>(A, blockIdx.x, gridDim.x, S, smem, s_inv_ready);
+}
+
+// Batched form: the launch is split into teams of `team` consecutive blocks;
+// each team takes the next instance from a device-side queue, runs its whole
+// 3D step behind the team's own barrier, and repeats until the queue is
+// empty.  Instances may differ in size, tiles and sweeps.
+template <bool REF>
+__global__ void __launch_bounds__(QS_ENGINE_THREADS, 1)
+    slice_engine_batched(const EngineArgs *list, int n_inst, int team, BatchState *bs) {
+    extern __shared__ double smem[];
+    __shared__ unsigned long long s_epoch;
+    __shared__ int s_inv_ready[2];
+    __shared__ EngineArgs sA;
+    const int tid = blockIdx.x / team, bid = blockIdx.x % team;
+    if (threadIdx.x == 0) s_epoch = 0ull;
+    __syncthreads();
+    for (;;) {
+        if (bid == 0 && threadIdx.x == 0) {
+            bs->team_inst[tid] = atomicAdd(&bs->next, 1);
+            __threadfence();
+        }
+        // team barrier on the team's counter (errors of a finished instance do
+        // not concern the next one, so this one checks the batch error word)
+        const Sync T0{&bs->sc, &bs->team_bar[tid], (unsigned)team, list[0].spin_cycles, nullptr,
+                      0, &s_epoch, false};
+        if (!T0(60)) return;
+        const int idx = vload(&bs->team_inst[tid]);
+        if (idx >= n_inst) return;
+        for (int k = threadIdx.x; k < (int)(sizeof(EngineArgs) / 4); k += blockDim.x)
+            ((int *)&sA)[k] = ((const int *)(list + idx))[k];
+        if (threadIdx.x == 0) s_inv_ready[0] = s_inv_ready[1] = 0;
+        __syncthreads();
+        const Sync S{sA.sc, &bs->team_bar[tid], (unsigned)team, sA.spin_cycles, nullptr, 0,
+                     &s_epoch, false};
+        if (!run_step<REF>(sA, bid, team, S, smem, s_inv_ready)) {
+            // the instance failed: its blocks stop; record it for the batch
+            if (bid == 0 && threadIdx.x == 0) atomicCAS(&bs->sc.err, 0, vload(&sA.sc->err));
+            return;
         }
     }
 }
@@ -778,12 +959,46 @@ size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int p
     return total + 256;
 }
 
+cudaError_t qs_launch_engine_batched(cudaStream_t st, const EngineArgs *list, int n_inst,
+                                     int precision, int team, int teams, BatchState *bs,
+                                     size_t smem_bytes) {
+    void *args[] = {(void *)&list, &n_inst, &team, &bs};
+    const void *fn = precision == QS_FP32_REFINED ? (const void *)slice_engine_batched<true>
+                                                  : (const void *)slice_engine_batched<false>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
+        cudaSuccess)
+        return cudaGetLastError();
+    return cudaLaunchCooperativeKernel(fn, dim3(team * teams), dim3(QS_ENGINE_THREADS), args,
+                                       smem_bytes, st);
+}
+
+int qs_engine_batched_max_blocks(int device, int precision, size_t smem_bytes, int *blocks) {
+    const void *fn = precision == QS_FP32_REFINED ? (const void *)slice_engine_batched<true>
+                                                  : (const void *)slice_engine_batched<false>;
+    int per_sm = 0, sms = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
+        cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QS_ENGINE_THREADS,
+                                                      smem_bytes) != cudaSuccess)
+        return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return -1;
+    *blocks = per_sm * sms;
+    return 0;
+}
+
 cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_blocks,
                              size_t smem_bytes) {
     EngineArgs copy = a;
     void *args[] = {&copy};
     const void *fn = a.precision == QS_FP32_REFINED ? (const void *)slice_engine<true>
                                                     : (const void *)slice_engine<false>;
+    // the limit is a property of the kernel, shared by every context: set it
+    // for this launch (another context may have set a smaller one)
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(fn, dim3(grid_blocks), dim3(QS_ENGINE_THREADS), args,
                                        smem_bytes, st);
 }

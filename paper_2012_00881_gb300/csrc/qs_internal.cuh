@@ -31,6 +31,16 @@ struct DevScalars {
     unsigned long long trace_n;
 };
 
+// Device state of a batched launch: the instance queue, one barrier counter
+// and current instance per team, and a batch-wide error word.
+#define QS_MAX_TEAMS 1024
+struct BatchState {
+    int next;                       // next instance to hand out
+    int team_inst[QS_MAX_TEAMS];    // instance each team is working on
+    unsigned long long team_bar[QS_MAX_TEAMS];
+    DevScalars sc;                  // error word of the team barriers
+};
+
 // one grid level of a multigrid hierarchy (float64 levels, and the float32
 // levels of the refined form's inner cycles)
 struct LevelArrays {
@@ -61,15 +71,21 @@ struct EngineArgs {
     int nu1, nu2;
     int64_t np;
     long long spin_cycles;
-    // plasma macroparticles (working copy)
+    // plasma macroparticles (working copy; the refined form keeps positions
+    // in float64 and momenta and weights in float32)
     double *x, *y, *px, *py, *w;
+    float *px32, *py32, *w32;
     // deposited grids
     double *n_a, *n_b, *n_ion;
     double *jx, *jy, *txx, *txy, *tyy, *G;
+    float *jx32, *jy32, *txx32, *txy32, *tyy32, *G32;  // refined form (G32: n_* <gamma - 1>)
     // level-0 fields (multigrid unknowns) and right-hand sides
     double *psi, *ez, *bz, *bx, *by;
     double *f_psi, *f_ez, *f_bz, *f_bx, *f_by;
     double *dpx, *dpy, *jz, *kap, *invd0;
+    // warm start: solutions one and two slices back (psi, Ez, Bz, Bx, By)
+    double *hist1[5], *hist2[5];
+    int ws_order;
     // coarse levels 1..nlev-1 (scratch shared by the three solves)
     int nlev;
     int lev_n[QS_MAX_LEV];
@@ -181,12 +197,18 @@ cudaError_t qs_launch_beam_deposit(cudaStream_t st, const qs_beam &b, int n, dou
 cudaError_t qs_launch_beam_push(cudaStream_t st, const qs_beam &b, int n, double x_min,
                                 double x_max, double y_min, double y_max, double h, int n_xi,
                                 double xi_min, double dxi0, const double *hist, double dt);
+cudaError_t qs_launch_convert(cudaStream_t st, const double *src, float *dst, int64_t n);
+cudaError_t qs_launch_widen(cudaStream_t st, const float *src, double *dst, int64_t n);
 cudaError_t qs_launch_cell_sort(cudaStream_t st, const double *x, const double *y,
                                 const int32_t *id, int64_t np, int n, double x_min,
                                 double y_min, double h, int32_t *cell, int32_t *count,
                                 int32_t *offset, int32_t *cursor, int32_t *perm);
 cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_blocks,
                              size_t smem_bytes);
+cudaError_t qs_launch_engine_batched(cudaStream_t st, const EngineArgs *list, int n_inst,
+                                     int precision, int team, int teams, BatchState *bs,
+                                     size_t smem_bytes);
+int qs_engine_batched_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
 int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
                             int tile_x, int tile_y, int nu, size_t *block_offset,

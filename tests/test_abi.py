@@ -46,7 +46,8 @@ def test_default_config_through_the_abi(lib):
     assert cfg.x_min == -6.0 and cfg.xi_max == 12.0 and cfg.n_xi == 128
     assert cfg.max_psi_guard_hits == -1 and cfg.sort_every == 16
     assert cfg.pre_sweeps == 2 and cfg.post_sweeps == 2 and cfg.coarse_block_n == 0
-    assert cfg.trace_capacity == 0 and list(cfg.reserved) == [0] * 6
+    assert cfg.trace_capacity == 0 and cfg.warm_start_order == 2
+    assert cfg.tile_x == 0 and cfg.tile_y == 0 and list(cfg.reserved) == [0] * 3
 
 
 def test_status_strings(lib):
@@ -63,7 +64,8 @@ def test_invalid_config_rejected_without_gpu(lib):
     l = qs.load_library()
     h = ctypes.c_void_p()
     for bad in (dict(nx=64, ny=32), dict(nx=100, ny=100), dict(refine_k=0),
-                dict(precision=7), dict(mg_tol=0.0), dict(x_max=7.0)):
+                dict(precision=7), dict(mg_tol=0.0), dict(x_max=7.0), dict(tile_x=7, tile_y=8),
+                dict(warm_start_order=3)):
         cfg = qs.default_config(**bad)
         assert l.qs_create(ctypes.byref(cfg), None, ctypes.byref(h)) == qs.QS_ERR_ARG, bad
     assert l.qs_create(None, None, ctypes.byref(h)) == qs.QS_ERR_ARG

@@ -1,0 +1,125 @@
+"""Full-size and edge-case parity of the CUDA path against the FP64 oracle (GPU).
+
+At the benchmark sizes the GPU runs the whole window exactly as the
+benchmark does; the oracle (about one second per slice at 256^2) computes the
+first base slices, which depend only on what came before them (the xi loop
+is causal), so they are compared element by element.  Over the whole window
+the properties that hold at any size are checked: charge conservation on
+every slice (Eq. continuity), the refinement rule (Alg. 1), slice counts.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# relative L2 per field: 1e-9 for float64, 2e-5 for the refined form (float32
+# particles and smoothing, float64 residuals); plus an absolute floor of 1e-13
+# RMS per element for slices ahead of the driver, where the fields are at the
+# rounding level
+TOL = {"fp64": 1e-9, "fp32r": 2e-5}
+ABS_RMS = 1e-13
+
+
+def _prefix_parity(qs, wl, form, n_prefix, tol):
+    beams_np = [W.sample_beam(b) for b in wl.beams]
+    ctx = qs.Context(qs.config_from_workload(wl, precision=form, mg_tol=1e-12))
+    if wl.profile is None:
+        ctx.init_plasma(wl.ppc)
+    else:
+        ctx.init_plasma(wl.ppc, wl.profile[0], wl.profile[1])
+    st = ctx.step3d([qs.Beam(b) for b in beams_np])
+    got = ctx.fields(qs.FIELD_ALL, 0, n_prefix, device=False).numpy()
+    m, vmax, charge = ctx.slice_diagnostics()
+    cfg = O.config_from_workload(wl)
+    pl, n_ion = O.plasma_from_workload(wl)
+    ref = O.step3d(cfg, pl, n_ion, beams_np, n_slices=n_prefix)
+    scale = np.linalg.norm(ref.history[0])
+    floor = ABS_RMS * np.sqrt(ref.history[0].size)
+    errs = {name: np.linalg.norm(got[i] - ref.history[i]) / max(np.linalg.norm(ref.history[i]), scale, floor / tol)
+            for i, name in enumerate(O.FIELD_NAMES)}
+    assert max(errs.values()) < tol, errs
+    # whole window: every slice conserves the plasma charge (float32
+    # deposits in the refined form round at 1e-7)
+    wsum = pl.w.sum()
+    assert np.max(np.abs(charge - wsum)) < (1e-10 if form == "fp64" else 1e-6) * wsum
+    # refinement rule and slice bookkeeping over the whole window
+    v0 = cfg.grid.h / cfg.dxi0
+    for j in range(1, wl.n_xi):
+        assert m[j] == O.refine_m(vmax[j - 1], v0, wl.refine_k)
+    assert st["slices"] == wl.n_xi + int((m[:-1] - 1).sum())
+    assert st["psi_guard_hits"] == 0
+    return st
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32r"])
+def test_blowout256_full_window_prefix_parity(qs, form):
+    """256^2, 1024 slices, 262,144 plasma particles, 700k beam particles."""
+    _prefix_parity(qs, W.workload("blowout256"), form, 12, TOL[form])
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32r"])
+def test_blowout256_driver_at_head_prefix_parity(qs, form):
+    """Full 256^2 size with the driver moved to the window head, so that the
+    slices the oracle can afford cover the driver and its wake."""
+    wl = W.workload("blowout256")
+    wl = wl.with_(beams=tuple(b.with_(xi_c=b.xi_c - 2.0) for b in wl.beams))
+    _prefix_parity(qs, wl, form, 24, TOL[form])
+
+
+def test_blowout512_full_window_prefix_parity(qs):
+    """512^2, 2048 slices, 9 ppc (2.36M particles), parabolic channel, 2M-particle driver."""
+    _prefix_parity(qs, W.workload("blowout512"), "fp32r", 3, TOL["fp32r"])
+
+
+@pytest.mark.parametrize("n,half,ppc", [(48, 4.0, 4), (40, 5.0, 1), (24, 3.0, 9)])
+def test_ragged_grids_and_lattices(qs, n, half, ppc):
+    """Sides whose coarsening ends at 3 or 5 cells, and 1 or 9 particles per cell."""
+    wl = W.Workload(name="r", n=n, half_width=half, n_xi=20, xi_len=5.0, ppc=ppc,
+                    beams=(W.BeamSpec(amplitude=2.0, sigma_x=0.5, sigma_y=0.5, sigma_z=0.6,
+                                      xi_c=1.8, n_particles=8000, seed=5),))
+    for form in ("fp64", "fp32r"):
+        _prefix_parity(qs, wl, form, 20, TOL[form])
+
+
+def test_no_driver_gives_zero_wake(qs):
+    wl = W.workload("linear64").with_(n_xi=16, xi_len=1.5)
+    ctx = qs.Context(qs.config_from_workload(wl))
+    ctx.init_plasma(4)
+    st = ctx.step3d([])
+    f = ctx.fields(qs.FIELD_ALL, device=False).numpy()
+    assert np.max(np.abs(f)) < 1e-12
+    assert st["slices"] == 16
+
+
+def test_single_slice_and_no_refinement(qs):
+    wl = W.workload("linear64").with_(n_xi=1, xi_len=0.1, refine_k=1)
+    beams_np = [W.sample_beam(b.with_(xi_c=0.05)) for b in wl.beams]
+    ctx = qs.Context(qs.config_from_workload(wl, mg_tol=1e-12))
+    ctx.init_plasma(4)
+    st = ctx.step3d([qs.Beam(b) for b in beams_np])
+    assert st["slices"] == 1 and st["pushes"] == 0
+    got = ctx.fields(qs.FIELD_ALL | qs.FIELD_JZB, device=False).numpy()
+    cfg = O.config_from_workload(wl)
+    pl, n_ion = O.plasma_from_workload(wl)
+    ref = O.step3d(cfg, pl, n_ion, beams_np)
+    jzb = O.deposit_beam(cfg, beams_np)
+    assert np.linalg.norm(got[5] - jzb) <= 1e-13 * np.linalg.norm(jzb)
+    assert np.linalg.norm(got[:5] - ref.history) <= 1e-9 * max(np.linalg.norm(ref.history), 1e-30)
+
+
+def test_warm_start_orders_agree(qs):
+    """The initial guess changes only the iteration count, not the solution."""
+    wl = W.workload("linear64")
+    beams = [qs.Beam(W.sample_beam(b)) for b in wl.beams]
+    out = []
+    for order in (0, 1, 2):
+        ctx = qs.Context(qs.config_from_workload(wl, mg_tol=1e-12, warm_start_order=order))
+        ctx.init_plasma(4)
+        st = ctx.step3d(beams)
+        out.append((ctx.fields(qs.FIELD_ALL, device=False).numpy(), st))
+    base = out[0][0]
+    for f, _ in out[1:]:
+        assert np.linalg.norm(f - base) <= 1e-9 * np.linalg.norm(base)
