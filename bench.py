@@ -364,6 +364,7 @@ def run_batched(args):
     tuned = AT.tune(insts, precision="fp32r", n_slices=16,
                     cands=AT.candidates(tiles=((32, 16), (64, 32)), sweeps=((2, 2),),
                                         coarse=(16, 32)))
+    team = AT.tune_team(insts, tuned, precision="fp32r", n_slices=16)
     tune_s = time.perf_counter() - t0
     beams_np = [[W.sample_beam(b) for b in wl.beams] for wl in insts]
     ctxs, beams, master = [], [], []
@@ -381,7 +382,7 @@ def run_batched(args):
                     b.t[k].copy_(a.t[k])
 
     def one_step():
-        st = qs.step3d_batched(ctxs, beams)
+        st = qs.step3d_batched(ctxs, beams, team_blocks=team)
         for c, b, wl in zip(ctxs, beams, insts):
             c.push_beam(b, wl.dt)
         return st
@@ -457,6 +458,7 @@ def run_batched(args):
                                "sigma_r 0.3..0.8, sigma_z 0.7, 100k), refined form, one batched "
                                "launch per 3D step",
                    "form": "fp32r-batched", "tuned": {str(k): v for k, v in tuned.items()},
+                   "team_blocks": team,
                    "tune_seconds": tune_s,
                    "l2": "history and beam grids larger than L2; 256 MB write between steps"},
         "pushes_per_s": pushes * world / (total_ms / 1e3),

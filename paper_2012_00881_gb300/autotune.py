@@ -8,7 +8,10 @@ keeps the fastest:
 * the red-black sweeps before and after the coarse correction (pre_sweeps,
   post_sweeps),
 * the side below which a level is relaxed by one thread block
-  (coarse_block_n).
+  (coarse_block_n),
+
+and, for the whole batch, the number of thread blocks per team
+(tune_team).
 
 Every candidate solves to the same residual tolerance, so the choice changes
 only the time, not the result.  A candidate is timed on a batch of the
@@ -42,13 +45,16 @@ def _truncated(wl, n_slices: int):
 
 
 def time_candidate(wls: Sequence, cand: Dict, n_slices: int, precision: str,
-                   beams_cache: Dict, repeats: int = 2) -> float:
-    """Device milliseconds per computed slice of a truncated batched step."""
+                   beams_cache: Dict, repeats: int = 2, team_blocks: int = 0,
+                   per_size: Dict = None) -> float:
+    """Device milliseconds per computed slice of a truncated batched step
+    (settings `cand` for every instance, or per size from `per_size`)."""
     ctxs, beams = [], []
     try:
         for wl in wls:
             w2 = _truncated(wl, n_slices)
-            cfg = B.config_from_workload(w2, precision=precision, **cand)
+            over = apply(wl, per_size) if per_size else cand
+            cfg = B.config_from_workload(w2, precision=precision, **over)
             ctx = B.Context(cfg)
             if w2.profile is None:
                 ctx.init_plasma(w2.ppc)
@@ -65,9 +71,9 @@ def time_candidate(wls: Sequence, cand: Dict, n_slices: int, precision: str,
             c.close()
         return float("inf")
     best = float("inf")
-    B.step3d_batched(ctxs, beams)  # warm-up (also fills the coarse inverses)
+    B.step3d_batched(ctxs, beams, team_blocks=team_blocks)  # warm-up
     for _ in range(repeats):
-        st = B.step3d_batched(ctxs, beams)
+        st = B.step3d_batched(ctxs, beams, team_blocks=team_blocks)
         slices = sum(s["slices"] for s in st)
         best = min(best, st[0]["gpu_ms"] / max(slices, 1))
     for c in ctxs:
@@ -95,6 +101,21 @@ def tune(wls: Sequence, precision: str = "fp32r", n_slices: int = 16,
         t, best = min(scored, key=lambda x: x[0])
         result[n] = dict(best, ms_per_slice=t)
     return result
+
+
+def tune_team(wls: Sequence, per_size: Dict, precision: str = "fp32r", n_slices: int = 16,
+              teams: Sequence[int] = (0, 6, 12, 19), verbose: bool = False) -> int:
+    """Blocks per team (0 = one team per instance) that minimise the time of
+    the whole truncated batch with the per-size settings `per_size`."""
+    beams_cache: Dict = {}
+    scored = []
+    for tb in teams:
+        t = time_candidate(wls, {}, n_slices, precision, beams_cache, team_blocks=tb,
+                           per_size=per_size)
+        scored.append((t, tb))
+        if verbose:
+            print(f"team_blocks={tb} -> {t:.4f} ms/slice", flush=True)
+    return min(scored)[1]
 
 
 def apply(wl, tuned: Dict) -> Dict:
