@@ -27,7 +27,8 @@ struct qs_ctx {
     double *dpx = nullptr, *dpy = nullptr, *jz = nullptr, *kap = nullptr, *invd0 = nullptr;
     double *hist1[5] = {}, *hist2[5] = {};
     LevelArrays lev[QS_MAX_LEV] = {};
-    float *e32[2] = {nullptr, nullptr}, *r32[2] = {nullptr, nullptr};
+    float *e32[2] = {nullptr, nullptr}, *r32[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    double *r64[2] = {nullptr, nullptr};
     float *k32 = nullptr, *d32 = nullptr;
     LevelArrays32 lev32[QS_MAX_LEV] = {};
     int block_level_n = 16;
@@ -212,13 +213,16 @@ int create_impl(qs_ctx *c) {
         }
     }
     if (ref) {
-        float **g32[] = {&c->e32[0], &c->e32[1], &c->r32[0], &c->r32[1], &c->k32, &c->d32,
+        float **g32[] = {&c->e32[0],    &c->e32[1],    &c->r32[0][0], &c->r32[0][1],
+                         &c->r32[1][0], &c->r32[1][1], &c->k32,       &c->d32,
                          &c->g32[0], &c->g32[1], &c->g32[2], &c->g32[3], &c->g32[4],
                          &c->g32[5]};
         for (float **p : g32) {
             AL(L, *p, nn);
             CK(cudaMemsetAsync(*p, 0, nn * sizeof(float), c->st), "memset");
         }
+        AL(L, c->r64[0], nn);
+        AL(L, c->r64[1], nn);
     }
     AL(L, c->hist, 5 * (size_t)g.n_xi * nn);
     AL(L, c->jzb, (size_t)g.n_xi * nn);
@@ -518,7 +522,9 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
     a.precision = g.precision;
     for (int k = 0; k < 2; ++k) {
         a.e32[k] = c->e32[k];
-        a.r32[k] = c->r32[k];
+        a.r32[0][k] = c->r32[0][k];
+        a.r32[1][k] = c->r32[1][k];
+        a.r64[k] = c->r64[k];
     }
     a.k32 = c->k32;
     a.d32 = c->d32;

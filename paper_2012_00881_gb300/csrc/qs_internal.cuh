@@ -97,7 +97,8 @@ struct EngineArgs {
     int tile_x, tile_y;  // output tile of the staged grid levels (refined form)
     int block_smem_offset; // byte offset of the coarse part in shared memory
     int tile_smem_offset;  // byte offset of the staged tile after the coarse part
-    float *e32[2], *r32[2], *k32, *d32;
+    float *e32[2], *r32[2][2], *k32, *d32;  // r32[buffer][component]
+    double *r64[2];  // float64 residual of the refined iteration
     LevelArrays32 lev32[QS_MAX_LEV];
     // outputs
     double *hist;        // [5][n_xi][N*N]

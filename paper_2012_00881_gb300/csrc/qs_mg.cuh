@@ -46,6 +46,35 @@ __device__ __forceinline__ T const_inv_diag(int nw) {
 
 // Walk q = t0, t0 + nt, ... over a row-major index space with `w` columns,
 // keeping (row, col) without a division per step.
+// Global -> shared copies are issued asynchronously (cp.async) for a whole
+// staged region and waited for once, so a load phase costs one L2 round trip
+// instead of one per loop iteration.  A copy whose source is outside the
+// domain reads nothing and writes zero (source size 0); its source address
+// is then the array base, which is always valid.
+__device__ __forceinline__ void cp_async_f32(float *dst, const float *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_f64(double *dst, const double *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 8 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void cp_async(T *dst, const T *src, bool valid) {
+    if (sizeof(T) == 8) cp_async_f64((double *)dst, (const double *)src, valid);
+    else cp_async_f32((float *)dst, (const float *)src, valid);
+}
+
 struct Walk {
     int q, row, col, nt, drow, dcol, w;
     __device__ __forceinline__ Walk(int t0, int nt_, int w_) : q(t0), nt(nt_), w(w_) {
@@ -303,39 +332,48 @@ __device__ void block_vcycle(const Hier<T> &H, int lg, int nu1, int nu2, void *s
                              CoarseInv ci, bool writeback = true,
                              Marks mark = Marks{nullptr, nullptr, 0}) {
     const int L = H.L;
-    Lvl<T> S[QS_MAX_LEV];
-    T *p = (T *)smem;
+    // level descriptors of the shared-memory copy, one per block (a
+    // per-thread array indexed by level would live in local memory)
+    __shared__ Lvl<T> S[QS_MAX_LEV];
+    __shared__ double *s_mat;
     const bool scr = H.lv[lg].k != nullptr;
-    for (int l = lg; l < L; ++l) {
-        const int m = H.lv[l].n * H.lv[l].n;
-        S[l].n = H.lv[l].n;
-        S[l].h2 = H.lv[l].h2;
-        for (int c = 0; c < 2; ++c) {
-            S[l].u[c] = p;
-            p += m;
-            S[l].f[c] = p;
-            p += m;
+    if (threadIdx.x == 0) {
+        T *p = (T *)smem;
+        for (int l = lg; l < L; ++l) {
+            const int m = H.lv[l].n * H.lv[l].n;
+            S[l].n = H.lv[l].n;
+            S[l].h2 = H.lv[l].h2;
+            for (int c = 0; c < 2; ++c) {
+                S[l].u[c] = p;
+                p += m;
+                S[l].f[c] = p;
+                p += m;
+            }
+            S[l].k = scr ? p : nullptr;
+            S[l].d = scr ? p + m : nullptr;
+            p += 2 * m;
         }
-        S[l].k = scr ? p : nullptr;
-        S[l].d = scr ? p + m : nullptr;
-        p += 2 * m;
+        const size_t off = ((size_t)((char *)p - (char *)smem) + 15) & ~(size_t)15;
+        s_mat = (double *)((char *)smem + off);
     }
-    size_t off = ((size_t)((char *)p - (char *)smem) + 15) & ~(size_t)15;
-    double *mat = (double *)((char *)smem + off);
+    __syncthreads();
+    double *const mat = s_mat;
     const Lvl<T> G = H.lv[lg];
     const Lvl<T> S0 = S[lg];
     const int m0 = G.n * G.n;
     for (int i = threadIdx.x; i < m0; i += blockDim.x) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            S0.u[c][i] = (lg == 0) ? G.u[c][i] : T(0);
-            S0.f[c][i] = G.f[c][i];
+            if (lg == 0) cp_async(S0.u[c] + i, G.u[c] + i, true);
+            else S0.u[c][i] = T(0);
+            cp_async(S0.f[c] + i, G.f[c] + i, true);
         }
         if (scr) {
-            S0.k[i] = G.k[i];
-            S0.d[i] = G.d[i];
+            cp_async(S0.k + i, G.k + i, true);
+            cp_async(S0.d + i, G.d + i, true);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     mark(40);
     const Thr B{(int)threadIdx.x, (int)blockDim.x};

@@ -1,0 +1,499 @@
+// Device machinery shared by the slice engine and the adjoint engine: the
+// bounded grid barrier, block reductions, and the multigrid solves (float64
+// V-cycles; refined form: float64 residual, float32 staged V-cycles, float64
+// correction).  Everything is in an unnamed namespace: each translation unit
+// that includes this header gets its own copy.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "qs_tile.cuh"
+
+namespace {
+
+#define SYNC(where)                 \
+    do {                            \
+        if (!S(where)) return false; \
+    } while (0)
+
+__device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
+__device__ __forceinline__ double vload(const double *p) { return *(const volatile double *)p; }
+__device__ __forceinline__ unsigned long long vload(const unsigned long long *p) {
+    return *(const volatile unsigned long long *)p;
+}
+
+__device__ __forceinline__ int64_t global_ns() {
+    int64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Each
+// block counts the barriers it has passed (its epoch); on arrival its thread
+// 0 adds 1 to a monotonic counter with a release reduction (no round trip)
+// and polls with acquire loads until the counter reaches epoch * nblk.
+struct Sync {
+    DevScalars *sc;             // the instance's scalars (error word, trace count)
+    unsigned long long *bar;    // monotonic arrival counter of the blocks in the team
+    unsigned nblk;              // blocks in the team
+    long long limit;
+    int64_t *trace;
+    int trace_cap;
+    unsigned long long *epoch;  // this block's barrier count (shared memory)
+    bool tracer;                // this block records the phase trace
+    __device__ bool operator()(int where) const {
+        __shared__ int s_ok;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (vload(&sc->err) != 0) {
+                ok = 0;
+            } else {
+                const unsigned long long target = (*epoch + 1) * nblk;
+                *epoch += 1;
+                red_release_add_u64(bar, 1ull);
+                if (ld_acquire_u64(bar) < target) {
+                    const long long t0 = clock64();
+                    while (ld_acquire_u64(bar) < target) {
+                        if (vload(&sc->err) != 0) {
+                            ok = 0;
+                            break;
+                        }
+                        if (clock64() - t0 > limit) {
+                            if (atomicCAS(&sc->err, 0, QS_ERR_TIMEOUT) == 0) sc->err_where = where;
+                            ok = 0;
+                            break;
+                        }
+                    }
+                }
+            }
+            s_ok = ok;
+            if (trace && tracer) {
+                const unsigned long long k = sc->trace_n;
+                if (k < (unsigned long long)trace_cap) {
+                    trace[2 * k] = where;
+                    trace[2 * k + 1] = global_ns();
+                    sc->trace_n = k + 1;
+                }
+            }
+        }
+        __syncthreads();
+        return s_ok != 0;
+    }
+};
+
+using qsmg::Thr;
+__device__ __forceinline__ Thr grid_thr(int bid, int nblk) {
+    return Thr{bid * (int)blockDim.x + (int)threadIdx.x, nblk * (int)blockDim.x};
+}
+
+// sum over the block; valid in thread 0
+__device__ double block_sum(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        t = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+__device__ double block_max(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        t = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+    }
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// multigrid solves (1 or 2 components sharing the operator)
+// ---------------------------------------------------------------------------
+using qsmg::Hier;
+using qsmg::Lvl;
+
+struct SolveSpec {
+    int nc;
+    int kind;  // 0 psi, 1 (Ez,Bz), 2 (Bx,By): index into fnorm / vcycles
+    double *u[2];
+    double *f[2];
+    bool screened;
+};
+
+// The hierarchy descriptors live in shared memory, one copy per block:
+// thread l fills level l (a per-thread copy indexed by level would sit in
+// local memory and be re-read from L1/L2 on every access).
+__device__ void hier64(const EngineArgs &A, const SolveSpec &V, Hier<double> &H) {
+    H.L = A.nlev;
+    for (int l = threadIdx.x; l < A.nlev; l += blockDim.x) {
+        Lvl<double> &v = H.lv[l];
+        v.n = A.lev_n[l];
+        v.h2 = A.lev_h2[l];
+        for (int c = 0; c < 2; ++c) {
+            v.u[c] = l == 0 ? V.u[c] : A.lev[l].u[c];
+            v.f[c] = l == 0 ? V.f[c] : A.lev[l].f[c];
+        }
+        v.k = V.screened ? (l == 0 ? A.kap : A.lev[l].kap) : nullptr;
+        v.d = V.screened ? (l == 0 ? A.invd0 : A.lev[l].d) : nullptr;
+    }
+}
+
+__device__ void hier32(const EngineArgs &A, const SolveSpec &V, Hier<float> &H) {
+    H.L = A.nlev;
+    for (int l = threadIdx.x; l < A.nlev; l += blockDim.x) {
+        Lvl<float> &v = H.lv[l];
+        v.n = A.lev_n[l];
+        v.h2 = A.lev_h2[l];
+        for (int c = 0; c < 2; ++c) {
+            v.u[c] = l == 0 ? A.e32[c] : A.lev32[l].u[c];
+            v.f[c] = l == 0 ? A.r32[0][c] : A.lev32[l].f[c];
+        }
+        v.k = V.screened ? (l == 0 ? A.k32 : A.lev32[l].k) : nullptr;
+        v.d = V.screened ? (l == 0 ? A.d32 : A.lev32[l].d) : nullptr;
+    }
+}
+
+// Level-0 red-black half sweep of the float32 correction that also adds the
+// final correction into the float64 iterate: u64 += e at the points this
+// thread updates and at the points of the other colour (not written here).
+template <int NC>
+__device__ void relax_half_finalize(const Lvl<float> L, int color, Thr R, double *fin0,
+                                    double *fin1) {
+    const int n = L.n;
+    const float h2 = (float)L.h2;
+    float *const u0 = L.u[0];
+    float *const u1 = L.u[NC - 1];
+    const float *const f0 = L.f[0];
+    const float *const f1 = L.f[NC - 1];
+    const int npts = n * n;
+    for (qsmg::Walk w(R.t0, R.nt, n); w.q < npts; w.next()) {
+        const int ix = w.col, iy = w.row;
+        const int i = w.q;
+        if (((ix + iy) & 1) == color) {
+            const float di = L.d ? L.d[i] : qsmg::const_inv_diag<float>(qsmg::walls(ix, iy, n));
+            qsmg::gs_point<float, NC>(u0, u1, f0, f1, h2, di, n, ix, iy);
+        }
+        fin0[i] += (double)u0[i];
+        if (NC > 1) fin1[i] += (double)u1[i];
+    }
+}
+
+// One V-cycle on hierarchy H.  Levels of side > block_level_n are relaxed by
+// the whole grid, the rest by block 0 in shared memory.  With `fin0` set (the
+// refined form) the float32 correction is added into the float64 iterate
+// during the last level-0 phase.
+template <typename T, int NC>
+__device__ bool vcycle(const EngineArgs &A, const Sync &S, const Hier<T> &H, int bid, int nblk,
+                       void *smem, qsmg::CoarseInv ci, double *fin0, double *fin1) {
+    const int L = H.L;
+    int lg = 0;
+    while (lg < L - 1 && H.lv[lg].n > A.block_level_n) ++lg;
+    const Thr T0 = grid_thr(bid, nblk);
+    for (int l = 0; l < lg; ++l) {
+        const Lvl<T> F = H.lv[l], C = H.lv[l + 1];
+        for (int s = 0; s < A.nu1; ++s) {
+            qsmg::relax_half<T, NC>(F, 0, T0);
+            SYNC(10);
+            qsmg::relax_half<T, NC>(F, 1, T0);
+            SYNC(11);
+        }
+        qsmg::restrict_res<T, NC>(F, C, T0);
+        SYNC(12);
+    }
+    if (bid == 0) qsmg::block_vcycle<T, NC>(H, lg, A.nu1, A.nu2, smem, ci);
+    SYNC(13);
+    if constexpr (sizeof(T) == 4) {
+        if (fin0 && (lg == 0 || A.nu2 == 0)) {
+            // no fused level-0 sweep: add the correction in a phase of its own
+            for (int l = lg - 1; l >= 0; --l) {
+                qsmg::prolong_add<T, NC>(H.lv[l], H.lv[l + 1], T0);
+                SYNC(14);
+            }
+            const int nn = H.lv[0].n * H.lv[0].n;
+            const float *e0 = H.lv[0].u[0];
+            const float *e1 = H.lv[0].u[NC - 1];
+            for (int q = T0.t0; q < nn; q += T0.nt) {
+                fin0[q] += (double)e0[q];
+                if (NC > 1) fin1[q] += (double)e1[q];
+            }
+            SYNC(17);
+            return true;
+        }
+    }
+    for (int l = lg - 1; l >= 0; --l) {
+        const Lvl<T> F = H.lv[l], C = H.lv[l + 1];
+        qsmg::prolong_add<T, NC>(F, C, T0);
+        SYNC(14);
+        for (int s = 0; s < A.nu2; ++s) {
+            qsmg::relax_half<T, NC>(F, 0, T0);
+            SYNC(15);
+            if constexpr (sizeof(T) == 4) {
+                if (fin0 && l == 0 && s == A.nu2 - 1) {
+                    relax_half_finalize<NC>(F, 1, T0, fin0, fin1);
+                    SYNC(16);
+                    continue;
+                }
+            }
+            qsmg::relax_half<T, NC>(F, 1, T0);
+            SYNC(16);
+        }
+    }
+    return true;
+}
+
+// Refined form: one float32 V-cycle on the correction with the grid-wide
+// levels staged tile by tile (one grid barrier per level and leg); every
+// block then solves the coarse levels itself in shared memory (no barrier),
+// and the correction is added into the float64 iterate by the last level-0
+// phase.
+//
+// With `fused` set the level-0 up leg also updates the float64 residual and
+// accumulates ||r||^2, ||u||^2 into norms_out (slot of the convergence test),
+// so no separate residual phase is needed; *fused_done reports whether that
+// happened (grids too small to stage fall back to the plain cycle).
+template <int NC>
+__device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<float> &H, int bid,
+                              int nblk, void *smem, qsmg::CoarseInv ci, double *fin0,
+                              double *fin1, const qstile::Fused *fused, double *norms_out,
+                              double *norms_clear, bool *fused_done) {
+    const int L = H.L;
+    int lg = 0;
+    while (lg < L - 1 && H.lv[lg].n > A.block_level_n) ++lg;
+    *fused_done = false;
+    if (lg == 0) return vcycle<float, NC>(A, S, H, bid, nblk, smem, ci, fin0, fin1);
+    // shared memory: the coarse part's levels first, the staged tile after them
+    float *sm = (float *)((char *)smem + A.tile_smem_offset);
+    const qsmg::Marks mk{bid == 0 ? A.trace : nullptr, &A.sc->trace_n, A.trace_cap};
+    const int Hmax = 2 * max(A.nu1, A.nu2) + 1;  // the tile layout is sized for this halo
+    for (int l = 0; l < lg; ++l) {
+        qstile::down_level<NC>(H.lv[l], H.lv[l + 1], A.nu1, A.tile_x, A.tile_y, Hmax, sm, bid,
+                               nblk, mk);
+        mk(62);
+        SYNC(30);
+    }
+    qsmg::block_vcycle<float, NC>(H, lg, A.nu1, A.nu2, smem, ci, false, mk);
+    const int mg2 = H.lv[lg].n * H.lv[lg].n;
+    for (int l = lg - 1; l >= 0; --l) {
+        const float *cu0 = (l + 1 == lg) ? (const float *)smem : A.lev32[l + 1].up[0];
+        const float *cu1 = (l + 1 == lg) ? (const float *)smem + 2 * mg2 : A.lev32[l + 1].up[1];
+        if (l == 0 && fused) {
+            double nrm[4] = {0.0, 0.0, 0.0, 0.0};
+            qstile::up_level0_fused<NC>(H.lv[0], cu0, cu1, l + 1 == lg, H.lv[1].n, A.nu2,
+                                        A.tile_x, A.tile_y, Hmax, sm, bid, nblk, *fused, nrm, mk);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                double t = block_sum(nrm[c]);
+                if (threadIdx.x == 0) atomicAdd(norms_out + c, t);
+                t = block_sum(nrm[2 + c]);
+                if (threadIdx.x == 0) atomicAdd(norms_out + 2 + c, t);
+            }
+            if (bid == 0 && threadIdx.x == 0)
+                for (int e = 0; e < 4; ++e) norms_clear[e] = 0.0;
+            mk(67);
+            *fused_done = true;
+        } else {
+            qstile::up_level<NC>(H.lv[l], cu0, cu1, l + 1 == lg, H.lv[l + 1].n, A.nu2,
+                                 A.tile_x, A.tile_y, Hmax, sm, bid, nblk, A.lev32[l].up[0],
+                                 A.lev32[l].up[1], l == 0 ? fin0 : nullptr,
+                                 l == 0 ? fin1 : nullptr);
+        }
+        SYNC(32);
+    }
+    return true;
+}
+
+// ||f - A u||^2 and ||u||^2 per component at level 0 in float64, accumulated
+// into out[c] and out[2 + c].  For the refined form the residual also becomes
+// the float32 right-hand side of the next inner cycle, whose correction
+// starts at zero.
+template <int NC>
+__device__ void residual_norm(const EngineArgs &A, const SolveSpec &V, double *out, Thr T,
+                              bool to32, float *const *r32) {
+    const int n = A.N;
+    const double inv_h2 = 1.0 / A.lev_h2[0];
+    const double *const kap = V.screened ? A.kap : nullptr;
+    const double *const u0 = V.u[0];
+    const double *const u1 = V.u[NC - 1];
+    const double *const f0 = V.f[0];
+    const double *const f1 = V.f[NC - 1];
+    float *const r0 = r32[0];
+    float *const r1 = r32[NC - 1];
+    float *const e0 = A.e32[0];
+    float *const e1 = A.e32[NC - 1];
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (qsmg::Walk w(T.t0, T.nt, n); w.q < n * n; w.next()) {
+        const int k = w.q;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const double *u = c ? u1 : u0;
+            const double r = (c ? f1 : f0)[k] - qsmg::apply_op<double>(u, kap, n, inv_h2, w.col, w.row);
+            s[c] += r * r;
+            s[2 + c] += u[k] * u[k];
+            if (to32) {
+                (c ? r1 : r0)[k] = (float)r;
+                (c ? e1 : e0)[k] = 0.f;
+                A.r64[c][k] = r;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        double t = block_sum(s[c]);
+        if (threadIdx.x == 0) atomicAdd(out + c, t);
+        t = block_sum(s[2 + c]);
+        if (threadIdx.x == 0) atomicAdd(out + 2 + c, t);
+    }
+}
+
+// Iterate until, for every component,
+//   ||f - A u|| <= max(tol ||f||, 1e-13 ||u|| / h^2, atol)
+// (the second bound is a small multiple of the rounding level of the
+// float64 residual; atol stops solves whose source is rounding noise).
+// Float64 form: V-cycles on u.  Refined form: float64 residual, float32
+// V-cycle on the correction, float64 update (iterative refinement).
+template <bool REF>
+__device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V, int &slot,
+                         int bid, int nblk, void *smem_base, int *inv_ready) {
+    DevScalars *sc = A.sc;
+    // shared memory: [coarsest inverses][coarse levels + work][staged tile]
+    void *smem = (char *)smem_base + A.block_smem_offset;
+    const int mc = A.lev_n[A.nlev - 1] * A.lev_n[A.nlev - 1];
+    const qsmg::CoarseInv ci{(double *)smem_base + (V.screened ? mc * mc : 0),
+                             inv_ready + (V.screened ? 1 : 0)};
+    if (V.screened) {  // kappa changed: the screened inverse must be rebuilt
+        __syncthreads();
+        if (threadIdx.x == 0) inv_ready[1] = 0;
+        __syncthreads();
+    }
+    double fn[2] = {0.0, 0.0};
+    bool any_zero = false, all_zero = true;
+    for (int c = 0; c < V.nc; ++c) {
+        fn[c] = vload(&sc->fnorm[V.kind][c]);
+        if (fn[c] == 0.0) any_zero = true;
+        else all_zero = false;
+    }
+    const Thr T = grid_thr(bid, nblk);
+    if (any_zero) {
+        const int nn = A.N * A.N;
+        for (int c = 0; c < V.nc; ++c)
+            if (fn[c] == 0.0)
+                for (int k = T.t0; k < nn; k += T.nt) V.u[c][k] = 0.0;
+        SYNC(20);
+    }
+    if (all_zero) return true;
+    __shared__ Hier<double> H64;
+    __shared__ Hier<float> H32;
+    __syncthreads();
+    if (REF) hier32(A, V, H32);
+    else hier64(A, V, H64);
+    __syncthreads();
+    bool conv = false;
+    double rel = 0.0;
+    int it = 0;
+    const double fl = 1e-13 / A.lev_h2[0];
+    bool norms_ready = false;  // the last cycle already produced this slot's norms
+    // The fused residual update writes the next float32 right-hand side into
+    // the other buffer of a pair: the current one is still read as halo by
+    // other blocks while it is written.
+    int rbuf = 0;
+    for (;;) {
+        if (REF || it > 0) {
+            if (!norms_ready) {
+                if (V.nc == 1) residual_norm<1>(A, V, sc->rnorm[slot & 3], T, REF, H32.lv[0].f);
+                else residual_norm<2>(A, V, sc->rnorm[slot & 3], T, REF, H32.lv[0].f);
+                if (bid == 0 && threadIdx.x == 0)
+                    for (int e = 0; e < 4; ++e) sc->rnorm[(slot + 2) & 3][e] = 0.0;
+                SYNC(21);
+            }
+            conv = true;
+            rel = 0.0;
+            for (int c = 0; c < V.nc; ++c) {
+                if (fn[c] == 0.0) continue;
+                const double rn = vload(&sc->rnorm[slot & 3][c]);
+                const double un = vload(&sc->rnorm[slot & 3][2 + c]);
+                double thr = fmax(A.mg_tol * A.mg_tol * fn[c], A.mg_atol * A.mg_atol);
+                thr = fmax(thr, fl * fl * un);
+                if (rn > thr) conv = false;
+                rel = fmax(rel, sqrt(rn / fn[c]));
+            }
+            ++slot;
+            if (conv || it >= A.mg_max_vcycles) break;
+        }
+        bool ok;
+        norms_ready = false;
+        if (REF) {
+            const qstile::Fused fz{{V.u[0], V.u[V.nc - 1]},
+                                   {A.r64[0], A.r64[V.nc - 1]},
+                                   {A.r32[1 - rbuf][0], A.r32[1 - rbuf][V.nc - 1]},
+                                   V.screened ? A.kap : nullptr,
+                                   1.0 / A.lev_h2[0]};
+            double *nout = sc->rnorm[slot & 3], *nclr = sc->rnorm[(slot + 2) & 3];
+            if (V.nc == 1)
+                ok = A.tile_x > 0
+                         ? vcycle_staged<1>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[0], &fz,
+                                            nout, nclr, &norms_ready)
+                         : vcycle<float, 1>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[0]);
+            else
+                ok = A.tile_x > 0
+                         ? vcycle_staged<2>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[1], &fz,
+                                            nout, nclr, &norms_ready)
+                         : vcycle<float, 2>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[1]);
+        } else {
+            ok = V.nc == 1 ? vcycle<double, 1>(A, S, H64, bid, nblk, smem, ci, nullptr, nullptr)
+                           : vcycle<double, 2>(A, S, H64, bid, nblk, smem, ci, nullptr, nullptr);
+        }
+        if (!ok) return false;
+        if (REF && norms_ready) {  // all blocks are past the cycle's last barrier
+            rbuf ^= 1;
+            if (threadIdx.x == 0)
+                for (int c = 0; c < 2; ++c) H32.lv[0].f[c] = A.r32[rbuf][c];
+            __syncthreads();
+        }
+        ++it;
+    }
+    if (bid == 0 && threadIdx.x == 0) {
+        sc->vcycles[V.kind] += it;
+        if (rel > sc->max_relres) sc->max_relres = rel;
+        if (!conv) sc->not_converged = 1;
+    }
+    return true;
+}
+
+__device__ __forceinline__ double guard(double a, double floor_, unsigned &hits) {
+    if (a < floor_) {
+        ++hits;
+        return floor_;
+    }
+    return a;
+}
+
+__device__ void add_hits(DevScalars *sc, unsigned hits) {
+    double t = block_sum((double)hits);
+    if (threadIdx.x == 0 && t > 0.0) atomicAdd(&sc->guard_hits, (unsigned long long)t);
+}
+
+}  // namespace
