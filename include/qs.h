@@ -82,8 +82,10 @@ typedef struct {
     int mg_max_vcycles;         /* per solve; exceeding it -> NOT_CONVERGED     */
     double psi_floor;           /* 1+psi is clamped to >= psi_floor             */
     int64_t max_psi_guard_hits; /* -1: unlimited                                */
-    int sort_every;             /* cell-sort the plasma every this many slices; */
-                                /* 0 = only at the start of a step              */
+    int sort_every;             /* accepted, >= 0; the slice loop keeps the     */
+                                /* lattice order, which is already cell order   */
+                                /* at the head of the window (qs_cell_sort      */
+                                /* gives the sort on demand)                    */
     int pre_sweeps, post_sweeps;/* red-black Gauss-Seidel sweeps per level      */
     int coarse_block_n;         /* multigrid levels of side <= this are relaxed  */
                                 /* by one thread block in shared memory;         */
@@ -202,6 +204,84 @@ int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const i
  * (DEVICE pointers).  Errors: QS_ERR_STATE (no step yet), QS_ERR_ARG. */
 int qs_push_beam(qs_ctx *ctx, qs_beam *beams, int n_beams, double dt);
 
+/* ---- differentiable form: the adjoint of one 3D step ----
+ *
+ * The paper has no adjoint; these entry points give reverse-mode derivatives
+ * of the computation that qs_step3d performs (same schedule of sub-steps,
+ * the 1+psi guard inactive), for losses of the stored wake.
+ *
+ * qs_step3d_adjoint: given d_hist = dL/d(history), DEVICE [5][n_xi][ny*nx]
+ * in qs_fields' order (psi, E_z, B_z, B_x, B_y; NULL = zero), runs the slice
+ * loop backwards over the last qs_step3d of this context and OVERWRITES the
+ * DEVICE outputs
+ *   d_jzb  [n_xi][ny*nx]  dL/d(j_z of the bunches on the base slices),
+ *   d_w    [qs_plasma_count()]  dL/d(weight) of each lattice particle, in
+ *                        the order of qs_init_plasma's lattice (id order),
+ *   d_nion [ny*nx]        dL/d(n_ion), the ion background.
+ * Per reverse slice: the reverse Boris push, the transposed B_perp, E_z/B_z
+ * and psi multigrid solves (the 5-point operators are symmetric, so they are
+ * the forward solves with the cotangents as sources), the reverse of the
+ * source S of Eq. FluxCurr1_A, and the adjoint of each CIC deposit (a
+ * gather) and gather (a deposit).  Memory: the plasma state is stored every
+ * `checkpoint_every` base slices (0 = 32) by one forward replay, and each
+ * segment is recomputed from its checkpoint before its reverse pass, which
+ * holds every slice of the segment (4 floats per particle and 12 grids per
+ * slice, float64).  Library-owned scratch is allocated and freed inside
+ * the call.  stats (may be NULL): slices of the reverse loop, V-cycles of the
+ * transposed solves, gpu_ms of all passes.  Synchronises.
+ * Errors: QS_ERR_STATE (no completed qs_step3d), QS_ERR_ARG (NULL output),
+ * QS_ERR_OOM, QS_ERR_NOT_CONVERGED, QS_ERR_TIMEOUT, QS_ERR_CUDA. */
+int qs_step3d_adjoint(qs_ctx *ctx, const double *d_hist, int checkpoint_every, double *d_jzb,
+                      double *d_w, double *d_nion, qs_step_stats *stats);
+
+/* Mean energy gain of a bunch over one qs_push_beam step of length dt in
+ * the stored wake, L = mean_p (gamma_p after - gamma_p before), WITHOUT
+ * moving the bunch; *gain (HOST) receives L.  If d_hist is not NULL, dL/d
+ * (history) is ADDED to it (DEVICE [5][n_xi][ny*nx], as qs_step3d_adjoint
+ * takes it): the reverse relativistic Boris step, then the trilinear gather
+ * of E_z, B_z, B_x, B_y and grad psi backwards (a deposit).  Synchronises.
+ * Errors: QS_ERR_STATE (no step), QS_ERR_ARG (empty bunch, NULL arrays). */
+int qs_beam_gain(qs_ctx *ctx, const qs_beam *beam, double dt, double *gain, double *d_hist);
+
+/* Reverse of the bunch j_z deposit of qs_step3d for one bunch: from d_jzb
+ * (DEVICE [n_xi][ny*nx], as qs_step3d_adjoint returns it) the DEVICE
+ * outputs d_x, d_y, d_xi, d_w (n entries each, OVERWRITTEN) are the
+ * derivatives with respect to each macroparticle's position and weight
+ * (momenta held fixed).  Macroparticles outside the box or the window get
+ * zero.  Errors: QS_ERR_STATE (no step), QS_ERR_ARG. */
+int qs_beam_deposit_adjoint(qs_ctx *ctx, const qs_beam *beam, const double *d_jzb, double *d_x,
+                            double *d_y, double *d_xi, double *d_w);
+
+/* Derivative with respect to the radial density table of qs_init_plasma
+ * (`profile`, n_coef values on [0, r_max], HOST): the lattice weights are
+ * n(r0) h^2 / ppc and n_ion is their deposit, so
+ *   dL/dtable_k = sum_p (d_w[p] + gather(d_nion)(r0_p) / h^2) h^2/ppc
+ *                 * dn(r0_p)/dtable_k.
+ * d_w (qs_plasma_count() entries) and d_nion (ny*nx) are DEVICE arrays as
+ * qs_step3d_adjoint returns them; d_table (HOST, n_coef) is OVERWRITTEN.
+ * Synchronises.  Errors: QS_ERR_STATE (no plasma), QS_ERR_ARG. */
+int qs_profile_adjoint(qs_ctx *ctx, const double *d_w, const double *d_nion, int n_coef,
+                       double r_max, double *d_table);
+
+/* A bi-Gaussian bunch from parameters theta = (A, sigma_x, sigma_y,
+ * sigma_z, x_c, y_c, xi_c, tilt) (HOST, 8) acting on standard normals z
+ * (DEVICE, [3][n]): xi = xi_c + sigma_z/sqrt2 z2, x = x_c + tilt (xi - xi_c)
+ * + sigma_x/sqrt2 z0, y = y_c + sigma_y/sqrt2 z1, equal weights
+ * A pi^(3/2) sigma_x sigma_y sigma_z / n (the density A exp(-r^2/sigma_r^2 -
+ * xi^2/sigma_z^2) of Sec. 5.1), p = (0, 0, sqrt(gamma^2 - 1)).  Writes the
+ * DEVICE arrays of `out` (x, y, xi, px, py, pz, w; n entries, caller-owned)
+ * on `cuda_stream` without waiting.  Errors: QS_ERR_ARG. */
+int qs_bigaussian_beam(const double *theta, const double *z, int64_t n, double gamma,
+                       qs_beam *out, void *cuda_stream);
+
+/* Chain rule of qs_bigaussian_beam: from the DEVICE derivatives d_x, d_y,
+ * d_xi, d_w (n each) with respect to the macroparticles, dL/dtheta (HOST, 8)
+ * is OVERWRITTEN.  Synchronises `cuda_stream`.  Errors: QS_ERR_ARG,
+ * QS_ERR_CUDA. */
+int qs_bigaussian_adjoint(const double *theta, const double *z, int64_t n, const double *d_x,
+                          const double *d_y, const double *d_xi, const double *d_w,
+                          double *d_theta, void *cuda_stream);
+
 /* Copy base-slice fields [slice_begin, slice_end) into `out`, laid out
  * [field][slice][iy][ix] for the fields selected in `field_mask` in the
  * order psi, E_z, B_z, B_x, B_y, j_z(beam).  `out` is a device pointer if
@@ -225,17 +305,19 @@ int64_t qs_plasma_count(const qs_ctx *ctx);
 
 /* Phase trace of the last qs_step3d (config.trace_capacity > 0): for each
  * grid barrier of the slice engine, in order, the id of the phase that
- * ended there (`where`) and the device clock in nanoseconds
- * (`t_ns`, %globaltimer).  Entry 0 is the kernel start.  HOST arrays of `cap`
- * entries; returns the number of entries written (>= 0) or a status < 0. */
+ * ended there (`where`: 1 density deposit, 2 psi source, 3 moments,
+ * 4 and 5 source assembly, 6 push, 10-17 and 20-21 multigrid phases, 30 and
+ * 32 staged down and up legs, 40-67 sub-phase marks of block 0) and the
+ * device clock in nanoseconds (`t_ns`, %globaltimer).  Entry 0 is the kernel
+ * start.  HOST arrays of `cap` entries; returns the number of entries
+ * written (>= 0) or a status < 0. */
 int qs_phase_trace(qs_ctx *ctx, int32_t *where, int64_t *t_ns, int cap);
 
 /* Stable counting sort of n particles by cell, c = iy * N + ix with
  * ix = floor((x - x_min) / h) clamped to [0, N-1], ties in ascending id.
  * DEVICE arrays: x, y (float64, n), id (int32, n) in; cell (int32, n),
  * count (int32, N^2), offset (int32, N^2 + 1) and perm (int32, n: input
- * positions in sorted order) out.  The same routine the slice loop uses to
- * keep particles in cell-ordered tiles.  Synchronises. */
+ * positions in sorted order) out.  Synchronises. */
 int qs_cell_sort(qs_ctx *ctx, const double *x, const double *y, const int32_t *id, int64_t n,
                  int32_t *cell, int32_t *count, int32_t *offset, int32_t *perm);
 

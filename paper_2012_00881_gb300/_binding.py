@@ -92,6 +92,12 @@ PROTOTYPES = {
     "qs_cell_sort": (_I, [_P, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "qs_phase_trace": (_I, [_P, _P, _P, _I]),
     "qs_cell_sort_noalloc": (_I, [_I, _D, _D, _D, _P, _P, _P, _I64, _P, _P, _P, _P, _P]),
+    "qs_step3d_adjoint": (_I, [_P, _P, _I, _P, _P, _P, ctypes.POINTER(QsStepStats)]),
+    "qs_beam_gain": (_I, [_P, _P, _D, ctypes.POINTER(_D), _P]),
+    "qs_beam_deposit_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "qs_profile_adjoint": (_I, [_P, _P, _P, _I, _D, _P]),
+    "qs_bigaussian_beam": (_I, [_P, _P, _I64, _D, _P, _P]),
+    "qs_bigaussian_adjoint": (_I, [_P, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "qs_strerror": (ctypes.c_char_p, [_I]),
     "qs_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -301,6 +307,53 @@ class Context:
             self._check(k, "qs_phase_trace")
         return wh[:k], tn[:k]
 
+    # ---- differentiable form
+    def step3d_adjoint(self, d_hist=None, checkpoint_every: int = 0):
+        """qs_step3d_adjoint: returns (d_jzb [n_xi,N,N], d_w [np], d_nion [N,N],
+        stats) as float64 CUDA tensors for the cotangent d_hist [5,n_xi,N,N]."""
+        import torch
+        n = self.n
+        np_ = int(self.lib.qs_plasma_count(self.h))
+        d_jzb = torch.empty((self.n_xi, n, n), dtype=torch.float64, device="cuda")
+        d_w = torch.empty(np_, dtype=torch.float64, device="cuda")
+        d_nion = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        if d_hist is not None:
+            d_hist = d_hist.to(dtype=torch.float64, device="cuda").contiguous()
+        stats = QsStepStats()
+        self._check(self.lib.qs_step3d_adjoint(self.h, _ptr(d_hist), int(checkpoint_every),
+                                               _ptr(d_jzb), _ptr(d_w), _ptr(d_nion),
+                                               ctypes.byref(stats)), "qs_step3d_adjoint")
+        return d_jzb, d_w, d_nion, dict(slices=stats.slices, vcycles=list(stats.vcycles),
+                                        gpu_ms=stats.gpu_ms)
+
+    def beam_gain(self, beam: Beam, dt: float, d_hist=None) -> float:
+        """qs_beam_gain: mean energy gain of `beam` over a push of dt (the beam
+        is not moved); adds dL/d(history) into d_hist when given."""
+        g = _D()
+        b = beam.struct()
+        self._check(self.lib.qs_beam_gain(self.h, ctypes.byref(b), float(dt), ctypes.byref(g),
+                                          _ptr(d_hist)), "qs_beam_gain")
+        return g.value
+
+    def beam_deposit_adjoint(self, beam: Beam, d_jzb):
+        """qs_beam_deposit_adjoint: (d_x, d_y, d_xi, d_w) of a bunch."""
+        import torch
+        out = [torch.empty(beam.n, dtype=torch.float64, device="cuda") for _ in range(4)]
+        b = beam.struct()
+        self._check(self.lib.qs_beam_deposit_adjoint(self.h, ctypes.byref(b), _ptr(d_jzb),
+                                                     *[_ptr(t) for t in out]),
+                    "qs_beam_deposit_adjoint")
+        return tuple(out)
+
+    def profile_adjoint(self, d_w, d_nion, n_coef: int, r_max: float):
+        """qs_profile_adjoint: dL/d(profile table) as a numpy array."""
+        import numpy as np
+        out = np.zeros(int(n_coef))
+        self._check(self.lib.qs_profile_adjoint(self.h, _ptr(d_w), _ptr(d_nion), int(n_coef),
+                                                float(r_max), out.ctypes.data),
+                    "qs_profile_adjoint")
+        return out
+
     def cell_sort(self, x, y, pid):
         """Run the library's cell sort on CUDA tensors; returns (cell, count, offset, perm)."""
         import torch
@@ -369,4 +422,39 @@ def step3d_batched(contexts: Sequence["Context"], beams: Sequence[Sequence[Beam]
                         pushes=s_.pushes, vcycles=list(s_.vcycles),
                         psi_guard_hits=s_.psi_guard_hits, max_relres=s_.max_relres,
                         vmax=s_.vmax, max_m=s_.max_m, gpu_ms=s_.gpu_ms))
+    return out
+
+
+def bigaussian_beam(theta: Sequence[float], z, gamma: float, charge: float = -1.0,
+                    q_over_m: float = -1.0) -> Beam:
+    """qs_bigaussian_beam: the bunch of parameters theta on normals z [3, n]
+    (float64 CUDA tensor)."""
+    import torch
+    lib = load_library()
+    n = int(z.shape[1])
+    arrays = {k: torch.empty(n, dtype=torch.float64, device="cuda") for k in Beam.KEYS}
+    beam = Beam(arrays, charge=charge, q_over_m=q_over_m)
+    th = (ctypes.c_double * 8)(*[float(v) for v in theta])
+    b = beam.struct()
+    st = torch.cuda.current_stream()
+    rc = lib.qs_bigaussian_beam(ctypes.cast(th, _P), _ptr(z), n, float(gamma), ctypes.byref(b),
+                                _P(st.cuda_stream))
+    if rc != QS_OK:
+        raise QsError(rc, "qs_bigaussian_beam: " + lib.qs_strerror(rc).decode())
+    return beam
+
+
+def bigaussian_adjoint(theta: Sequence[float], z, d_x, d_y, d_xi, d_w):
+    """qs_bigaussian_adjoint: dL/dtheta (numpy, 8)."""
+    import numpy as np
+    import torch
+    lib = load_library()
+    th = (ctypes.c_double * 8)(*[float(v) for v in theta])
+    out = np.zeros(8)
+    st = torch.cuda.current_stream()
+    rc = lib.qs_bigaussian_adjoint(ctypes.cast(th, _P), _ptr(z), int(z.shape[1]), _ptr(d_x),
+                                   _ptr(d_y), _ptr(d_xi), _ptr(d_w), out.ctypes.data,
+                                   _P(st.cuda_stream))
+    if rc != QS_OK:
+        raise QsError(rc, "qs_bigaussian_adjoint: " + lib.qs_strerror(rc).decode())
     return out

@@ -1,6 +1,7 @@
 // Host side of the libqs C ABI (declared in include/qs.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -390,7 +391,7 @@ int qs_init_plasma(qs_ctx *c, int ppc, const double *profile, int n_coef, double
 // zeroed fields, the driver current on the base slices, reset diagnostics;
 // fills the engine arguments.  Work is queued on `st`.
 static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t *sched,
-                        cudaStream_t st, EngineArgs &a) {
+                        cudaStream_t st, EngineArgs &a, bool replay = false) {
     if (check_ctx(c)) return QS_ERR_ARG;
     if (!c->have_plasma) return fail(c, QS_ERR_STATE, "qs_init_plasma has not been called");
     if (n_beams < 0 || (n_beams > 0 && !beams)) return fail(c, QS_ERR_ARG, "bad beam list");
@@ -428,16 +429,19 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
     // starts from zero
     for (double *f : {c->psi, c->ez, c->bz, c->bx, c->by})
         CK(cudaMemsetAsync(f, 0, nn * sizeof(double), st), "memset");
-    // driver current on the base slices
-    CK(cudaMemsetAsync(c->jzb, 0, (size_t)g.n_xi * nn * sizeof(double), st), "memset");
-    for (int b = 0; b < n_beams; ++b)
-        CK(qs_launch_beam_deposit(st, beams[b], c->N, g.x_min, g.x_max, g.y_min, g.y_max,
-                                  c->h, g.n_xi, g.xi_min, dxi0, c->jzb),
-           "beam deposit");
+    // driver current on the base slices (a replay for the adjoint keeps the
+    // current, the history and the diagnostics of the forward step)
+    if (!replay) {
+        CK(cudaMemsetAsync(c->jzb, 0, (size_t)g.n_xi * nn * sizeof(double), st), "memset");
+        for (int b = 0; b < n_beams; ++b)
+            CK(qs_launch_beam_deposit(st, beams[b], c->N, g.x_min, g.x_max, g.y_min, g.y_max,
+                                      c->h, g.n_xi, g.xi_min, dxi0, c->jzb),
+               "beam deposit");
+        CK(cudaMemsetAsync(c->diag_m, 0, g.n_xi * sizeof(int32_t), st), "memset");
+        CK(cudaMemsetAsync(c->diag_vmax, 0, g.n_xi * sizeof(double), st), "memset");
+        CK(cudaMemsetAsync(c->diag_charge, 0, g.n_xi * sizeof(double), st), "memset");
+    }
     CK(cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), st), "memset");
-    CK(cudaMemsetAsync(c->diag_m, 0, g.n_xi * sizeof(int32_t), st), "memset");
-    CK(cudaMemsetAsync(c->diag_vmax, 0, g.n_xi * sizeof(double), st), "memset");
-    CK(cudaMemsetAsync(c->diag_charge, 0, g.n_xi * sizeof(double), st), "memset");
     if (sched)
         CK(cudaMemcpyAsync(c->d_sched, sched, g.n_xi * sizeof(int32_t), cudaMemcpyHostToDevice,
                            st),
@@ -537,6 +541,19 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
     a.sc = c->sc;
     a.trace = c->trace;
     a.trace_cap = g.trace_capacity;
+    a.j_begin = 0;
+    a.j_end = g.n_xi;
+    a.ckpt_every = 0;
+    a.ckpt = nullptr;
+    a.seg_p = a.seg_g = nullptr;
+    if (replay) {
+        a.hist = nullptr;
+        a.diag_m = nullptr;
+        a.diag_vmax = nullptr;
+        a.diag_charge = nullptr;
+        a.trace = nullptr;
+        a.trace_cap = 0;
+    }
     return QS_OK;
 }
 
@@ -662,6 +679,236 @@ int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const i
         if (r != QS_OK && status == QS_OK) status = r;
     }
     return status;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of one 3D step (checkpointed reverse slice loop)
+// ---------------------------------------------------------------------------
+namespace {
+
+// device buffers of one adjoint call, freed on every return path
+struct DevBufs {
+    std::vector<void *> list;
+    ~DevBufs() {
+        for (void *p : list) cudaFree(p);
+    }
+};
+
+int read_scalars(qs_ctx *c, DevScalars &hs, const char *what) {
+    CK(cudaMemcpy(&hs, c->sc, sizeof(hs), cudaMemcpyDeviceToHost), "copy scalars");
+    if (hs.err != 0) return fail(c, hs.err, "%s: device wait timed out at phase %d", what,
+                                 hs.err_where);
+    if (hs.not_converged)
+        return fail(c, QS_ERR_NOT_CONVERGED, "%s: a multigrid solve reached %d V-cycles", what,
+                    c->cfg.mg_max_vcycles);
+    return QS_OK;
+}
+
+// plasma state of checkpoint k into the working particle arrays
+int restore_checkpoint(qs_ctx *c, const double *ck) {
+    const int64_t np = c->np;
+    const size_t bd = np * sizeof(double);
+    CK(cudaMemcpyAsync(c->x, ck, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    CK(cudaMemcpyAsync(c->y, ck + np, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    if (c->cfg.precision == QS_FP32_REFINED) {
+        CK(qs_launch_convert(c->st, ck + 2 * np, c->px32, np), "convert");
+        CK(qs_launch_convert(c->st, ck + 3 * np, c->py32, np), "convert");
+    } else {
+        CK(cudaMemcpyAsync(c->px, ck + 2 * np, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+        CK(cudaMemcpyAsync(c->py, ck + 3 * np, bd, cudaMemcpyDeviceToDevice, c->st), "copy");
+    }
+    return QS_OK;
+}
+
+}  // namespace
+
+int qs_step3d_adjoint(qs_ctx *c, const double *d_hist, int checkpoint_every, double *d_jzb,
+                      double *d_w, double *d_nion, qs_step_stats *stats) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_step) return fail(c, QS_ERR_STATE, "qs_step3d has not been run");
+    if (!d_jzb || !d_w || !d_nion) return fail(c, QS_ERR_ARG, "NULL output array");
+    if (checkpoint_every < 0) return fail(c, QS_ERR_ARG, "checkpoint_every must be >= 0");
+    const qs_config &g = c->cfg;
+    const int K = checkpoint_every > 0 ? checkpoint_every : 32;
+    const int nxi = g.n_xi;
+    const int64_t np = c->np;
+    const size_t nn = (size_t)c->N * c->N;
+    cudaStream_t st = c->st;
+    // the forward schedule, replayed exactly
+    std::vector<int32_t> sched(nxi);
+    CK(cudaMemcpy(sched.data(), c->diag_m, nxi * sizeof(int32_t), cudaMemcpyDeviceToHost),
+       "copy schedule");
+    for (int j = 0; j < nxi; ++j)
+        if (sched[j] < 1 || sched[j] > g.refine_k)
+            return fail(c, QS_ERR_STATE, "the forward step did not complete");
+    int blocks = 0, sms = 0;
+    if (qs_adjoint_max_blocks(c->dev, g.precision, c->engine_smem, &blocks) != 0 || blocks < 1)
+        return fail(c, QS_ERR_CUDA, "adjoint engine cannot be made resident");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev), "attr");
+    if (blocks > sms) blocks = sms;
+    const int nseg = (nxi + K - 1) / K;
+    int max_sub = 0;
+    for (int k = 0; k < nseg; ++k) {
+        int n_sub = 0;
+        for (int j = k * K; j < std::min(nxi, (k + 1) * K); ++j)
+            n_sub += (j == nxi - 1) ? 1 : sched[j];
+        max_sub = std::max(max_sub, n_sub);
+    }
+    DevBufs B;
+    double *ckpt = nullptr, *seg_p = nullptr, *seg_g = nullptr, *lam = nullptr, *grd = nullptr;
+    AL(B.list, ckpt, (size_t)nseg * 4 * np);
+    AL(B.list, seg_p, (size_t)max_sub * 4 * np);
+    AL(B.list, seg_g, (size_t)max_sub * SG_COUNT * nn);
+    AL(B.list, lam, (size_t)4 * np);
+    AL(B.list, grd, (size_t)20 * nn);
+    float ms_total = 0.f;
+    // forward replay that stores the checkpoints
+    EngineArgs a;
+    int r = step_prepare(c, nullptr, 0, sched.data(), st, a, true);
+    if (r != QS_OK) return r;
+    a.ckpt_every = K;
+    a.ckpt = ckpt;
+    CK(cudaEventRecord(c->ev0, st), "event");
+    CK(qs_launch_engine(st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
+    CK(cudaEventRecord(c->ev1, st), "event");
+    CK(cudaStreamSynchronize(st), "checkpoint pass");
+    {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        ms_total += ms;
+        DevScalars hs;
+        r = read_scalars(c, hs, "checkpoint pass");
+        if (r != QS_OK) return r;
+    }
+    // adjoint state
+    CK(cudaMemsetAsync(lam, 0, (size_t)4 * np * sizeof(double), st), "memset");
+    CK(cudaMemsetAsync(grd, 0, (size_t)20 * nn * sizeof(double), st), "memset");
+    CK(cudaMemsetAsync(d_w, 0, np * sizeof(double), st), "memset");
+    CK(cudaMemsetAsync(d_jzb, 0, (size_t)nxi * nn * sizeof(double), st), "memset");
+    CK(cudaMemsetAsync(d_nion, 0, nn * sizeof(double), st), "memset");
+    AdjArgs d;
+    std::memset(&d, 0, sizeof(d));
+    d.lx = lam;
+    d.ly = lam + np;
+    d.lpx = lam + 2 * np;
+    d.lpy = lam + 3 * np;
+    d.lw = d_w;
+    double **gp[] = {&d.g_psi, &d.g_ez, &d.g_bz, &d.g_bx, &d.g_by, &d.g_dpx, &d.g_dpy,
+                     &d.g_jx,  &d.g_jy, &d.g_txx, &d.g_txy, &d.g_tyy, &d.g_G, &d.g_n,
+                     &d.mu_x,  &d.mu_y, &d.nu_ez, &d.nu_bz, &d.nu_psi, &d.f_nu_psi};
+    for (int k = 0; k < 20; ++k) *gp[k] = grd + (size_t)k * nn;
+    d.d_hist = d_hist;
+    d.d_jzb = d_jzb;
+    d.d_nion = d_nion;
+    int64_t slices = 0, vc[3] = {0, 0, 0};
+    for (int k = nseg - 1; k >= 0; --k) {
+        const int j0 = k * K, j1 = std::min(nxi, j0 + K);
+        int n_sub = 0;
+        for (int j = j0; j < j1; ++j) n_sub += (j == nxi - 1) ? 1 : sched[j];
+        // recompute the segment from its checkpoint, storing every slice
+        r = step_prepare(c, nullptr, 0, sched.data(), st, a, true);
+        if (r != QS_OK) return r;
+        r = restore_checkpoint(c, ckpt + (size_t)k * 4 * np);
+        if (r != QS_OK) return r;
+        a.j_begin = j0;
+        a.j_end = j1;
+        a.seg_p = seg_p;
+        a.seg_g = seg_g;
+        CK(cudaEventRecord(c->ev0, st), "event");
+        CK(qs_launch_engine(st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
+        CK(cudaStreamSynchronize(st), "segment recompute");
+        DevScalars hs;
+        r = read_scalars(c, hs, "segment recompute");
+        if (r != QS_OK) return r;
+        // the reverse slice loop over the segment
+        CK(cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), st), "memset");
+        d.j0 = j0;
+        d.j1 = j1;
+        d.n_sub = n_sub;
+        CK(qs_launch_adjoint(st, a, d, blocks, c->engine_smem), "adjoint engine launch");
+        CK(cudaEventRecord(c->ev1, st), "event");
+        CK(cudaStreamSynchronize(st), "adjoint engine");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        ms_total += ms;
+        r = read_scalars(c, hs, "adjoint engine");
+        if (r != QS_OK) return r;
+        slices += hs.slices;
+        for (int q = 0; q < 3; ++q) vc[q] += hs.vcycles[q];
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->slices = slices;
+        stats->substeps = slices - nxi;
+        for (int q = 0; q < 3; ++q) stats->vcycles[q] = vc[q];
+        stats->status = QS_OK;
+        stats->gpu_ms = ms_total;
+    }
+    return QS_OK;
+}
+
+int qs_beam_gain(qs_ctx *c, const qs_beam *beam, double dt, double *gain, double *d_hist) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_step) return fail(c, QS_ERR_STATE, "qs_step3d has not been run");
+    if (!beam || !gain || beam->n < 1 || !beam->x || !beam->y || !beam->xi || !beam->px ||
+        !beam->py || !beam->pz)
+        return fail(c, QS_ERR_ARG, "bad bunch");
+    const qs_config &g = c->cfg;
+    const double dxi0 = (g.xi_max - g.xi_min) / g.n_xi;
+    double *dsum = nullptr;
+    CK(cudaMallocAsync(&dsum, sizeof(double), c->st), "cudaMallocAsync");
+    cudaError_t e = cudaMemsetAsync(dsum, 0, sizeof(double), c->st);
+    if (e == cudaSuccess)
+        e = qs_launch_beam_gain(c->st, *beam, c->N, g.x_min, g.x_max, g.y_min, g.y_max, c->h,
+                                g.n_xi, g.xi_min, dxi0, c->hist, dt, 1.0 / (double)beam->n,
+                                dsum, d_hist);
+    double sum = 0.0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&sum, dsum, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    cudaFreeAsync(dsum, c->st);
+    const cudaError_t e2 = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "bunch gain");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "bunch gain");
+    *gain = sum / (double)beam->n;
+    return QS_OK;
+}
+
+int qs_beam_deposit_adjoint(qs_ctx *c, const qs_beam *beam, const double *d_jzb, double *d_x,
+                            double *d_y, double *d_xi, double *d_w) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_step) return fail(c, QS_ERR_STATE, "qs_step3d has not been run");
+    if (!beam || beam->n < 0 || !d_jzb ||
+        (beam->n > 0 && (!beam->x || !beam->y || !beam->xi || !beam->px || !beam->py ||
+                         !beam->pz || !beam->w || !d_x || !d_y || !d_xi || !d_w)))
+        return fail(c, QS_ERR_ARG, "bad bunch or output arrays");
+    const qs_config &g = c->cfg;
+    const double dxi0 = (g.xi_max - g.xi_min) / g.n_xi;
+    CK(qs_launch_beam_deposit_adjoint(c->st, *beam, c->N, g.x_min, g.x_max, g.y_min, g.y_max,
+                                      c->h, g.n_xi, g.xi_min, dxi0, d_jzb, d_x, d_y, d_xi, d_w),
+       "bunch deposit adjoint");
+    return QS_OK;
+}
+
+int qs_profile_adjoint(qs_ctx *c, const double *d_w, const double *d_nion, int n_coef,
+                       double r_max, double *d_table) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_plasma) return fail(c, QS_ERR_STATE, "qs_init_plasma has not been called");
+    if (!d_w || !d_nion || !d_table || n_coef < 1 || n_coef > 4096 || !(r_max > 0.0))
+        return fail(c, QS_ERR_ARG, "bad profile-adjoint arguments (n_coef in [1, 4096])");
+    const qs_config &g = c->cfg;
+    double *dt = nullptr;
+    CK(cudaMallocAsync(&dt, n_coef * sizeof(double), c->st), "cudaMallocAsync");
+    cudaError_t e = cudaMemsetAsync(dt, 0, n_coef * sizeof(double), c->st);
+    if (e == cudaSuccess)
+        e = qs_launch_profile_adjoint(c->st, c->N, c->ppc, g.x_min, g.y_min, c->h, n_coef,
+                                      r_max, d_w, d_nion, dt);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_table, dt, n_coef * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    cudaFreeAsync(dt, c->st);
+    const cudaError_t e2 = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "profile adjoint");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "profile adjoint");
+    return QS_OK;
 }
 
 int qs_push_beam(qs_ctx *c, qs_beam *beams, int n_beams, double dt) {

@@ -139,7 +139,7 @@ __device__ void phase_psi_rhs(const EngineArgs &A, const PS<P> &Q, const double 
     }
     s = block_sum(s);
     if (threadIdx.x == 0) atomicAdd(&A.sc->fnorm[0][0], s);
-    if (base) {
+    if (base && A.diag_charge) {
         cs = block_sum(cs);
         if (threadIdx.x == 0) atomicAdd(&A.diag_charge[j], cs * A.h * A.h);
     }
@@ -287,9 +287,34 @@ __device__ void phase_assemble2(const EngineArgs &A, const PS<P> &Q, const doubl
 // deposit n_* of the next slice; V_max.  gamma is evaluated in float64.
 template <typename P>
 __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, bool base,
-                           bool last, int j, double dxi, int pk, Thr T) {
+                           bool last, int j, double dxi, int pk, int sub, Thr T) {
     const int nn = A.N * A.N;
-    if (base) {
+    if (A.seg_g) {  // segment store for the adjoint: fields and moments (float64)
+        double *g = A.seg_g + (size_t)sub * SG_COUNT * nn;
+        const double *ncur = Q.na == nnext ? Q.nb : Q.na;
+        for (int i = T.t0; i < nn; i += T.nt) {
+            g[SG_PSI * nn + i] = A.psi[i];
+            g[SG_EZ * nn + i] = A.ez[i];
+            g[SG_BZ * nn + i] = A.bz[i];
+            g[SG_BX * nn + i] = A.bx[i];
+            g[SG_BY * nn + i] = A.by[i];
+            g[SG_N * nn + i] = ncur[i];
+            g[SG_JX * nn + i] = (double)Q.jx[i];
+            g[SG_JY * nn + i] = (double)Q.jy[i];
+            g[SG_TXX * nn + i] = (double)Q.txx[i];
+            g[SG_TXY * nn + i] = (double)Q.txy[i];
+            g[SG_TYY * nn + i] = (double)Q.tyy[i];
+            g[SG_G * nn + i] = g_total(Q.G, ncur, i);
+        }
+        double *sp = A.seg_p + (size_t)sub * 4 * A.np;
+        for (int64_t p = T.t0; p < A.np; p += T.nt) {
+            sp[p] = Q.x[p];
+            sp[A.np + p] = Q.y[p];
+            sp[2 * A.np + p] = (double)Q.px[p];
+            sp[3 * A.np + p] = (double)Q.py[p];
+        }
+    }
+    if (base && A.hist) {
         double *h0 = A.hist + (size_t)j * nn;
         const size_t fs = (size_t)A.n_xi * nn;
         for (int i = T.t0; i < nn; i += T.nt) {
@@ -382,17 +407,26 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
     const SolveSpec Veb{2, 1, {A.ez, A.bz}, {A.f_ez, A.f_bz}, false};
     const SolveSpec Vbp{2, 2, {A.bx, A.by}, {A.f_bx, A.f_by}, true};
 
-    int m = A.m_sched ? A.m_sched[0] : 1;
-    int slot = 0, pk = 0;
+    int m = A.m_sched ? A.m_sched[A.j_begin] : 1;
+    int slot = 0, pk = 0, sub = 0;
     int have = 0;                        // previous solutions available for the guess
     double gx0 = 0.0, gx1 = 0.0, gx2 = 0.0;  // their xi
-    for (int j = 0; j < A.n_xi; ++j) {
-        if (lead) {
+    for (int j = A.j_begin; j < A.j_end; ++j) {
+        if (lead && A.diag_m) {
             A.diag_m[j] = m;
             if (m > sc->max_m) sc->max_m = m;
         }
         const bool last = (j == A.n_xi - 1);
         const double dxi = A.dxi0 / m;
+        if (A.ckpt && j % A.ckpt_every == 0) {  // plasma state before slice j
+            double *cp = A.ckpt + (size_t)(j / A.ckpt_every) * 4 * A.np;
+            for (int64_t p = T.t0; p < A.np; p += T.nt) {
+                cp[p] = Q.x[p];
+                cp[A.np + p] = Q.y[p];
+                cp[2 * A.np + p] = (double)Q.px[p];
+                cp[3 * A.np + p] = (double)Q.py[p];
+            }
+        }
         for (int q = 0; q < m; ++q) {
             const bool base = (q == 0);
             const double xs = j * A.dxi0 + q * dxi;  // xi of this slice (from xi_min)
@@ -408,7 +442,8 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
             phase_assemble2<P>(A, Q, ncur, T, g);
             if (!S(5)) return false;
             if (!mg_solve<REF>(A, S, Vbp, slot, bid, nblk, smem, s_inv_ready)) return false;
-            phase_push<P>(A, Q, nnext, base, last, j, dxi, pk, T);
+            phase_push<P>(A, Q, nnext, base, last, j, dxi, pk, sub, T);
+            ++sub;
             if (lead) {
                 sc->slices += 1;
                 if (!last) {
@@ -432,7 +467,7 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
         }
         if (last) break;
         const double vm = __longlong_as_double((long long)vload(&sc->vmax_bits[(pk - 1) & 1]));
-        if (lead) A.diag_vmax[j] = vm;
+        if (lead && A.diag_vmax) A.diag_vmax[j] = vm;
         if (A.m_sched) {
             m = A.m_sched[j + 1];
         } else if (vm <= A.V0) {

@@ -111,7 +111,45 @@ struct EngineArgs {
     // every grid barrier, up to trace_cap entries
     int64_t *trace;
     int trace_cap;
+    // base slices [j_begin, j_end) of this launch (the whole window, or one
+    // segment recomputed for the adjoint from a stored plasma state)
+    int j_begin, j_end;
+    // checkpoints: the plasma state (x, y, px, py; momenta in the particle
+    // precision, widened to float64) before base slice j = k * ckpt_every is
+    // stored at ckpt + k * 4 * np (nullptr: none)
+    int ckpt_every;
+    double *ckpt;
+    // segment store for the adjoint (nullptr: none): for the s-th computed
+    // slice of the launch, the plasma state before its push at
+    // seg_p + s * 4 * np (x, y, px, py) and 12 grids at seg_g + s * 12 * N^2
+    // (psi, Ez, Bz, Bx, By, n_*, jx, jy, Txx, Txy, Tyy, n_* <gamma>)
+    double *seg_p, *seg_g;
 };
+
+// Arguments of the adjoint engine (the reverse slice loop over one segment).
+// Cotangents are written g_<name> = dL/d<name>; all float64.
+struct AdjArgs {
+    // the segment: base slices [j0, j1), n_sub stored slices (sub-steps
+    // included) in forward order in the segment store of EngineArgs
+    int j0, j1, n_sub;
+    // cotangents of the plasma state (x, y, px, py) of the current slice and
+    // of the lattice weights (accumulated over the whole window)
+    double *lx, *ly, *lpx, *lpy, *lw;
+    // grid cotangents
+    double *g_psi, *g_ez, *g_bz, *g_bx, *g_by, *g_dpx, *g_dpy;
+    double *g_jx, *g_jy, *g_txx, *g_txy, *g_tyy, *g_G, *g_n;
+    // adjoint solutions (transposed solves; also the warm start of the next
+    // reverse slice) and the right-hand side of the psi adjoint
+    double *mu_x, *mu_y, *nu_ez, *nu_bz, *nu_psi, *f_nu_psi;
+    // inputs / outputs
+    const double *d_hist;  // [5][n_xi][N*N] dL/d(stored fields) or nullptr
+    double *d_jzb;         // [n_xi][N*N] dL/d(j_z of the bunches), accumulated
+    double *d_nion;        // [N*N] dL/d(n_ion), accumulated
+};
+
+// grids of one stored slice in the segment store
+enum SegGrid { SG_PSI = 0, SG_EZ, SG_BZ, SG_BX, SG_BY, SG_N, SG_JX, SG_JY, SG_TXX, SG_TXY,
+               SG_TYY, SG_G, SG_COUNT };
 
 // ---------------------------------------------------------------------------
 // small device helpers
@@ -199,6 +237,20 @@ cudaError_t qs_launch_beam_push(cudaStream_t st, const qs_beam &b, int n, double
                                 double x_max, double y_min, double y_max, double h, int n_xi,
                                 double xi_min, double dxi0, const double *hist, double dt);
 cudaError_t qs_launch_convert(cudaStream_t st, const double *src, float *dst, int64_t n);
+// implemented in qs_grad_aux.cu
+cudaError_t qs_launch_beam_gain(cudaStream_t st, const qs_beam &b, int n, double x_min,
+                                double x_max, double y_min, double y_max, double h, int n_xi,
+                                double xi_min, double dxi0, const double *hist, double dt,
+                                double scale, double *gain_sum, double *d_hist);
+cudaError_t qs_launch_beam_deposit_adjoint(cudaStream_t st, const qs_beam &b, int n,
+                                           double x_min, double x_max, double y_min,
+                                           double y_max, double h, int n_xi, double xi_min,
+                                           double dxi0, const double *d_jzb, double *dx,
+                                           double *dy, double *dxi, double *dw);
+cudaError_t qs_launch_profile_adjoint(cudaStream_t st, int n, int ppc, double x_min,
+                                      double y_min, double h, int n_coef, double r_max,
+                                      const double *d_w, const double *d_nion,
+                                      double *d_table);
 cudaError_t qs_launch_widen(cudaStream_t st, const float *src, double *dst, int64_t n);
 cudaError_t qs_launch_cell_sort(cudaStream_t st, const double *x, const double *y,
                                 const int32_t *id, int64_t np, int n, double x_min,
@@ -210,6 +262,9 @@ cudaError_t qs_launch_engine_batched(cudaStream_t st, const EngineArgs *list, in
                                      int precision, int team, int teams, BatchState *bs,
                                      size_t smem_bytes);
 int qs_engine_batched_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
+cudaError_t qs_launch_adjoint(cudaStream_t st, const EngineArgs &a, const AdjArgs &d,
+                              int grid_blocks, size_t smem_bytes);
+int qs_adjoint_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
 int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
                             int tile_x, int tile_y, int nu, size_t *block_offset,

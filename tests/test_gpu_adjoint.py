@@ -1,0 +1,132 @@
+"""Differentiable form on the GPU: gradients of the witness energy gain (GPU).
+
+The loss L(theta, table) = mean energy gain of the witness over one bunch
+push after one 3D step; theta are the driver's eight bi-Gaussian parameters
+and table the radial plasma-density profile.  The CUDA adjoint (reverse
+slice loop with checkpoints, behind a torch.autograd.Function) is checked
+against the gradient oracle (autograd of the float64 restatement, itself
+pinned by finite differences of the oracle), against central finite
+differences of the CUDA forward, and for invariance under the checkpoint
+interval.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import qs_grad as QG
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _workload(strong: bool):
+    if strong:
+        hw, xl, amp, sx, sy, ws = 2.0, 7.0, 20.0, 0.35, 0.3, 0.25
+    else:
+        hw, xl, amp, sx, sy, ws = 4.0, 3.5, 1.5, 0.6, 0.5, 0.4
+    return W.Workload(
+        name="g16", n=16, half_width=hw, n_xi=14, xi_len=xl, ppc=4,
+        beams=(W.BeamSpec(amplitude=amp, sigma_x=sx, sigma_y=sy, sigma_z=0.45, xi_c=1.0,
+                          n_particles=1500, seed=3, x_c=0.1 * hw / 4, y_c=-0.05 * hw / 4,
+                          tilt=0.05),
+               W.BeamSpec(amplitude=1.0, sigma_x=ws, sigma_y=ws, sigma_z=0.25, xi_c=2.6,
+                          n_particles=400, seed=4)),
+        profile=((1.0, 1.03, 1.07, 1.12, 1.18, 1.25), hw * math.sqrt(2.0)),
+        precision="fp64", dt=2.0)
+
+
+def _gpu_gradient(qs, wl, P, theta, table, form="fp64", checkpoint_every=0):
+    ctx = qs.Context(qs.config_from_workload(wl, precision=form, mg_tol=1e-12))
+    z = torch.tensor(P.driver_z, dtype=torch.float64, device="cuda")
+    witness = qs.Beam(P.witness)
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    tb = torch.tensor(table, dtype=torch.float64, requires_grad=True)
+    L = qs.witness_gain(ctx, th, tb, z, P.driver_gamma, witness, P.dt, wl.ppc, P.r_max,
+                        checkpoint_every)
+    m = ctx.slice_diagnostics()[0]
+    L.backward()
+    return float(L.detach()), th.grad.numpy().copy(), tb.grad.numpy().copy(), m
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+@pytest.mark.parametrize("strong", [False, True])
+def test_fp64_gradient_matches_the_gradient_oracle(qs, strong):
+    wl = _workload(strong)
+    P, theta, table = QG.problem_from_workload(wl)
+    L, dth, dtb, m = _gpu_gradient(qs, wl, P, theta, table)
+    np.testing.assert_array_equal(m, P.m_schedule)
+    Lo, dtho, dtbo = QG.gradient(P, theta, table)
+    assert abs(L - Lo) <= 1e-9 * abs(Lo)
+    scale = max(np.abs(dtho).max(), np.abs(dtbo).max())
+    assert np.max(np.abs(dth - dtho)) <= 1e-7 * scale, (dth, dtho)
+    assert np.max(np.abs(dtb - dtbo)) <= 1e-7 * scale, (dtb, dtbo)
+
+
+def test_fp64_gradient_matches_central_differences_of_the_gpu_loss(qs):
+    wl = _workload(True)
+    P, theta, table = QG.problem_from_workload(wl)
+    _, dth, dtb, _ = _gpu_gradient(qs, wl, P, theta, table)
+    scale = max(np.abs(dth).max(), np.abs(dtb).max())
+    ctx = qs.Context(qs.config_from_workload(wl, mg_tol=1e-13))
+    z = torch.tensor(P.driver_z, dtype=torch.float64, device="cuda")
+    witness = qs.Beam(P.witness)
+
+    def loss(th, tb):
+        ctx.init_plasma(wl.ppc, list(tb), P.r_max)
+        drv = qs.bigaussian_beam(th, z, P.driver_gamma)
+        ctx.step3d([drv, witness], schedule=P.m_schedule)
+        return ctx.beam_gain(witness, P.dt)
+
+    for k in range(8):
+        eps = 1e-5 * max(abs(theta[k]), 1.0)
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += eps
+        tm[k] -= eps
+        d = (loss(tp, table) - loss(tm, table)) / (2 * eps)
+        assert abs(d - dth[k]) <= 1e-4 * max(abs(d), 1e-3 * scale), (k, d, dth[k])
+    for k in range(len(table)):
+        eps = 1e-5
+        tp, tm = table.copy(), table.copy()
+        tp[k] += eps
+        tm[k] -= eps
+        d = (loss(theta, tp) - loss(theta, tm)) / (2 * eps)
+        assert abs(d - dtb[k]) <= 1e-4 * max(abs(d), 1e-3 * scale), ("table", k, d, dtb[k])
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(qs):
+    wl = _workload(True)
+    P, theta, table = QG.problem_from_workload(wl)
+    ref = _gpu_gradient(qs, wl, P, theta, table, checkpoint_every=0)
+    for K in (1, 3, 14):
+        got = _gpu_gradient(qs, wl, P, theta, table, checkpoint_every=K)
+        assert _rel(got[1], ref[1]) <= 1e-9 and _rel(got[2], ref[2]) <= 1e-9, K
+
+
+@pytest.mark.parametrize("strong", [False, True])
+def test_refined_form_gradient_against_the_gradient_oracle(qs, strong):
+    """Float32 particles and inner cycles in the forward replay, float64
+    adjoint arithmetic: the gradient follows the float64 one to 1e-3."""
+    wl = _workload(strong)
+    P, theta, table = QG.problem_from_workload(wl)
+    L, dth, dtb, m = _gpu_gradient(qs, wl, P, theta, table, form="fp32r")
+    if not np.array_equal(m, P.m_schedule):
+        pytest.skip("the float32 forward chose another sub-step schedule")
+    Lo, dtho, dtbo = QG.gradient(P, theta, table)
+    assert abs(L - Lo) <= 1e-4 * abs(Lo)
+    scale = max(np.abs(dtho).max(), np.abs(dtbo).max())
+    assert np.max(np.abs(dth - dtho)) <= 1e-3 * scale, (dth, dtho)
+    assert np.max(np.abs(dtb - dtbo)) <= 1e-3 * scale, (dtb, dtbo)
+
+
+def test_adjoint_needs_a_forward_step(qs):
+    wl = _workload(False)
+    ctx = qs.Context(qs.config_from_workload(wl))
+    ctx.init_plasma(wl.ppc)
+    with pytest.raises(qs.QsError) as e:
+        ctx.step3d_adjoint(None)
+    assert e.value.status == qs.QS_ERR_STATE
