@@ -78,7 +78,7 @@ def _workload_desc(wl):
 
 
 # ---------------------------------------------------------------- ncu traffic
-ENGINE_SOURCES = ("qs_engine.cu", "qs_mg.cuh", "qs_tile.cuh", "qs_internal.cuh")
+ENGINE_SOURCES = ("qs_engine.cu", "qs_solve.cuh", "qs_mg.cuh", "qs_tile.cuh", "qs_internal.cuh")
 
 
 def engine_source_hash() -> str:
@@ -118,7 +118,7 @@ def measured_traffic(kernel: str, workload: str, form: str):
 
 # ---------------------------------------------------------------- roofline model
 def algorithmic_bytes(stats, wl, b: int, n_xi: int) -> float:
-    """Bytes one slice-engine launch must move at minimum (the design doc model):
+    """Bytes one slice-engine launch must move at minimum (the byte model):
     particles 14b per particle per pushed slice (5b on the last slice), grid
     phases 50b per point per slice + 10b per point per base slice, multigrid
     24b per component-point per V-cycle plus 8b per point per screened cycle."""
@@ -338,6 +338,88 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------- gradient
+GRAD = "grad256"
+
+
+def run_grad(args):
+    """The differentiable form on the 256^2 case: one gradient evaluation is
+    the forward (plasma lattice with the density table, driver from its 8
+    parameters, one 3D step, witness gain) plus the backward (witness gain
+    cotangent, checkpointed reverse slice loop, chain rules).  Reports
+    gradient evaluations' slices/s and the grad/forward time ratio."""
+    import numpy as np
+    import torch
+
+    import paper_2012_00881_gb300 as qs
+    import workloads as W
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    wl = W.workload(GRAD)
+    if args.slices > 0:
+        wl = wl.with_(n_xi=args.slices, xi_len=wl.xi_len * args.slices / wl.n_xi)
+    drv, wit = wl.beams
+    theta = [drv.amplitude, drv.sigma_x, drv.sigma_y, drv.sigma_z, drv.x_c, drv.y_c, drv.xi_c,
+             drv.tilt]
+    table, r_max = wl.profile
+    z = torch.tensor(W.beam_normals(drv.n_particles, drv.seed), dtype=torch.float64,
+                     device="cuda")
+    witness = qs.Beam(W.sample_beam(wit))
+    forms = ["fp64", "fp32r"] if args.form == "both" else [args.form]
+    results = {}
+    for form in forms:
+        ctx = qs.Context(qs.config_from_workload(wl, precision=form))
+        th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        tb = torch.tensor(table, dtype=torch.float64, requires_grad=True)
+
+        def one():
+            th.grad = None
+            tb.grad = None
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            L = qs.witness_gain(ctx, th, tb, z, drv.gamma, witness, wl.dt, wl.ppc, r_max)
+            e1.record()
+            L.backward()
+            e2.record()
+            torch.cuda.synchronize()
+            return float(L.detach()), e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+        for _ in range(args.warmup):
+            one()
+        sampler = ClockSampler(local)
+        sampler.start()
+        fwd, bwd = [], []
+        for _ in range(args.steps):
+            L, f, b = one()
+            fwd.append(f)
+            bwd.append(b)
+        clocks = sampler.stop()
+        slices = wl.n_xi
+        results[form] = dict(loss=L, fwd_ms=sum(fwd) / len(fwd), bwd_ms=sum(bwd) / len(bwd),
+                             grad_theta=th.grad.tolist(), grad_table=tb.grad.tolist(),
+                             clocks=clocks)
+        results[form]["value"] = slices / ((results[form]["fwd_ms"] + results[form]["bwd_ms"]) / 1e3)
+        ctx.close()
+    main = "fp32r" if "fp32r" in results else forms[0]
+    r = results[main]
+    out = {
+        "metric": "xi_slices_per_s", "value": r["value"], "unit": "slices/s (gradient evaluations)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["fwd_ms"] + r["bwd_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if main == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": _workload_desc(wl) + ", loss = witness mean energy gain, "
+                   "gradient w.r.t. 8 driver parameters and a 16-value density table, "
+                   "checkpoint every 32 slices", "form": main},
+        "grad_over_fwd": r["bwd_ms"] / r["fwd_ms"] + 1.0,
+        "forms": {k: {kk: v[kk] for kk in ("value", "fwd_ms", "bwd_ms", "loss", "grad_theta",
+                                            "grad_table")} for k, v in results.items()},
+        "clocks": r["clocks"],
+    }
+    print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------------- batched scan
 def run_batched(args):
     """The 48-instance parameter scan (16 each of 128^2, 192^2, 256^2 over
@@ -547,5 +629,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == SCAN:
         run_batched(a)
+    elif a.workload == GRAD:
+        run_grad(a)
     else:
         run_native(a)

@@ -130,3 +130,39 @@ def test_adjoint_needs_a_forward_step(qs):
     with pytest.raises(qs.QsError) as e:
         ctx.step3d_adjoint(None)
     assert e.value.status == qs.QS_ERR_STATE
+
+
+def test_fullsize_directional_derivative(qs):
+    """The 256^2 differentiable case (512 slices, 262,144 plasma particles,
+    500k + 200k bunch particles, 16-value table): the adjoint's directional
+    derivative along a random direction equals the central difference of
+    the CUDA loss (same schedule), float64."""
+    wl = W.workload("grad256")
+    drv, wit = wl.beams
+    theta = np.array([drv.amplitude, drv.sigma_x, drv.sigma_y, drv.sigma_z, drv.x_c, drv.y_c,
+                      drv.xi_c, drv.tilt])
+    table, r_max = np.array(wl.profile[0]), wl.profile[1]
+    z = torch.tensor(W.beam_normals(drv.n_particles, drv.seed), dtype=torch.float64,
+                     device="cuda")
+    witness = qs.Beam(W.sample_beam(wit))
+    ctx = qs.Context(qs.config_from_workload(wl, mg_tol=1e-12))
+    th = torch.tensor(theta, requires_grad=True)
+    tb = torch.tensor(table, requires_grad=True)
+    L = qs.witness_gain(ctx, th, tb, z, drv.gamma, witness, wl.dt, wl.ppc, r_max)
+    m = ctx.slice_diagnostics()[0]
+    L.backward()
+    rng = np.random.default_rng(7)
+    vth = rng.standard_normal(8) * np.maximum(np.abs(theta), 0.1)
+    vtb = rng.standard_normal(len(table)) * 0.05
+    dd = float(th.grad.numpy() @ vth + tb.grad.numpy() @ vtb)
+
+    def loss(t):
+        ctx.init_plasma(wl.ppc, list(table + t * vtb), r_max)
+        b = qs.bigaussian_beam(theta + t * vth, z, drv.gamma)
+        st = ctx.step3d([b, witness], schedule=m)
+        assert st["psi_guard_hits"] == 0
+        return ctx.beam_gain(witness, wl.dt)
+
+    eps = 1e-5
+    fd = (loss(eps) - loss(-eps)) / (2 * eps)
+    assert abs(fd - dd) <= 1e-4 * abs(fd), (fd, dd)
