@@ -444,7 +444,7 @@ def run_batched(args):
                  for wl in insts]
     t0 = time.perf_counter()
     tuned = AT.tune(insts, precision="fp32r", n_slices=16,
-                    cands=AT.candidates(tiles=((32, 16), (64, 32)), sweeps=((2, 2),),
+                    cands=AT.candidates(tiles=((32, 16), (64, 32)), sweeps=((2, 2), (2, 1)),
                                         coarse=(16, 32)))
     team = AT.tune_team(insts, tuned, precision="fp32r", n_slices=16)
     tune_s = time.perf_counter() - t0

@@ -47,7 +47,8 @@ class QsConfig(ctypes.Structure):
         ("trace_capacity", ctypes.c_int),
         ("warm_start_order", ctypes.c_int),
         ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("omega_pct", ctypes.c_int),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 

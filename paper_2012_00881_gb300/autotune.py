@@ -6,7 +6,7 @@ keeps the fastest:
 * the output tile of the grid-wide multigrid levels staged in shared memory
   (tile_x, tile_y, refined form),
 * the red-black sweeps before and after the coarse correction (pre_sweeps,
-  post_sweeps),
+  post_sweeps) and their over-relaxation factor (omega_pct),
 * the side below which a level is relaxed by one thread block
   (coarse_block_n),
 
@@ -31,11 +31,14 @@ from . import _binding as B
 DEFAULT_TILES = ((32, 16), (32, 32), (64, 32))
 DEFAULT_SWEEPS = ((2, 2), (3, 3))
 DEFAULT_COARSE = (16, 32)
+DEFAULT_OMEGAS = (0,)  # 0: the library default
 
 
-def candidates(tiles=DEFAULT_TILES, sweeps=DEFAULT_SWEEPS, coarse=DEFAULT_COARSE) -> List[Dict]:
-    return [dict(tile_x=t[0], tile_y=t[1], pre_sweeps=s[0], post_sweeps=s[1], coarse_block_n=c)
-            for t, s, c in itertools.product(tiles, sweeps, coarse)]
+def candidates(tiles=DEFAULT_TILES, sweeps=DEFAULT_SWEEPS, coarse=DEFAULT_COARSE,
+               omegas=DEFAULT_OMEGAS) -> List[Dict]:
+    return [dict(tile_x=t[0], tile_y=t[1], pre_sweeps=s[0], post_sweeps=s[1], coarse_block_n=c,
+                 omega_pct=o)
+            for t, s, c, o in itertools.product(tiles, sweeps, coarse, omegas)]
 
 
 def _truncated(wl, n_slices: int):

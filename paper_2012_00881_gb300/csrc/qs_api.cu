@@ -163,7 +163,11 @@ int validate(const qs_config *cfg, char *why, size_t nwhy) {
         snprintf(why, nwhy, "tile_x, tile_y must both be 0 or even in [2, 256]");
         return QS_ERR_ARG;
     }
-    for (int i = 0; i < 3; ++i)
+    if (cfg->omega_pct != 0 && (cfg->omega_pct < 50 || cfg->omega_pct > 195)) {
+        snprintf(why, nwhy, "omega_pct must be 0 or in [50, 195]");
+        return QS_ERR_ARG;
+    }
+    for (int i = 0; i < 2; ++i)
         if (cfg->reserved[i] != 0) {
             snprintf(why, nwhy, "reserved fields must be zero");
             return QS_ERR_ARG;
@@ -465,6 +469,7 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
     a.mg_max_vcycles = g.mg_max_vcycles;
     a.nu1 = g.pre_sweeps;
     a.nu2 = g.post_sweeps;
+    a.omega = (g.omega_pct > 0 ? g.omega_pct : QS_DEFAULT_OMEGA_PCT) / 100.0;
     a.np = c->np;
     a.spin_cycles = 4000000000LL;
     a.x = c->x;

@@ -7,6 +7,7 @@
 #include "qs.h"
 
 #define QS_MAX_LEV 12
+#define QS_DEFAULT_OMEGA_PCT 120
 #define QS_ENGINE_THREADS 512
 
 // ---------------------------------------------------------------------------
@@ -69,6 +70,7 @@ struct EngineArgs {
     double mg_tol, mg_atol;
     int mg_max_vcycles;
     int nu1, nu2;
+    double omega;  // over-relaxation factor of the red-black smoother
     int64_t np;
     long long spin_cycles;
     // plasma macroparticles (working copy; the refined form keeps positions

@@ -27,6 +27,7 @@ struct Lvl {
     T *d;  // inverse diagonal 1/(4 + walls + h^2 kappa) (screened) or nullptr
     int n;
     double h2;
+    T omega;  // relaxation factor of the red-black sweeps (1 = Gauss-Seidel)
 };
 
 template <typename T>
@@ -109,9 +110,12 @@ __device__ __forceinline__ T apply_op(const T *u, const T *k, int n, T inv_h2, i
     return r;
 }
 
+// Red-black update of one point: the Gauss-Seidel value g, over-relaxed by
+// omega (u <- u + omega (g - u)).
 template <typename T, int NC>
 __device__ __forceinline__ void gs_point(T *const u0, T *const u1, const T *const f0,
-                                         const T *const f1, T h2, T di, int n, int ix, int iy) {
+                                         const T *const f1, T h2, T di, T omega, int n, int ix,
+                                         int iy) {
     const int i = iy * n + ix;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -121,7 +125,9 @@ __device__ __forceinline__ void gs_point(T *const u0, T *const u1, const T *cons
         if (ix < n - 1) nb += u[i + 1];
         if (iy > 0) nb += u[i - n];
         if (iy < n - 1) nb += u[i + n];
-        u[i] = (nb - h2 * (c ? f1 : f0)[i]) * di;
+        const T g = (nb - h2 * (c ? f1 : f0)[i]) * di;
+        const T uo = u[i];
+        u[i] = uo + omega * (g - uo);
     }
 }
 
@@ -140,7 +146,7 @@ __device__ void relax_half(const Lvl<T> L, int color, Thr R) {
             const int ix = w.col, iy = w.row;
             if (((ix + iy) & 1) != color) continue;
             const T di = dd ? dd[iy * n + ix] : const_inv_diag<T>(walls(ix, iy, n));
-            gs_point<T, NC>(u0, u1, f0, f1, h2, di, n, ix, iy);
+            gs_point<T, NC>(u0, u1, f0, f1, h2, di, L.omega, n, ix, iy);
         }
         return;
     }
@@ -149,7 +155,7 @@ __device__ void relax_half(const Lvl<T> L, int color, Thr R) {
         const int iy = w.row;
         const int ix = 2 * w.col + ((iy + color) & 1);
         const T di = dd ? dd[iy * n + ix] : const_inv_diag<T>(walls(ix, iy, n));
-        gs_point<T, NC>(u0, u1, f0, f1, h2, di, n, ix, iy);
+        gs_point<T, NC>(u0, u1, f0, f1, h2, di, L.omega, n, ix, iy);
     }
 }
 
@@ -343,6 +349,7 @@ __device__ void block_vcycle(const Hier<T> &H, int lg, int nu1, int nu2, void *s
             const int m = H.lv[l].n * H.lv[l].n;
             S[l].n = H.lv[l].n;
             S[l].h2 = H.lv[l].h2;
+            S[l].omega = H.lv[l].omega;
             for (int c = 0; c < 2; ++c) {
                 S[l].u[c] = p;
                 p += m;

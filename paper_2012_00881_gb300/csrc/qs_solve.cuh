@@ -153,6 +153,7 @@ __device__ void hier64(const EngineArgs &A, const SolveSpec &V, Hier<double> &H)
         Lvl<double> &v = H.lv[l];
         v.n = A.lev_n[l];
         v.h2 = A.lev_h2[l];
+        v.omega = A.omega;
         for (int c = 0; c < 2; ++c) {
             v.u[c] = l == 0 ? V.u[c] : A.lev[l].u[c];
             v.f[c] = l == 0 ? V.f[c] : A.lev[l].f[c];
@@ -168,6 +169,7 @@ __device__ void hier32(const EngineArgs &A, const SolveSpec &V, Hier<float> &H) 
         Lvl<float> &v = H.lv[l];
         v.n = A.lev_n[l];
         v.h2 = A.lev_h2[l];
+        v.omega = (float)A.omega;
         for (int c = 0; c < 2; ++c) {
             v.u[c] = l == 0 ? A.e32[c] : A.lev32[l].u[c];
             v.f[c] = l == 0 ? A.r32[0][c] : A.lev32[l].f[c];
@@ -195,7 +197,7 @@ __device__ void relax_half_finalize(const Lvl<float> L, int color, Thr R, double
         const int i = w.q;
         if (((ix + iy) & 1) == color) {
             const float di = L.d ? L.d[i] : qsmg::const_inv_diag<float>(qsmg::walls(ix, iy, n));
-            qsmg::gs_point<float, NC>(u0, u1, f0, f1, h2, di, n, ix, iy);
+            qsmg::gs_point<float, NC>(u0, u1, f0, f1, h2, di, L.omega, n, ix, iy);
         }
         fin0[i] += (double)u0[i];
         if (NC > 1) fin1[i] += (double)u1[i];

@@ -51,7 +51,7 @@ __device__ __forceinline__ Region make_region(int tx0, int ty0, int TX, int TY, 
 template <int NC>
 __device__ void staged_sweeps(const Region &g, int n, float h2, float *const su0,
                               float *const su1, const float *const sf0, const float *const sf1,
-                              const float *const sd, int ns) {
+                              const float *const sd, int ns, float omega) {
     // cells are visited through the in-domain part of the region only
     const int wx = g.bx - g.ax + 1, wy = g.by - g.ay + 1;
     const int RX = g.RX;
@@ -74,7 +74,9 @@ __device__ void staged_sweeps(const Region &g, int n, float h2, float *const su0
                 if (x < n - 1) nb += u[li + 1];
                 if (y > 0) nb += u[li - RX];
                 if (y < n - 1) nb += u[li + RX];
-                u[li] = (nb - h2 * (c ? sf1 : sf0)[li]) * di;
+                const float gv = (nb - h2 * (c ? sf1 : sf0)[li]) * di;
+                const float uo = u[li];
+                u[li] = uo + omega * (gv - uo);
             }
         }
         __syncthreads();
@@ -202,7 +204,7 @@ __device__ void down_level(const Lvl<float> F, const Lvl<float> C, int nu1, int 
         cp_async_wait_all();
         __syncthreads();
         mark(60);
-        staged_sweeps<NC>(g, n, h2, su0, su1, sf0, sf1, sd, 2 * nu1);
+        staged_sweeps<NC>(g, n, h2, su0, su1, sf0, sf1, sd, 2 * nu1, F.omega);
         mark(61);
         // residual on the tile, restricted to the coarse cells it covers
         const int CTX = TX / 2, CTY = TY / 2, cx0 = tx0 / 2, cy0 = ty0 / 2;
@@ -309,7 +311,7 @@ __device__ void up_level(const Lvl<float> F, const float *cu0, const float *cu1,
         const TileSmem t = tile_layout(sm, g.R, TX, TY, Hmax);
         const float *sd;
         stage_up_region<NC>(F, g, t, cu0, cu1, cu_shared, m, &sd);
-        staged_sweeps<NC>(g, n, h2, t.su0, t.su1, t.sf0, t.sf1, sd, 2 * nu2);
+        staged_sweeps<NC>(g, n, h2, t.su0, t.su1, t.sf0, t.sf1, sd, 2 * nu2, F.omega);
         for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
             const int x = tx0 + w.col, y = ty0 + w.row;
             if (x >= n || y >= n) continue;
@@ -378,7 +380,7 @@ __device__ void up_level0_fused(const Lvl<float> F, const float *cu0, const floa
         const float *sd;
         stage_up_region<NC>(F, g, t, cu0, cu1, cu_shared, m, &sd);
         mark(65);
-        staged_sweeps<NC>(g, n, h2, t.su0, t.su1, t.sf0, t.sf1, sd, 2 * nu2);
+        staged_sweeps<NC>(g, n, h2, t.su0, t.su1, t.sf0, t.sf1, sd, 2 * nu2, F.omega);
         mark(66);
         const int RX = g.RX;
         for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
