@@ -100,19 +100,20 @@ def measured_traffic(kernel: str, workload: str, form: str):
     for fn in sorted(os.listdir(d)):
         if not fn.endswith(".md"):
             continue
-        meta = {}
         with open(os.path.join(d, fn)) as f:
             for line in f:
-                if line.startswith("<!-- traffic "):
-                    for kv in line[len("<!-- traffic "):].replace("-->", "").split():
-                        k, _, v = kv.partition("=")
-                        meta[k] = v
-        if (meta.get("kernel") == kernel and meta.get("workload") == workload
-                and meta.get("form") == form and meta.get("source_sha256") == want):
-            try:
-                return float(meta["bytes_per_launch"])
-            except (KeyError, ValueError):
-                return None
+                if not line.startswith("<!-- traffic "):
+                    continue
+                meta = {}
+                for kv in line[len("<!-- traffic "):].replace("-->", "").split():
+                    k, _, v = kv.partition("=")
+                    meta[k] = v
+                if (meta.get("kernel") == kernel and meta.get("workload") == workload
+                        and meta.get("form") == form and meta.get("source_sha256") == want):
+                    try:
+                        return float(meta["bytes_per_launch"])
+                    except (KeyError, ValueError):
+                        return None
     return None
 
 
