@@ -277,6 +277,23 @@ __device__ bool vcycle(const EngineArgs &A, const Sync &S, const Hier<T> &H, int
 // accumulates ||r||^2, ||u||^2 into norms_out (slot of the convergence test),
 // so no separate residual phase is needed; *fused_done reports whether that
 // happened (grids too small to stage fall back to the plain cycle).
+// Output tile of a staged level of side n: the configured tile, halved
+// (the longer side first, down to 8) while the level has fewer than nblk/2
+// tiles, so that coarser grid-wide levels still spread over the blocks and
+// each block's region stays small.
+__device__ __forceinline__ void level_tile(const EngineArgs &A, int n, int nblk, int &TX,
+                                           int &TY) {
+    TX = A.tile_x;
+    TY = A.tile_y;
+    for (;;) {
+        const int tiles = ((n + TX - 1) / TX) * ((n + TY - 1) / TY);
+        if (2 * tiles >= nblk) break;
+        if (TX >= TY && TX > 8) TX >>= 1;
+        else if (TY > 8) TY >>= 1;
+        else break;
+    }
+}
+
 template <int NC>
 __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<float> &H, int bid,
                               int nblk, void *smem, qsmg::CoarseInv ci, double *fin0,
@@ -292,7 +309,9 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
     const qsmg::Marks mk{bid == 0 ? A.trace : nullptr, &A.sc->trace_n, A.trace_cap};
     const int Hmax = 2 * max(A.nu1, A.nu2) + 1;  // the tile layout is sized for this halo
     for (int l = 0; l < lg; ++l) {
-        qstile::down_level<NC>(H.lv[l], H.lv[l + 1], A.nu1, A.tile_x, A.tile_y, Hmax, sm, bid,
+        int TX, TY;
+        level_tile(A, H.lv[l].n, nblk, TX, TY);
+        qstile::down_level<NC>(H.lv[l], H.lv[l + 1], A.nu1, TX, TY, Hmax, sm, bid,
                                nblk, mk);
         mk(62);
         SYNC(30);
@@ -302,10 +321,12 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
     for (int l = lg - 1; l >= 0; --l) {
         const float *cu0 = (l + 1 == lg) ? (const float *)smem : A.lev32[l + 1].up[0];
         const float *cu1 = (l + 1 == lg) ? (const float *)smem + 2 * mg2 : A.lev32[l + 1].up[1];
+        int TX, TY;
+        level_tile(A, H.lv[l].n, nblk, TX, TY);
         if (l == 0 && fused) {
             double nrm[4] = {0.0, 0.0, 0.0, 0.0};
             qstile::up_level0_fused<NC>(H.lv[0], cu0, cu1, l + 1 == lg, H.lv[1].n, A.nu2,
-                                        A.tile_x, A.tile_y, Hmax, sm, bid, nblk, *fused, nrm, mk);
+                                        TX, TY, Hmax, sm, bid, nblk, *fused, nrm, mk);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 double t = block_sum(nrm[c]);
@@ -319,7 +340,7 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
             *fused_done = true;
         } else {
             qstile::up_level<NC>(H.lv[l], cu0, cu1, l + 1 == lg, H.lv[l + 1].n, A.nu2,
-                                 A.tile_x, A.tile_y, Hmax, sm, bid, nblk, A.lev32[l].up[0],
+                                 TX, TY, Hmax, sm, bid, nblk, A.lev32[l].up[0],
                                  A.lev32[l].up[1], l == 0 ? fin0 : nullptr,
                                  l == 0 ? fin1 : nullptr);
         }
