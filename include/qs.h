@@ -101,7 +101,10 @@ typedef struct {
     int omega_pct;              /* red-black smoother over-relaxation, percent: */
                                 /* u += omega (u_GS - u), omega = omega_pct/100 */
                                 /* in [0.5, 1.95]; 0 = default (1.2)            */
-    int reserved[2];            /* must be zero                                  */
+    int coarse_pre_sweeps;      /* pre-sweeps on the levels solved in shared    */
+                                /* memory (side <= coarse_block_n); 0 = same    */
+                                /* as pre_sweeps                                */
+    int reserved[1];            /* must be zero                                  */
 } qs_config;
 
 /* Driver-beam macroparticles: structure of arrays of float64, n entries each.
@@ -133,8 +136,8 @@ typedef struct {
 
 /* Defaults: N = 64 on [-6,6]^2, 128 slices on [0,12], refine_k = 8,
  * QS_FP64, mg_tol = 1e-10, 60 V-cycles, psi_floor = 1e-3, unlimited guard
- * hits, sort_every = 16, V(2,2) red-black sweeps over-relaxed by 1.2,
- * warm_start_order = 2. */
+ * hits, sort_every = 16, V(2,2) red-black sweeps over-relaxed by 1.2 with
+ * one pre-sweep on the shared-memory levels, warm_start_order = 2. */
 void qs_config_default(qs_config *cfg);
 
 /* Create a context on the current CUDA device; `cuda_stream` is a

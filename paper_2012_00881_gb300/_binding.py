@@ -48,7 +48,8 @@ class QsConfig(ctypes.Structure):
         ("warm_start_order", ctypes.c_int),
         ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
         ("omega_pct", ctypes.c_int),
-        ("reserved", ctypes.c_int * 2),
+        ("coarse_pre_sweeps", ctypes.c_int),
+        ("reserved", ctypes.c_int * 1),
     ]
 
 

@@ -167,7 +167,11 @@ int validate(const qs_config *cfg, char *why, size_t nwhy) {
         snprintf(why, nwhy, "omega_pct must be 0 or in [50, 195]");
         return QS_ERR_ARG;
     }
-    for (int i = 0; i < 2; ++i)
+    if (cfg->coarse_pre_sweeps < 0 || cfg->coarse_pre_sweeps > 8) {
+        snprintf(why, nwhy, "coarse_pre_sweeps must be in [0, 8]");
+        return QS_ERR_ARG;
+    }
+    for (int i = 0; i < 1; ++i)
         if (cfg->reserved[i] != 0) {
             snprintf(why, nwhy, "reserved fields must be zero");
             return QS_ERR_ARG;
@@ -247,8 +251,8 @@ int create_impl(qs_ctx *c) {
     c->tile_y = ref ? (g.tile_y > 0 ? g.tile_y : 16) : 0;
     const int nu = g.pre_sweeps > g.post_sweeps ? g.pre_sweeps : g.post_sweeps;
     c->engine_smem = qs_engine_smem_bytes(c->lev_n, c->nlev, c->block_level_n, g.precision,
-                                          c->tile_x, c->tile_y, nu, &c->block_offset,
-                                          &c->tile_offset);
+                                          c->tile_x, c->tile_y, nu, g.post_sweeps,
+                                          &c->block_offset, &c->tile_offset);
     if (c->engine_smem > 220 * 1024)
         return fail(c, QS_ERR_ARG,
                     "coarse_block_n = %d with %d x %d tiles needs %zu bytes of shared memory",
@@ -294,6 +298,7 @@ void qs_config_default(qs_config *cfg) {
     cfg->sort_every = 16;
     cfg->pre_sweeps = 2;
     cfg->post_sweeps = 2;
+    cfg->coarse_pre_sweeps = 1;
     cfg->warm_start_order = 2;
 }
 
@@ -469,6 +474,7 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
     a.mg_max_vcycles = g.mg_max_vcycles;
     a.nu1 = g.pre_sweeps;
     a.nu2 = g.post_sweeps;
+    a.nu1c = g.coarse_pre_sweeps > 0 ? g.coarse_pre_sweeps : g.pre_sweeps;
     a.omega = (g.omega_pct > 0 ? g.omega_pct : QS_DEFAULT_OMEGA_PCT) / 100.0;
     a.np = c->np;
     a.spin_cycles = 4000000000LL;

@@ -561,7 +561,7 @@ int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *bloc
 }
 
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
-                            int tile_x, int tile_y, int nu, size_t *block_offset,
+                            int tile_x, int tile_y, int nu, int nu2, size_t *block_offset,
                             size_t *tile_offset) {
     int lg = 0;
     while (lg < nlev - 1 && lev_n[lg] > block_level_n) ++lg;
@@ -573,7 +573,7 @@ size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int p
     if (tile_offset) *tile_offset = b;  // relative to the block part
     size_t total = inv + b;
     if (precision == QS_FP32_REFINED && tile_x > 0)
-        total += qstile::tile_smem_bytes(tile_x, tile_y, nu);
+        total += qstile::tile_smem_bytes(tile_x, tile_y, nu, nu2);
     return total + 256;
 }
 

@@ -70,6 +70,7 @@ struct EngineArgs {
     double mg_tol, mg_atol;
     int mg_max_vcycles;
     int nu1, nu2;
+    int nu1c;      // pre-sweeps on the levels solved in shared memory
     double omega;  // over-relaxation factor of the red-black smoother
     int64_t np;
     long long spin_cycles;
@@ -269,5 +270,5 @@ cudaError_t qs_launch_adjoint(cudaStream_t st, const EngineArgs &a, const AdjArg
 int qs_adjoint_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
 int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
-                            int tile_x, int tile_y, int nu, size_t *block_offset,
+                            int tile_x, int tile_y, int nu, int nu2, size_t *block_offset,
                             size_t *tile_offset);

@@ -226,7 +226,7 @@ __device__ bool vcycle(const EngineArgs &A, const Sync &S, const Hier<T> &H, int
         qsmg::restrict_res<T, NC>(F, C, T0);
         SYNC(12);
     }
-    if (bid == 0) qsmg::block_vcycle<T, NC>(H, lg, A.nu1, A.nu2, smem, ci);
+    if (bid == 0) qsmg::block_vcycle<T, NC>(H, lg, A.nu1c, A.nu2, smem, ci);
     SYNC(13);
     if constexpr (sizeof(T) == 4) {
         if (fin0 && (lg == 0 || A.nu2 == 0)) {
@@ -316,8 +316,29 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
         mk(62);
         SYNC(30);
     }
-    qsmg::block_vcycle<float, NC>(H, lg, A.nu1, A.nu2, smem, ci, false, mk);
+    qsmg::block_vcycle<float, NC>(H, lg, A.nu1c, A.nu2, smem, ci, false, mk);
     const int mg2 = H.lv[lg].n * H.lv[lg].n;
+    if (fused) {
+        // every up leg and the level-0 update in one phase
+        int TX, TY;
+        level_tile(A, H.lv[0].n, nblk, TX, TY);
+        double nrm[4] = {0.0, 0.0, 0.0, 0.0};
+        qstile::up_cascade_fused<NC>(H, lg, (const float *)smem, (const float *)smem + 2 * mg2,
+                                     A.nu2, TX, TY, sm, bid, nblk, *fused, nrm, mk);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            double t = block_sum(nrm[c]);
+            if (threadIdx.x == 0) atomicAdd(norms_out + c, t);
+            t = block_sum(nrm[2 + c]);
+            if (threadIdx.x == 0) atomicAdd(norms_out + 2 + c, t);
+        }
+        if (bid == 0 && threadIdx.x == 0)
+            for (int e = 0; e < 4; ++e) norms_clear[e] = 0.0;
+        mk(67);
+        *fused_done = true;
+        SYNC(32);
+        return true;
+    }
     for (int l = lg - 1; l >= 0; --l) {
         const float *cu0 = (l + 1 == lg) ? (const float *)smem : A.lev32[l + 1].up[0];
         const float *cu1 = (l + 1 == lg) ? (const float *)smem + 2 * mg2 : A.lev32[l + 1].up[1];

@@ -131,13 +131,79 @@ __device__ __forceinline__ TileSmem tile_layout(float *sm, int R, int TX, int TY
     return t;
 }
 
-// Shared memory (bytes) for one staged tile (nu = the larger sweep count).
-__host__ __device__ inline size_t tile_smem_bytes(int TX, int TY, int nu) {
-    const int H = 2 * nu + 1;
-    const int Rmax = (TX + 2 * H) * (TY + 2 * H);
-    const size_t f = ((size_t)(6 * Rmax + 2 * coarse_window_floats(TX, TY, H)) * sizeof(float) +
-                      15) & ~(size_t)15;
-    return f + (size_t)5 * TX * TY * sizeof(double);
+// Region and coarse-window sizes (cells) of the up cascade for a level-0
+// tile TX x TY and nu2 post-sweeps: the level-0 region is the tile plus a
+// halo 2 nu2 + 1; each coarser level needs the window of coarse cells that
+// the finer region prolongs from (at most half its width plus 3), staged
+// with a halo 2 nu2.  The widths converge to 6 + 8 nu2, so a fixed number of
+// levels bounds them.
+__host__ __device__ inline void cascade_bounds(int TX, int TY, int nu2, int &rbig, int &wbig) {
+    int x = TX + 2 * (2 * nu2 + 1), y = TY + 2 * (2 * nu2 + 1);
+    rbig = x * y;
+    wbig = 0;
+    for (int l = 1; l < 16; ++l) {
+        const int wx = x / 2 + 3, wy = y / 2 + 3;
+        wbig = wbig > wx * wy ? wbig : wx * wy;
+        x = wx + 4 * nu2;
+        y = wy + 4 * nu2;
+        rbig = rbig > x * y ? rbig : x * y;
+    }
+}
+
+// Layout of the up cascade: six region arrays, two ping-pong coarse windows
+// of two components, float64 copies of the level-0 tile.
+struct CascadeSmem {
+    float *su0, *su1, *sf0, *sf1, *sd;
+    float *win;  // window buffer b, component c at win + (2 b + c) * wbig
+    int wbig;
+    double *du0, *du1, *dr0, *dr1, *dk;
+};
+
+__device__ __forceinline__ CascadeSmem cascade_layout(float *sm, int R, int TX, int TY,
+                                                      int nu2) {
+    int rbig, wbig;
+    cascade_bounds(TX, TY, nu2, rbig, wbig);
+    CascadeSmem t;
+    t.su0 = sm;
+    t.su1 = sm + R;
+    t.sf0 = sm + 2 * R;
+    t.sf1 = sm + 3 * R;
+    t.sd = sm + 5 * R;
+    t.win = sm + 6 * rbig;
+    t.wbig = wbig;
+    const size_t off = ((size_t)(6 * rbig + 4 * wbig) * sizeof(float) + 15) & ~(size_t)15;
+    double *d = (double *)((char *)sm + off);
+    const int T = TX * TY;
+    t.du0 = d;
+    t.du1 = d + T;
+    t.dr0 = d + 2 * T;
+    t.dr1 = d + 3 * T;
+    t.dk = d + 4 * T;
+    return t;
+}
+
+// Shared memory (bytes) for the staged legs with tile TX x TY and any tile
+// obtained from it by halving sides down to 8 (nu = the larger sweep count,
+// nu2 = post-sweeps).
+__host__ __device__ inline size_t tile_smem_bytes(int TX, int TY, int nu, int nu2) {
+    size_t best = 0;
+    for (int tx = TX, ty = TY;;) {
+        const int H = 2 * nu + 1;
+        const int Rmax = (tx + 2 * H) * (ty + 2 * H);
+        size_t a = ((size_t)(6 * Rmax + 2 * coarse_window_floats(tx, ty, H)) * sizeof(float) +
+                    15) & ~(size_t)15;
+        a += (size_t)5 * tx * ty * sizeof(double);
+        int rbig, wbig;
+        cascade_bounds(tx, ty, nu2, rbig, wbig);
+        size_t b = ((size_t)(6 * rbig + 4 * wbig) * sizeof(float) + 15) & ~(size_t)15;
+        b += (size_t)5 * tx * ty * sizeof(double);
+        best = best > a ? best : a;
+        best = best > b ? best : b;
+        if (tx >= ty && tx > 8) tx >>= 1;
+        else if (ty > 8) ty >>= 1;
+        else break;
+    }
+    return best;
 }
 
 // Bilinear cell-centred interpolation (odd ghosts) of a coarse array of side
@@ -381,6 +447,172 @@ __device__ void up_level0_fused(const Lvl<float> F, const float *cu0, const floa
         stage_up_region<NC>(F, g, t, cu0, cu1, cu_shared, m, &sd);
         mark(65);
         staged_sweeps<NC>(g, n, h2, t.su0, t.su1, t.sf0, t.sf1, sd, 2 * nu2, F.omega);
+        mark(66);
+        const int RX = g.RX;
+        for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
+            const int x = tx0 + w.col, y = ty0 + w.row;
+            if (x >= n || y >= n) continue;
+            const int li = (y - g.oy) * RX + (x - g.ox);
+            const int gi = y * n + x;
+            const int nw = qsmg::walls(x, y, n);
+            const double kk = kap ? t.dk[w.q] : 0.0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float *e = c ? t.su1 : t.su0;
+                const double ec = (double)e[li];
+                double nb = 0.0;
+                if (x > 0) nb += (double)e[li - 1];
+                if (x < n - 1) nb += (double)e[li + 1];
+                if (y > 0) nb += (double)e[li - RX];
+                if (y < n - 1) nb += (double)e[li + RX];
+                const double ae = (nb - (double)(4 + nw) * ec) * inv_h2 - kk * ec;
+                const double u = (c ? t.du1 : t.du0)[w.q] + ec;
+                const double r = (c ? t.dr1 : t.dr0)[w.q] - ae;
+                (c ? u64_1 : u64_0)[gi] = u;
+                (c ? r64_1 : r64_0)[gi] = r;
+                (c ? r32_1 : r32_0)[gi] = (float)r;
+                norms[c] += r * r;
+                norms[2 + c] += u * u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Up cascade: the up legs of every staged level and the fused level-0 update
+// in one grid phase.
+//
+// The separate up legs cost a grid barrier and a global round trip per
+// level.  Here each block starts from the coarse correction of the first
+// block-local level (held, complete, in its shared memory after the
+// redundant coarse part) and walks up to level 0 for its own level-0 tile.
+// At level l it needs the corrected values only on the window of level-l
+// cells that the finer region prolongs from; it stages that window plus a
+// halo of 2 nu2 (pre-smoothed u, f, inverse diagonal), adds the prolongated
+// correction, sweeps, and keeps the window, which is exact.  The level-0
+// region is the tile plus a halo 2 nu2 + 1, as in up_level0_fused.
+// ---------------------------------------------------------------------------
+
+// coarse window of an in-domain box [ax, bx] x [ay, by] at a level of side m
+__device__ __forceinline__ void coarse_window(const Region &g, int m, int &wx0, int &wy0,
+                                              int &wx1, int &wy1) {
+    wx0 = max((g.ax >> 1) - 1, 0);
+    wy0 = max((g.ay >> 1) - 1, 0);
+    wx1 = min((g.bx >> 1) + 1, m - 1);
+    wy1 = min((g.by >> 1) + 1, m - 1);
+}
+
+// region of cascade level l for the level-0 tile at (tx0, ty0)
+__device__ __forceinline__ Region cascade_region(const qsmg::Hier<float> &Hh, int l, int tx0,
+                                                 int ty0, int TX, int TY, int nu2) {
+    Region g = make_region(tx0, ty0, TX, TY, 2 * nu2 + 1, Hh.lv[0].n);
+    for (int k = 1; k <= l; ++k) {
+        int wx0, wy0, wx1, wy1;
+        coarse_window(g, Hh.lv[k].n, wx0, wy0, wx1, wy1);
+        g = make_region(wx0, wy0, wx1 - wx0 + 1, wy1 - wy0 + 1, 2 * nu2, Hh.lv[k].n);
+    }
+    return g;
+}
+
+// stage u, f (and the inverse diagonal) of level F on region g and add the
+// prolongation of the coarse correction held as a window (origin sox, soy,
+// pitch sp) of a level of side m; ends with a block barrier
+template <int NC>
+__device__ void stage_cascade(const Lvl<float> F, const Region &g, const CascadeSmem &t,
+                              const float *src0, const float *src1, int sox, int soy, int sp,
+                              int m) {
+    const int n = F.n;
+    const bool scr = F.d != nullptr;
+    for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
+        const int x = g.ox + w.col, y = g.oy + w.row;
+        const bool in = x >= 0 && x < n && y >= 0 && y < n;
+        const int gi = in ? y * n + x : 0, li = w.q;
+        if (scr) cp_async_f32(t.sd + li, F.d + gi, in);
+        cp_async_f32(t.su0 + li, F.u[0] + gi, in);
+        cp_async_f32(t.sf0 + li, F.f[0] + gi, in);
+        if (NC > 1) {
+            cp_async_f32(t.su1 + li, F.u[1] + gi, in);
+            cp_async_f32(t.sf1 + li, F.f[1] + gi, in);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int wx = g.bx - g.ax + 1, wy = g.by - g.ay + 1;
+    for (Walk w(threadIdx.x, blockDim.x, wx); w.q < wx * wy; w.next()) {
+        const int x = g.ax + w.col, y = g.ay + w.row;
+        const int li = (y - g.oy) * g.RX + (x - g.ox);
+        t.su0[li] += bilinear_win(src0, sox, soy, sp, m, x, y);
+        if (NC > 1) t.su1[li] += bilinear_win(src1, sox, soy, sp, m, x, y);
+    }
+    __syncthreads();
+}
+
+// cs0, cs1: the correction of level lg (side H.lv[lg].n), complete, in this
+// block's shared memory.
+template <int NC>
+__device__ void up_cascade_fused(const qsmg::Hier<float> &Hh, int lg, const float *cs0,
+                                 const float *cs1, int nu2, int TX, int TY, float *sm, int bid,
+                                 int nblk, const Fused &o, double norms[4],
+                                 qsmg::Marks mark = qsmg::Marks{nullptr, nullptr, 0}) {
+    const int n = Hh.lv[0].n;
+    const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
+    double *const u64_0 = o.u64[0], *const u64_1 = o.u64[NC - 1];
+    double *const r64_0 = o.r64[0], *const r64_1 = o.r64[NC - 1];
+    float *const r32_0 = o.r32[0], *const r32_1 = o.r32[NC - 1];
+    const double *const kap = o.kap;
+    const double inv_h2 = o.inv_h2;
+    for (int tile = bid; tile < ntx * nty; tile += nblk) {
+        const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
+        const float *src0 = cs0, *src1 = cs1;
+        int sox = 0, soy = 0, sp = Hh.lv[lg].n, cur = 0;
+        for (int l = lg - 1; l >= 1; --l) {
+            const Lvl<float> F = Hh.lv[l];
+            const Region g = cascade_region(Hh, l, tx0, ty0, TX, TY, nu2);
+            const CascadeSmem t = cascade_layout(sm, g.R, TX, TY, nu2);
+            stage_cascade<NC>(F, g, t, src0, src1, sox, soy, sp, Hh.lv[l + 1].n);
+            staged_sweeps<NC>(g, F.n, (float)F.h2, t.su0, t.su1, t.sf0, t.sf1,
+                              F.d ? t.sd : nullptr, 2 * nu2, F.omega);
+            // keep the window that the next finer region prolongs from
+            const Region gf = cascade_region(Hh, l - 1, tx0, ty0, TX, TY, nu2);
+            int wx0, wy0, wx1, wy1;
+            coarse_window(gf, F.n, wx0, wy0, wx1, wy1);
+            const int wpx = wx1 - wx0 + 1, wpy = wy1 - wy0 + 1;
+            float *const w0 = t.win + (2 * cur) * t.wbig;
+            float *const w1 = w0 + t.wbig;
+            for (Walk w(threadIdx.x, blockDim.x, wpx); w.q < wpx * wpy; w.next()) {
+                const int li = (wy0 + w.row - g.oy) * g.RX + (wx0 + w.col - g.ox);
+                w0[w.q] = t.su0[li];
+                if (NC > 1) w1[w.q] = t.su1[li];
+            }
+            __syncthreads();
+            src0 = w0;
+            src1 = w1;
+            sox = wx0;
+            soy = wy0;
+            sp = wpx;
+            cur ^= 1;
+        }
+        // level 0
+        const Lvl<float> F = Hh.lv[0];
+        const Region g = cascade_region(Hh, 0, tx0, ty0, TX, TY, nu2);
+        const CascadeSmem t = cascade_layout(sm, g.R, TX, TY, nu2);
+        for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
+            const int x = tx0 + w.col, y = ty0 + w.row;
+            const bool in = x < n && y < n;
+            const int gi = in ? y * n + x : 0;
+            cp_async_f64(t.du0 + w.q, u64_0 + gi, in);
+            cp_async_f64(t.dr0 + w.q, r64_0 + gi, in);
+            if (NC > 1) {
+                cp_async_f64(t.du1 + w.q, u64_1 + gi, in);
+                cp_async_f64(t.dr1 + w.q, r64_1 + gi, in);
+            }
+            if (kap) cp_async_f64(t.dk + w.q, kap + gi, in);
+        }
+        stage_cascade<NC>(F, g, t, src0, src1, sox, soy, sp, Hh.lv[1].n);
+        mark(65);
+        staged_sweeps<NC>(g, n, (float)F.h2, t.su0, t.su1, t.sf0, t.sf1, F.d ? t.sd : nullptr,
+                          2 * nu2, F.omega);
         mark(66);
         const int RX = g.RX;
         for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
