@@ -157,8 +157,9 @@ __device__ void phase_moments(const EngineArgs &A, const PS<P> &Q, Thr T) {
         const double a = guard(1.0 + cic_gather(A.psi, cd), A.psi_floor, hits);
         const P px = Q.px[p], py = Q.py[p];
         const double p2 = (double)px * px + (double)py * py;
-        const P ap = (P)a;
-        const P vx = px / ap, vy = py / ap;
+        const double ia = 1.0 / a;  // one division per particle (FP64 divides are slow)
+        const P iap = (P)ia;
+        const P vx = px * iap, vy = py * iap;
         const P wq = Q.w[p] * s;
         dep(Q.jx, c, wq * vx);
         dep(Q.jy, c, wq * vy);
@@ -166,10 +167,10 @@ __device__ void phase_moments(const EngineArgs &A, const PS<P> &Q, Thr T) {
         dep(Q.txy, c, wq * vx * vy);
         dep(Q.tyy, c, wq * vy * vy);
         if constexpr (sizeof(P) == 8) {
-            dep(Q.G, c, wq * ((1.0 + p2 + a * a) / (2.0 * a)));  // gamma
+            dep(Q.G, c, wq * ((1.0 + p2 + a * a) * (0.5 * ia)));  // gamma
         } else {
             const double am1 = a - 1.0;  // gamma - 1 = (p^2 + psi^2) / (2 (1 + psi))
-            dep(Q.G, c, wq * (P)((p2 + am1 * am1) / (2.0 * a)));
+            dep(Q.G, c, wq * (P)((p2 + am1 * am1) * (0.5 * ia)));
         }
     }
     add_hits(A.sc, hits);
@@ -226,8 +227,9 @@ __device__ void phase_assemble1(const EngineArgs &A, const PS<P> &Q, const doubl
         double a = guard(1.0 + A.psi[i], A.psi_floor, hits);
         double jzb = q == 0 ? J0[i] : (1.0 - frac) * J0[i] + frac * (J1 ? J1[i] : 0.0);
         const double nv = ncur[i];
-        A.jz[i] = g_total(Q.G, ncur, i) / a - nv + jzb;
-        const double kap = nv / a;
+        const double ia = 1.0 / a;
+        A.jz[i] = g_total(Q.G, ncur, i) * ia - nv + jzb;
+        const double kap = nv * ia;
         A.kap[i] = kap;
         const int nw = qsmg::walls(ix, iy, n);
         if (A.precision == QS_FP32_REFINED) {
@@ -266,12 +268,13 @@ __device__ void phase_assemble2(const EngineArgs &A, const PS<P> &Q, const doubl
         const double jx = Q.jx[i], jy = Q.jy[i], txx = Q.txx[i], txy = Q.txy[i],
                      tyy = Q.tyy[i], G = g_total(Q.G, ncur, i), ez = A.ez[i], bz = A.bz[i];
         const double gx = A.dpx[i], gy = A.dpy[i];
+        const double ia = 1.0 / a, Gia2 = G * ia * ia;
         double sx = dx0(A.jz, n, ix, i, inv2h) - dx0(Q.txx, n, ix, i, inv2h) -
-                    dy0(Q.txy, n, iy, i, inv2h) - jy * bz / a + G * gx / (a * a) - jx * ez / a -
-                    (txx * gx + txy * gy) / a;
+                    dy0(Q.txy, n, iy, i, inv2h) + Gia2 * gx -
+                    (jy * bz + jx * ez + txx * gx + txy * gy) * ia;
         double sy = dy0(A.jz, n, iy, i, inv2h) - dx0(Q.txy, n, ix, i, inv2h) -
-                    dy0(Q.tyy, n, iy, i, inv2h) + jx * bz / a + G * gy / (a * a) - jy * ez / a -
-                    (txy * gx + tyy * gy) / a;
+                    dy0(Q.tyy, n, iy, i, inv2h) + Gia2 * gy +
+                    (jx * bz - jy * ez - txy * gx - tyy * gy) * ia;
         A.f_bx[i] = sy;
         A.f_by[i] = -sx;
         sbx += sy * sy;
@@ -335,26 +338,27 @@ __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, b
         const Cic cd = cic_stencil(x, y, A.x_min, A.y_min, A.h, A.N);
         const CicP<P> c = cic_p<P>(cd);
         const double a = guard(1.0 + cic_gather(A.psi, cd), A.psi_floor, hits);
-        const P ap = (P)a;
+        const double ia = 1.0 / a;
+        const P iap = (P)ia;
         const P gx = gat<P>(A.dpx, c), gy = gat<P>(A.dpy, c);
         const P bx = gat<P>(A.bx, c), by = gat<P>(A.by, c), bz = gat<P>(A.bz, c);
         P px = Q.px[p], py = Q.py[p];
         // half kick: gamma grad psi / (1+psi) + e_z x B_perp
-        const double gam = (1.0 + (double)px * px + (double)py * py + a * a) / (2.0 * a);
-        const P pxm = px + half * ((P)gam * gx / ap - by);
-        const P pym = py + half * ((P)gam * gy / ap + bx);
+        const double gam = (1.0 + (double)px * px + (double)py * py + a * a) * (0.5 * ia);
+        const P pxm = px + half * ((P)gam * gx * iap - by);
+        const P pym = py + half * ((P)gam * gy * iap + bx);
         // rotation by the B_z term (e_z x p) B_z / (1+psi)
-        const P tau = half * bz / ap;
+        const P tau = half * bz * iap;
         const P pxp = pxm - tau * pym;
         const P pyp = pym + tau * pxm;
         const P sr = P(2) * tau / (P(1) + tau * tau);
         const P pxr = pxm - sr * pyp;
         const P pyr = pym + sr * pxp;
-        const double gam2 = (1.0 + (double)pxr * pxr + (double)pyr * pyr + a * a) / (2.0 * a);
-        px = pxr + half * ((P)gam2 * gx / ap - by);
-        py = pyr + half * ((P)gam2 * gy / ap + bx);
-        double nx = x + (double)(dxp * px / ap);
-        double ny = y + (double)(dxp * py / ap);
+        const double gam2 = (1.0 + (double)pxr * pxr + (double)pyr * pyr + a * a) * (0.5 * ia);
+        px = pxr + half * ((P)gam2 * gx * iap - by);
+        py = pyr + half * ((P)gam2 * gy * iap + bx);
+        double nx = x + (double)(dxp * px * iap);
+        double ny = y + (double)(dxp * py * iap);
         if (nx > A.x_max) { nx = 2.0 * A.x_max - nx; px = -px; }
         if (nx < A.x_min) { nx = 2.0 * A.x_min - nx; px = -px; }
         if (ny > A.y_max) { ny = 2.0 * A.y_max - ny; py = -py; }
@@ -363,7 +367,7 @@ __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, b
         Q.y[p] = ny;
         Q.px[p] = px;
         Q.py[p] = py;
-        vmax = fmax(vmax, sqrt((double)px * px + (double)py * py) / a);
+        vmax = fmax(vmax, sqrt((double)px * px + (double)py * py) * ia);
         const Cic c2 = cic_stencil(nx, ny, A.x_min, A.y_min, A.h, A.N);
         cic_deposit(nnext, c2, Q.wd[p] * s);
     }
