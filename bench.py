@@ -68,6 +68,24 @@ def _dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value: float, device="cpu") -> float:
+    """The largest `value` over the ranks of the default process group (the
+    job's time is the slowest rank's); the value itself with no group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput of replicas (weak scaling): every rank processed
+    `units_per_rank` units; the job took the slowest rank's time."""
+    return units_per_rank * world / max_seconds
+
+
 def _workload_desc(wl):
     beams = ", ".join(f"n_b={b.amplitude:g} sigma_r={b.sigma_x:g} sigma_z={b.sigma_z:g} "
                       f"xi_c={b.xi_c:g} N={b.n_particles}" for b in wl.beams)
@@ -262,11 +280,7 @@ def run_native(args):
             max_m = max(max_m, st["max_m"])
             bytes_alg += algorithmic_bytes(st, wl, 8 if form == "fp64" else 4, wl.n_xi)
         clocks = sampler.stop()
-        total_ms = sum(times)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(times), dev)
         # end to end through the public API with host buffers
         host = [{k: torch.as_tensor(b[k]).pin_memory() for k in qs.Beam.KEYS} for b in beams_np]
         back = [{k: torch.empty_like(h[k]).pin_memory() for k in qs.Beam.KEYS} for h in host]
@@ -287,8 +301,8 @@ def run_native(args):
         eng_s = sum(engine_ms) / 1e3
         achieved = bytes_alg / eng_s / 1e9
         results[form] = dict(
-            value=slices * world / (total_ms / 1e3),
-            pushes_per_s=pushes * world / (total_ms / 1e3),
+            value=job_rate(slices, world, total_ms / 1e3),
+            pushes_per_s=job_rate(pushes, world, total_ms / 1e3),
             ms_per_step=total_ms / args.steps,
             slices_per_step=slices / args.steps,
             vcycles_per_step=[v / args.steps for v in vc],
@@ -497,11 +511,7 @@ def run_batched(args):
             pushes += s_["pushes"]
             bytes_alg += algorithmic_bytes(s_, wl, 4, wl.n_xi)
     clocks = sampler.stop()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), dev)
     # end to end: beams from pinned host memory each step, read back after
     host = [[{k: torch.as_tensor(b[k]).pin_memory() for k in qs.Beam.KEYS} for b in bn]
             for bn in beams_np]
@@ -531,7 +541,7 @@ def run_batched(args):
             torch.distributed.destroy_process_group()
         return
     out = {
-        "metric": METRIC, "value": slices * world / (total_ms / 1e3), "unit": UNIT,
+        "metric": METRIC, "value": job_rate(slices, world, total_ms / 1e3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -544,7 +554,7 @@ def run_batched(args):
                    "team_blocks": team,
                    "tune_seconds": tune_s,
                    "l2": "history and beam grids larger than L2; 256 MB write between steps"},
-        "pushes_per_s": pushes * world / (total_ms / 1e3),
+        "pushes_per_s": job_rate(pushes, world, total_ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": None,
                      "kernel": "slice_engine_batched", "peak_source": "measured",
