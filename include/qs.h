@@ -104,7 +104,10 @@ typedef struct {
     int coarse_pre_sweeps;      /* pre-sweeps on the levels solved in shared    */
                                 /* memory (side <= coarse_block_n); 0 = same    */
                                 /* as pre_sweeps                                */
-    int reserved[1];            /* must be zero                                  */
+    int checkpoint_every;       /* > 0: qs_step3d also stores the plasma state  */
+                                /* every this many base slices, which           */
+                                /* qs_step3d_adjoint then uses instead of a     */
+                                /* replay; 0 = off                              */
 } qs_config;
 
 /* Driver-beam macroparticles: structure of arrays of float64, n entries each.
@@ -230,7 +233,9 @@ int qs_push_beam(qs_ctx *ctx, qs_beam *beams, int n_beams, double dt);
  * the forward solves with the cotangents as sources), the reverse of the
  * source S of Eq. FluxCurr1_A, and the adjoint of each CIC deposit (a
  * gather) and gather (a deposit).  Memory: the plasma state is stored every
- * `checkpoint_every` base slices (0 = 32) by one forward replay, and each
+ * `checkpoint_every` base slices (0 = 32) by one forward replay (skipped when
+ * the last qs_step3d already stored them: config.checkpoint_every > 0 and
+ * equal to this argument, or this argument 0), and each
  * segment is recomputed from its checkpoint before its reverse pass, which
  * holds every slice of the segment (4 floats per particle and 12 grids per
  * slice, float64).  Library-owned scratch is allocated and freed inside

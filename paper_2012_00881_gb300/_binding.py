@@ -49,7 +49,7 @@ class QsConfig(ctypes.Structure):
         ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
         ("omega_pct", ctypes.c_int),
         ("coarse_pre_sweeps", ctypes.c_int),
-        ("reserved", ctypes.c_int * 1),
+        ("checkpoint_every", ctypes.c_int),
     ]
 
 

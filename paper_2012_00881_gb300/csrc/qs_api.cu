@@ -53,6 +53,11 @@ struct qs_ctx {
     float *g32[6] = {};  // refined form: jx, jy, txx, txy, tyy, G
     std::vector<void *> plasma_allocs;
     bool have_plasma = false, have_step = false;
+    // plasma checkpoints of the last qs_step3d (config.checkpoint_every > 0)
+    double *ckpt = nullptr;
+    size_t ckpt_count = 0;
+    int ckpt_every = 0;
+    bool ckpt_valid = false;
     int engine_blocks = 0;
     size_t engine_smem = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -171,11 +176,10 @@ int validate(const qs_config *cfg, char *why, size_t nwhy) {
         snprintf(why, nwhy, "coarse_pre_sweeps must be in [0, 8]");
         return QS_ERR_ARG;
     }
-    for (int i = 0; i < 1; ++i)
-        if (cfg->reserved[i] != 0) {
-            snprintf(why, nwhy, "reserved fields must be zero");
-            return QS_ERR_ARG;
-        }
+    if (cfg->checkpoint_every < 0) {
+        snprintf(why, nwhy, "checkpoint_every must be >= 0");
+        return QS_ERR_ARG;
+    }
     return QS_OK;
 }
 
@@ -328,6 +332,7 @@ void qs_destroy(qs_ctx *c) {
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
+    if (c->ckpt) cudaFree(c->ckpt);
     free_list(c->plasma_allocs);
     free_list(c->allocs);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -348,6 +353,7 @@ int qs_init_plasma(qs_ctx *c, int ppc, const double *profile, int n_coef, double
     CK(cudaStreamSynchronize(c->st), "sync");
     free_list(c->plasma_allocs);
     c->have_plasma = c->have_step = false;
+    c->ckpt_valid = false;
     auto &L = c->plasma_allocs;
     AL(L, c->t_x, np);
     AL(L, c->t_y, np);
@@ -608,15 +614,34 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
                      qs_step_stats *stats) {
     if (check_ctx(c)) return QS_ERR_ARG;
     EngineArgs a;
+    c->ckpt_valid = false;
     int r = step_prepare(c, beams, n_beams, sched, c->st, a);
     if (r != QS_OK) return r;
+    const int K = c->cfg.checkpoint_every;
+    if (K > 0) {  // plasma checkpoints for a later qs_step3d_adjoint
+        const size_t need = (size_t)((c->cfg.n_xi + K - 1) / K) * 4 * c->np;
+        if (c->ckpt_count < need) {
+            if (c->ckpt) cudaFree(c->ckpt);
+            c->ckpt = nullptr;
+            c->ckpt_count = 0;
+            CK(cudaMalloc(&c->ckpt, need * sizeof(double)), "cudaMalloc checkpoints");
+            c->ckpt_count = need;
+        }
+        a.ckpt_every = K;
+        a.ckpt = c->ckpt;
+    }
     CK(cudaEventRecord(c->ev0, c->st), "event");
     CK(qs_launch_engine(c->st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
     CK(cudaEventRecord(c->ev1, c->st), "event");
     CK(cudaStreamSynchronize(c->st), "slice engine");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    return step_finish(c, stats, ms);
+    r = step_finish(c, stats, ms);
+    if (r == QS_OK && K > 0) {
+        c->ckpt_valid = true;
+        c->ckpt_every = K;
+    }
+    return r;
 }
 
 int qs_step3d(qs_ctx *c, const qs_beam *beams, int n_beams, qs_step_stats *stats) {
@@ -645,6 +670,7 @@ int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const i
     std::vector<EngineArgs> list(n);
     size_t smem = 0;
     for (int i = 0; i < n; ++i) {
+        ctxs[i]->ckpt_valid = false;  // the batched step stores no checkpoints
         const int r = step_prepare(ctxs[i], beams ? beams[i] : nullptr, n_beams ? n_beams[i] : 0,
                                    nullptr, st, list[i]);
         if (r != QS_OK) {
@@ -740,7 +766,9 @@ int qs_step3d_adjoint(qs_ctx *c, const double *d_hist, int checkpoint_every, dou
     if (!d_jzb || !d_w || !d_nion) return fail(c, QS_ERR_ARG, "NULL output array");
     if (checkpoint_every < 0) return fail(c, QS_ERR_ARG, "checkpoint_every must be >= 0");
     const qs_config &g = c->cfg;
-    const int K = checkpoint_every > 0 ? checkpoint_every : 32;
+    const bool stored = c->ckpt_valid && (checkpoint_every == 0 ||
+                                          checkpoint_every == c->ckpt_every);
+    const int K = stored ? c->ckpt_every : (checkpoint_every > 0 ? checkpoint_every : 32);
     const int nxi = g.n_xi;
     const int64_t np = c->np;
     const size_t nn = (size_t)c->N * c->N;
@@ -767,23 +795,27 @@ int qs_step3d_adjoint(qs_ctx *c, const double *d_hist, int checkpoint_every, dou
     }
     DevBufs B;
     double *ckpt = nullptr, *seg_p = nullptr, *seg_g = nullptr, *lam = nullptr, *grd = nullptr;
-    AL(B.list, ckpt, (size_t)nseg * 4 * np);
+    if (stored) ckpt = c->ckpt;
+    else AL(B.list, ckpt, (size_t)nseg * 4 * np);
     AL(B.list, seg_p, (size_t)max_sub * 4 * np);
     AL(B.list, seg_g, (size_t)max_sub * SG_COUNT * nn);
     AL(B.list, lam, (size_t)4 * np);
     AL(B.list, grd, (size_t)20 * nn);
     float ms_total = 0.f;
-    // forward replay that stores the checkpoints
+    // forward replay that stores the checkpoints (unless the step stored them)
     EngineArgs a;
-    int r = step_prepare(c, nullptr, 0, sched.data(), st, a, true);
-    if (r != QS_OK) return r;
-    a.ckpt_every = K;
-    a.ckpt = ckpt;
-    CK(cudaEventRecord(c->ev0, st), "event");
-    CK(qs_launch_engine(st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
-    CK(cudaEventRecord(c->ev1, st), "event");
-    CK(cudaStreamSynchronize(st), "checkpoint pass");
-    {
+    int r;
+    if (!stored) {
+        r = step_prepare(c, nullptr, 0, sched.data(), st, a, true);
+        if (r != QS_OK) return r;
+        a.ckpt_every = K;
+        a.ckpt = ckpt;
+        CK(cudaEventRecord(c->ev0, st), "event");
+        CK(qs_launch_engine(st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
+        CK(cudaEventRecord(c->ev1, st), "event");
+        CK(cudaStreamSynchronize(st), "checkpoint pass");
+    }
+    if (!stored) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, c->ev0, c->ev1);
         ms_total += ms;
