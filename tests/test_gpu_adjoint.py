@@ -199,3 +199,32 @@ def test_short_windows_and_zero_cotangent(qs, n_xi):
     assert float(d_jzb.abs().max()) == 0.0 and float(d_w.abs().max()) == 0.0
     assert float(d_nion.abs().max()) == 0.0
     assert st["slices"] >= n_xi
+
+
+def test_fullsize_refined_gradient_follows_the_fp64_gradient(qs):
+    """grad256 at full size: the refined form's gradient (float32 particles
+    and inner cycles in the forward, float64 adjoint arithmetic) against the
+    float64 form's, which the directional-derivative test pins to central
+    differences; checkpoints stored by the forward step."""
+    wl = W.workload("grad256")
+    drv, wit = wl.beams
+    theta = [drv.amplitude, drv.sigma_x, drv.sigma_y, drv.sigma_z, drv.x_c, drv.y_c, drv.xi_c,
+             drv.tilt]
+    table, r_max = list(wl.profile[0]), wl.profile[1]
+    z = torch.tensor(W.beam_normals(drv.n_particles, drv.seed), dtype=torch.float64,
+                     device="cuda")
+    witness = qs.Beam(W.sample_beam(wit))
+    out = {}
+    for form in ("fp64", "fp32r"):
+        ctx = qs.Context(qs.config_from_workload(wl, precision=form, checkpoint_every=32))
+        th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        tb = torch.tensor(table, dtype=torch.float64, requires_grad=True)
+        L = qs.witness_gain(ctx, th, tb, z, drv.gamma, witness, wl.dt, wl.ppc, r_max)
+        L.backward()
+        out[form] = (float(L.detach()), th.grad.numpy().copy(), tb.grad.numpy().copy())
+        ctx.close()
+    (L64, g64, t64), (L32, g32, t32) = out["fp64"], out["fp32r"]
+    assert abs(L32 - L64) <= 1e-6 * abs(L64)
+    scale = max(np.abs(g64).max(), np.abs(t64).max())
+    assert np.max(np.abs(g32 - g64)) <= 1e-4 * scale, (g32, g64)
+    assert np.max(np.abs(t32 - t64)) <= 1e-4 * scale, (t32, t64)

@@ -41,9 +41,9 @@ def _worker(rank, world, port, out):
 def test_two_replicas_report_the_slowest_time_and_the_summed_rate():
     world = 2
     port = _free_port()
-    manager = mp.Manager()
-    out = manager.dict()
     ctx = mp.get_context("spawn")
+    manager = ctx.Manager()
+    out = manager.dict()
     procs = [ctx.Process(target=_worker, args=(r, world, port, out)) for r in range(world)]
     for p in procs:
         p.start()
