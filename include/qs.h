@@ -107,7 +107,10 @@ typedef struct {
     int checkpoint_every;       /* > 0: qs_step3d also stores the plasma state  */
                                 /* every this many base slices, which           */
                                 /* qs_step3d_adjoint then uses instead of a     */
-                                /* replay; 0 = off                              */
+                                /* replay; >= n_xi: it keeps every slice's      */
+                                /* state (up to 2 n_xi slices, if that fits in  */
+                                /* 40 % of free device memory), so the adjoint  */
+                                /* recomputes nothing; 0 = off                  */
 } qs_config;
 
 /* Driver-beam macroparticles: structure of arrays of float64, n entries each.

@@ -58,6 +58,12 @@ struct qs_ctx {
     size_t ckpt_count = 0;
     int ckpt_every = 0;
     bool ckpt_valid = false;
+    // every slice of the last qs_step3d (config.checkpoint_every >= n_xi and
+    // room in device memory): the adjoint's segment store for the whole window
+    double *store = nullptr;
+    size_t store_slots = 0;
+    int store_n_sub = 0;
+    bool store_valid = false;
     int engine_blocks = 0;
     size_t engine_smem = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -214,8 +220,6 @@ int create_impl(qs_ctx *c) {
             AL(L, c->lev32[l].f[1], m);
             AL(L, c->lev32[l].k, m);
             AL(L, c->lev32[l].d, m);
-            AL(L, c->lev32[l].up[0], m);
-            AL(L, c->lev32[l].up[1], m);
         } else {
             AL(L, c->lev[l].u[0], m);
             AL(L, c->lev[l].u[1], m);
@@ -333,6 +337,7 @@ void qs_destroy(qs_ctx *c) {
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
     if (c->ckpt) cudaFree(c->ckpt);
+    if (c->store) cudaFree(c->store);
     free_list(c->plasma_allocs);
     free_list(c->allocs);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -354,6 +359,7 @@ int qs_init_plasma(qs_ctx *c, int ppc, const double *profile, int n_coef, double
     free_list(c->plasma_allocs);
     c->have_plasma = c->have_step = false;
     c->ckpt_valid = false;
+    c->store_valid = false;
     auto &L = c->plasma_allocs;
     AL(L, c->t_x, np);
     AL(L, c->t_y, np);
@@ -563,6 +569,7 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
     a.ckpt_every = 0;
     a.ckpt = nullptr;
     a.seg_p = a.seg_g = nullptr;
+    a.seg_cap = 0;
     if (replay) {
         a.hist = nullptr;
         a.diag_m = nullptr;
@@ -622,6 +629,7 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
         const size_t need = (size_t)((c->cfg.n_xi + K - 1) / K) * 4 * c->np;
         if (c->ckpt_count < need) {
             if (c->ckpt) cudaFree(c->ckpt);
+    if (c->store) cudaFree(c->store);
             c->ckpt = nullptr;
             c->ckpt_count = 0;
             CK(cudaMalloc(&c->ckpt, need * sizeof(double)), "cudaMalloc checkpoints");
@@ -629,6 +637,35 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
         }
         a.ckpt_every = K;
         a.ckpt = c->ckpt;
+    }
+    c->store_valid = false;
+    if (K >= c->cfg.n_xi) {
+        // keep every slice's state (plasma before its push, 12 grids) for the
+        // adjoint if it fits in at most 40 % of the free device memory:
+        // room for two sub-steps per base slice on average, and the slots
+        // already held are reused
+        const size_t nn = (size_t)c->N * c->N;
+        const size_t per = 4 * (size_t)c->np + SG_COUNT * nn;
+        size_t want = (size_t)c->cfg.n_xi * 2;
+        if (c->store_slots < want) {
+            size_t fr = 0, tot = 0;
+            cudaMemGetInfo(&fr, &tot);
+            const size_t held = c->store_slots * per * sizeof(double);
+            if ((want * per * sizeof(double)) <= (size_t)(0.4 * (double)(fr + held))) {
+                if (c->store) cudaFree(c->store);
+                c->store = nullptr;
+                c->store_slots = 0;
+                if (cudaMalloc(&c->store, want * per * sizeof(double)) == cudaSuccess)
+                    c->store_slots = want;
+                else
+                    cudaGetLastError();
+            }
+        }
+        if (c->store_slots > 0) {
+            a.seg_p = c->store;
+            a.seg_g = c->store + c->store_slots * 4 * (size_t)c->np;
+            a.seg_cap = (int)c->store_slots;
+        }
     }
     CK(cudaEventRecord(c->ev0, c->st), "event");
     CK(qs_launch_engine(c->st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
@@ -640,6 +677,14 @@ static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t
     if (r == QS_OK && K > 0) {
         c->ckpt_valid = true;
         c->ckpt_every = K;
+    }
+    if (r == QS_OK && a.seg_p) {
+        DevScalars hs;
+        CK(cudaMemcpy(&hs, c->sc, sizeof(hs), cudaMemcpyDeviceToHost), "copy scalars");
+        if (hs.slices <= (unsigned long long)c->store_slots) {
+            c->store_valid = true;
+            c->store_n_sub = (int)hs.slices;
+        }
     }
     return r;
 }
@@ -671,6 +716,7 @@ int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const i
     size_t smem = 0;
     for (int i = 0; i < n; ++i) {
         ctxs[i]->ckpt_valid = false;  // the batched step stores no checkpoints
+        ctxs[i]->store_valid = false;
         const int r = step_prepare(ctxs[i], beams ? beams[i] : nullptr, n_beams ? n_beams[i] : 0,
                                    nullptr, st, list[i]);
         if (r != QS_OK) {
@@ -793,12 +839,19 @@ int qs_step3d_adjoint(qs_ctx *c, const double *d_hist, int checkpoint_every, dou
             n_sub += (j == nxi - 1) ? 1 : sched[j];
         max_sub = std::max(max_sub, n_sub);
     }
+    // every slice kept by the forward step: no checkpoints, no recompute
+    const bool whole = stored && nseg == 1 && c->store_valid && c->store_n_sub == max_sub;
     DevBufs B;
     double *ckpt = nullptr, *seg_p = nullptr, *seg_g = nullptr, *lam = nullptr, *grd = nullptr;
     if (stored) ckpt = c->ckpt;
     else AL(B.list, ckpt, (size_t)nseg * 4 * np);
-    AL(B.list, seg_p, (size_t)max_sub * 4 * np);
-    AL(B.list, seg_g, (size_t)max_sub * SG_COUNT * nn);
+    if (whole) {
+        seg_p = c->store;
+        seg_g = c->store + c->store_slots * 4 * (size_t)np;
+    } else {
+        AL(B.list, seg_p, (size_t)max_sub * 4 * np);
+        AL(B.list, seg_g, (size_t)max_sub * SG_COUNT * nn);
+    }
     AL(B.list, lam, (size_t)4 * np);
     AL(B.list, grd, (size_t)20 * nn);
     float ms_total = 0.f;
@@ -851,18 +904,22 @@ int qs_step3d_adjoint(qs_ctx *c, const double *d_hist, int checkpoint_every, dou
         // recompute the segment from its checkpoint, storing every slice
         r = step_prepare(c, nullptr, 0, sched.data(), st, a, true);
         if (r != QS_OK) return r;
-        r = restore_checkpoint(c, ckpt + (size_t)k * 4 * np);
-        if (r != QS_OK) return r;
         a.j_begin = j0;
         a.j_end = j1;
         a.seg_p = seg_p;
         a.seg_g = seg_g;
-        CK(cudaEventRecord(c->ev0, st), "event");
-        CK(qs_launch_engine(st, a, c->engine_blocks, c->engine_smem), "slice engine launch");
-        CK(cudaStreamSynchronize(st), "segment recompute");
+        a.seg_cap = n_sub;
         DevScalars hs;
-        r = read_scalars(c, hs, "segment recompute");
-        if (r != QS_OK) return r;
+        CK(cudaEventRecord(c->ev0, st), "event");
+        if (!whole) {
+            r = restore_checkpoint(c, ckpt + (size_t)k * 4 * np);
+            if (r != QS_OK) return r;
+            CK(qs_launch_engine(st, a, c->engine_blocks, c->engine_smem),
+               "slice engine launch");
+            CK(cudaStreamSynchronize(st), "segment recompute");
+            r = read_scalars(c, hs, "segment recompute");
+            if (r != QS_OK) return r;
+        }
         // the reverse slice loop over the segment
         CK(cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), st), "memset");
         d.j0 = j0;

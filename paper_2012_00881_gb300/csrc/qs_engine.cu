@@ -292,7 +292,7 @@ template <typename P>
 __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, bool base,
                            bool last, int j, double dxi, int pk, int sub, Thr T) {
     const int nn = A.N * A.N;
-    if (A.seg_g) {  // segment store for the adjoint: fields and moments (float64)
+    if (A.seg_g && sub < A.seg_cap) {  // segment store for the adjoint (float64)
         double *g = A.seg_g + (size_t)sub * SG_COUNT * nn;
         const double *ncur = Q.na == nnext ? Q.nb : Q.na;
         for (int i = T.t0; i < nn; i += T.nt) {

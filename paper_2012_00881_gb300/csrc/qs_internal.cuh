@@ -55,7 +55,6 @@ struct LevelArrays32 {
     float *f[2];
     float *k;
     float *d;
-    float *up[2];  // post-smoothed iterate of a tiled grid level
 };
 
 // Everything the slice engine reads or writes (passed by value).
@@ -127,6 +126,7 @@ struct EngineArgs {
     // seg_p + s * 4 * np (x, y, px, py) and 12 grids at seg_g + s * 12 * N^2
     // (psi, Ez, Bz, Bx, By, n_*, jx, jy, Txx, Txy, Tyy, n_* <gamma>)
     double *seg_p, *seg_g;
+    int seg_cap;  // slots of the segment store; slices beyond it are not stored
 };
 
 // Arguments of the adjoint engine (the reverse slice loop over one segment).

@@ -267,16 +267,6 @@ __device__ bool vcycle(const EngineArgs &A, const Sync &S, const Hier<T> &H, int
     return true;
 }
 
-// Refined form: one float32 V-cycle on the correction with the grid-wide
-// levels staged tile by tile (one grid barrier per level and leg); every
-// block then solves the coarse levels itself in shared memory (no barrier),
-// and the correction is added into the float64 iterate by the last level-0
-// phase.
-//
-// With `fused` set the level-0 up leg also updates the float64 residual and
-// accumulates ||r||^2, ||u||^2 into norms_out (slot of the convergence test),
-// so no separate residual phase is needed; *fused_done reports whether that
-// happened (grids too small to stage fall back to the plain cycle).
 // Output tile of a staged level of side n: the configured tile, halved
 // (the longer side first, down to 8) while the level has fewer than nblk/2
 // tiles, so that coarser grid-wide levels still spread over the blocks and
@@ -294,6 +284,14 @@ __device__ __forceinline__ void level_tile(const EngineArgs &A, int n, int nblk,
     }
 }
 
+// Refined form: one float32 V-cycle on the correction.  The grid-wide levels
+// are staged tile by tile on the way down (one grid barrier per level);
+// every block then solves the coarse levels itself in shared memory (no
+// barrier); one phase runs every up leg and the level-0 update of the
+// float64 iterate u and residual r (r <- r - A e) and accumulates ||r||^2,
+// ||u||^2 into norms_out (the slot of the convergence test).
+// *fused_done reports whether that happened: grids too small to stage fall
+// back to the plain cycle, which leaves the residual to a separate pass.
 template <int NC>
 __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<float> &H, int bid,
                               int nblk, void *smem, qsmg::CoarseInv ci, double *fin0,
@@ -307,66 +305,34 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
     // shared memory: the coarse part's levels first, the staged tile after them
     float *sm = (float *)((char *)smem + A.tile_smem_offset);
     const qsmg::Marks mk{bid == 0 ? A.trace : nullptr, &A.sc->trace_n, A.trace_cap};
-    const int Hmax = 2 * max(A.nu1, A.nu2) + 1;  // the tile layout is sized for this halo
     for (int l = 0; l < lg; ++l) {
         int TX, TY;
         level_tile(A, H.lv[l].n, nblk, TX, TY);
-        qstile::down_level<NC>(H.lv[l], H.lv[l + 1], A.nu1, TX, TY, Hmax, sm, bid,
+        qstile::down_level<NC>(H.lv[l], H.lv[l + 1], A.nu1, TX, TY, sm, bid,
                                nblk, mk);
         mk(62);
         SYNC(30);
     }
     qsmg::block_vcycle<float, NC>(H, lg, A.nu1c, A.nu2, smem, ci, false, mk);
     const int mg2 = H.lv[lg].n * H.lv[lg].n;
-    if (fused) {
-        // every up leg and the level-0 update in one phase
-        int TX, TY;
-        level_tile(A, H.lv[0].n, nblk, TX, TY);
-        double nrm[4] = {0.0, 0.0, 0.0, 0.0};
-        qstile::up_cascade_fused<NC>(H, lg, (const float *)smem, (const float *)smem + 2 * mg2,
-                                     A.nu2, TX, TY, sm, bid, nblk, *fused, nrm, mk);
+    // every up leg and the level-0 update in one phase
+    int TX, TY;
+    level_tile(A, H.lv[0].n, nblk, TX, TY);
+    double nrm[4] = {0.0, 0.0, 0.0, 0.0};
+    qstile::up_cascade_fused<NC>(H, lg, (const float *)smem, (const float *)smem + 2 * mg2,
+                                 A.nu2, TX, TY, sm, bid, nblk, *fused, nrm, mk);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            double t = block_sum(nrm[c]);
-            if (threadIdx.x == 0) atomicAdd(norms_out + c, t);
-            t = block_sum(nrm[2 + c]);
-            if (threadIdx.x == 0) atomicAdd(norms_out + 2 + c, t);
-        }
-        if (bid == 0 && threadIdx.x == 0)
-            for (int e = 0; e < 4; ++e) norms_clear[e] = 0.0;
-        mk(67);
-        *fused_done = true;
-        SYNC(32);
-        return true;
+    for (int c = 0; c < NC; ++c) {
+        double t = block_sum(nrm[c]);
+        if (threadIdx.x == 0) atomicAdd(norms_out + c, t);
+        t = block_sum(nrm[2 + c]);
+        if (threadIdx.x == 0) atomicAdd(norms_out + 2 + c, t);
     }
-    for (int l = lg - 1; l >= 0; --l) {
-        const float *cu0 = (l + 1 == lg) ? (const float *)smem : A.lev32[l + 1].up[0];
-        const float *cu1 = (l + 1 == lg) ? (const float *)smem + 2 * mg2 : A.lev32[l + 1].up[1];
-        int TX, TY;
-        level_tile(A, H.lv[l].n, nblk, TX, TY);
-        if (l == 0 && fused) {
-            double nrm[4] = {0.0, 0.0, 0.0, 0.0};
-            qstile::up_level0_fused<NC>(H.lv[0], cu0, cu1, l + 1 == lg, H.lv[1].n, A.nu2,
-                                        TX, TY, Hmax, sm, bid, nblk, *fused, nrm, mk);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                double t = block_sum(nrm[c]);
-                if (threadIdx.x == 0) atomicAdd(norms_out + c, t);
-                t = block_sum(nrm[2 + c]);
-                if (threadIdx.x == 0) atomicAdd(norms_out + 2 + c, t);
-            }
-            if (bid == 0 && threadIdx.x == 0)
-                for (int e = 0; e < 4; ++e) norms_clear[e] = 0.0;
-            mk(67);
-            *fused_done = true;
-        } else {
-            qstile::up_level<NC>(H.lv[l], cu0, cu1, l + 1 == lg, H.lv[l + 1].n, A.nu2,
-                                 TX, TY, Hmax, sm, bid, nblk, A.lev32[l].up[0],
-                                 A.lev32[l].up[1], l == 0 ? fin0 : nullptr,
-                                 l == 0 ? fin1 : nullptr);
-        }
-        SYNC(32);
-    }
+    if (bid == 0 && threadIdx.x == 0)
+        for (int e = 0; e < 4; ++e) norms_clear[e] = 0.0;
+    mk(67);
+    *fused_done = true;
+    SYNC(32);
     return true;
 }
 

@@ -6,10 +6,11 @@
 // in shared memory and performs all half sweeps of a leg there, recomputing
 // the halo redundantly; only the cells far enough from a cut edge of the
 // staged region are exact after each half sweep, and the halo is as wide as
-// the number of half sweeps (plus one for the residual).  A level then costs
-// two grid barriers per V-cycle (down: smooth + residual + restriction; up:
-// prolongation + smooth).  The inner correction starts from zero on every
-// level, so the down leg needs no neighbour data but the right-hand side.
+// the number of half sweeps (plus one for the residual).  A down leg then
+// costs one grid barrier per level (smooth + residual + restriction), and
+// all the up legs together one (the up cascade below).  The inner correction
+// starts from zero on every level, so the down leg needs no neighbour data
+// but the right-hand side.
 #pragma once
 
 #include "qs_mg.cuh"
@@ -95,20 +96,13 @@ __device__ __forceinline__ float staged_op(const float *u, const float *k, int R
     return r;
 }
 
-// Layout of one staged tile in shared memory: six region arrays (u0, u1, f0,
-// f1, kappa, inverse diagonal), a window of the coarse correction for the
-// prolongation (two components), then float64 copies of the tile's cells for
-// the fused level-0 update (u64 x2, r64 x2, kappa).
+// Layout of a staged down-leg region in shared memory: six arrays (u0, u1,
+// f0, f1, kappa, inverse diagonal) of R cells.
 struct TileSmem {
-    float *su0, *su1, *sf0, *sf1, *sk, *sd, *sc0, *sc1;
-    double *du0, *du1, *dr0, *dr1, *dk;
+    float *su0, *su1, *sf0, *sf1, *sk, *sd;
 };
 
-__host__ __device__ inline int coarse_window_floats(int TX, int TY, int H) {
-    return ((TX + 2 * H) / 2 + 4) * ((TY + 2 * H) / 2 + 4);
-}
-
-__device__ __forceinline__ TileSmem tile_layout(float *sm, int R, int TX, int TY, int Hmax) {
+__device__ __forceinline__ TileSmem tile_layout(float *sm, int R) {
     TileSmem t;
     t.su0 = sm;
     t.su1 = sm + R;
@@ -116,18 +110,6 @@ __device__ __forceinline__ TileSmem tile_layout(float *sm, int R, int TX, int TY
     t.sf1 = sm + 3 * R;
     t.sk = sm + 4 * R;
     t.sd = sm + 5 * R;
-    const int cw = coarse_window_floats(TX, TY, Hmax);
-    const int Rmax = (TX + 2 * Hmax) * (TY + 2 * Hmax);
-    t.sc0 = sm + 6 * Rmax;
-    t.sc1 = t.sc0 + cw;
-    size_t off = ((size_t)(6 * Rmax + 2 * cw) * sizeof(float) + 15) & ~(size_t)15;
-    double *d = (double *)((char *)sm + off);
-    const int T = TX * TY;
-    t.du0 = d;
-    t.du1 = d + T;
-    t.dr0 = d + 2 * T;
-    t.dr1 = d + 3 * T;
-    t.dk = d + 4 * T;
     return t;
 }
 
@@ -184,15 +166,13 @@ __device__ __forceinline__ CascadeSmem cascade_layout(float *sm, int R, int TX, 
 
 // Shared memory (bytes) for the staged legs with tile TX x TY and any tile
 // obtained from it by halving sides down to 8 (nu = the larger sweep count,
-// nu2 = post-sweeps).
+// nu2 = post-sweeps): the down legs' region or the up cascade, whichever is
+// larger.
 __host__ __device__ inline size_t tile_smem_bytes(int TX, int TY, int nu, int nu2) {
     size_t best = 0;
     for (int tx = TX, ty = TY;;) {
         const int H = 2 * nu + 1;
-        const int Rmax = (tx + 2 * H) * (ty + 2 * H);
-        size_t a = ((size_t)(6 * Rmax + 2 * coarse_window_floats(tx, ty, H)) * sizeof(float) +
-                    15) & ~(size_t)15;
-        a += (size_t)5 * tx * ty * sizeof(double);
+        const size_t a = (size_t)6 * (tx + 2 * H) * (ty + 2 * H) * sizeof(float);
         int rbig, wbig;
         cascade_bounds(tx, ty, nu2, rbig, wbig);
         size_t b = ((size_t)(6 * rbig + 4 * wbig) * sizeof(float) + 15) & ~(size_t)15;
@@ -233,7 +213,7 @@ __device__ __forceinline__ float bilinear_win(const float *cs, int cox, int coy,
 // inverse diagonal); the pre-smoothed tile is written to F.u.
 template <int NC>
 __device__ void down_level(const Lvl<float> F, const Lvl<float> C, int nu1, int TX, int TY,
-                           int Hmax, float *sm, int bid, int nblk,
+                           float *sm, int bid, int nblk,
                            qsmg::Marks mark = qsmg::Marks{nullptr, nullptr, 0}) {
     const int n = F.n, m = C.n;
     const int H = 2 * nu1 + 1;
@@ -245,7 +225,7 @@ __device__ void down_level(const Lvl<float> F, const Lvl<float> C, int nu1, int 
     for (int tile = bid; tile < ntx * nty; tile += nblk) {
         const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
         const Region g = make_region(tx0, ty0, TX, TY, H, n);
-        const TileSmem t = tile_layout(sm, g.R, TX, TY, Hmax);
+        const TileSmem t = tile_layout(sm, g.R);
         float *const su0 = t.su0;
         float *const su1 = t.su1;
         float *const sf0 = t.sf0;
@@ -307,98 +287,10 @@ __device__ void down_level(const Lvl<float> F, const Lvl<float> C, int nu1, int 
     }
 }
 
-// Stage the region of an up leg: u (pre-smoothed) and f of level F, the
-// inverse diagonal when screened, and (when the coarse correction `cu` lives
-// in global memory) the window of `cu` the prolongation reads; then add the
-// prolongated correction.  On return (after a block barrier) su = u + P cu.
-template <int NC>
-__device__ void stage_up_region(const Lvl<float> F, const Region &g, const TileSmem &t,
-                                const float *cu0, const float *cu1, bool cu_shared, int m,
-                                const float **sd_out) {
-    const int n = F.n;
-    const bool scr = F.k != nullptr;
-    float *const sd = scr ? t.sd : nullptr;
-    *sd_out = sd;
-    const float *cs0 = cu0, *cs1 = cu1;
-    int cox = 0, coy = 0, cp = m;
-    if (!cu_shared) {
-        cox = max((g.ax >> 1) - 1, 0);
-        coy = max((g.ay >> 1) - 1, 0);
-        const int cx1 = min((g.bx >> 1) + 1, m - 1), cy1 = min((g.by >> 1) + 1, m - 1);
-        cp = cx1 - cox + 1;
-        const int rows = cy1 - coy + 1;
-        for (Walk w(threadIdx.x, blockDim.x, cp); w.q < cp * rows; w.next()) {
-            const int gi = (coy + w.row) * m + cox + w.col;
-            cp_async_f32(t.sc0 + w.q, cu0 + gi, true);
-            if (NC > 1) cp_async_f32(t.sc1 + w.q, cu1 + gi, true);
-        }
-        cs0 = t.sc0;
-        cs1 = t.sc1;
-    }
-    for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
-        const int x = g.ox + w.col, y = g.oy + w.row;
-        const bool in = x >= 0 && x < n && y >= 0 && y < n;
-        const int gi = in ? y * n + x : 0, li = w.q;
-        if (scr) cp_async_f32(sd + li, F.d + gi, in);
-        cp_async_f32(t.su0 + li, F.u[0] + gi, in);
-        cp_async_f32(t.sf0 + li, F.f[0] + gi, in);
-        if (NC > 1) {
-            cp_async_f32(t.su1 + li, F.u[1] + gi, in);
-            cp_async_f32(t.sf1 + li, F.f[1] + gi, in);
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    const int wx = g.bx - g.ax + 1, wy = g.by - g.ay + 1;
-    for (Walk w(threadIdx.x, blockDim.x, wx); w.q < wx * wy; w.next()) {
-        const int x = g.ax + w.col, y = g.ay + w.row;
-        const int li = (y - g.oy) * g.RX + (x - g.ox);
-        t.su0[li] += bilinear_win(cs0, cox, coy, cp, m, x, y);
-        if (NC > 1) t.su1[li] += bilinear_win(cs1, cox, coy, cp, m, x, y);
-    }
-    __syncthreads();
-}
-
-// Up leg of grid level F: F.u (pre-smoothed) + bilinear interpolation of the
-// coarse correction `cu` (side m; in shared memory when cu_shared), then
-// post-smoothing; the tile result goes to `out` (float32), or is added into
-// the float64 iterate `fin` (level 0 of the refined form).
-template <int NC>
-__device__ void up_level(const Lvl<float> F, const float *cu0, const float *cu1, bool cu_shared,
-                         int m, int nu2, int TX, int TY, int Hmax, float *sm, int bid, int nblk,
-                         float *out0, float *out1, double *fin0, double *fin1) {
-    const int n = F.n;
-    const int H = 2 * nu2;
-    const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
-    const float h2 = (float)F.h2;
-    for (int tile = bid; tile < ntx * nty; tile += nblk) {
-        const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
-        const Region g = make_region(tx0, ty0, TX, TY, H, n);
-        const TileSmem t = tile_layout(sm, g.R, TX, TY, Hmax);
-        const float *sd;
-        stage_up_region<NC>(F, g, t, cu0, cu1, cu_shared, m, &sd);
-        staged_sweeps<NC>(g, n, h2, t.su0, t.su1, t.sf0, t.sf1, sd, 2 * nu2, F.omega);
-        for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
-            const int x = tx0 + w.col, y = ty0 + w.row;
-            if (x >= n || y >= n) continue;
-            const int li = (y - g.oy) * g.RX + (x - g.ox);
-            const int gi = y * n + x;
-            if (fin0) {
-                fin0[gi] += (double)t.su0[li];
-                if (NC > 1) fin1[gi] += (double)t.su1[li];
-            } else {
-                out0[gi] = t.su0[li];
-                if (NC > 1) out1[gi] = t.su1[li];
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Level-0 up leg of the refined form with the next residual fused in.  The
-// halo is one cell wider than the sweeps need, so the final float32
-// correction e is known on the tile and on the ring around it.  Then, on the
-// tile only, in float64:
+// The level-0 update of the refined form, fused into the last up phase.  The
+// level-0 region's halo is one cell wider than the sweeps need, so the final
+// float32 correction e is known on the tile and on the ring around it.
+// Then, on the tile only, in float64:
 //   u += e;   r -= (lap_h - kappa) e;   r32 = (float) r
 // (the residual update r_new = f - A(u + e) = r - A e), and this thread's
 // sums of r^2 and u^2 per component are added to norms[0..3].  No cell of u
@@ -412,73 +304,6 @@ struct Fused {
     double inv_h2;
 };
 
-template <int NC>
-__device__ void up_level0_fused(const Lvl<float> F, const float *cu0, const float *cu1,
-                                bool cu_shared, int m, int nu2, int TX, int TY, int Hmax,
-                                float *sm, int bid, int nblk, const Fused &o, double norms[4],
-                                qsmg::Marks mark = qsmg::Marks{nullptr, nullptr, 0}) {
-    const int n = F.n;
-    const int H = 2 * nu2 + 1;
-    const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
-    const float h2 = (float)F.h2;
-    double *const u64_0 = o.u64[0], *const u64_1 = o.u64[NC - 1];
-    double *const r64_0 = o.r64[0], *const r64_1 = o.r64[NC - 1];
-    float *const r32_0 = o.r32[0], *const r32_1 = o.r32[NC - 1];
-    const double *const kap = o.kap;
-    const double inv_h2 = o.inv_h2;
-    for (int tile = bid; tile < ntx * nty; tile += nblk) {
-        const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
-        const Region g = make_region(tx0, ty0, TX, TY, H, n);
-        const TileSmem t = tile_layout(sm, g.R, TX, TY, Hmax);
-        // float64 tile values (issued first; waited for inside the staging)
-        for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
-            const int x = tx0 + w.col, y = ty0 + w.row;
-            const bool in = x < n && y < n;
-            const int gi = in ? y * n + x : 0;
-            cp_async_f64(t.du0 + w.q, u64_0 + gi, in);
-            cp_async_f64(t.dr0 + w.q, r64_0 + gi, in);
-            if (NC > 1) {
-                cp_async_f64(t.du1 + w.q, u64_1 + gi, in);
-                cp_async_f64(t.dr1 + w.q, r64_1 + gi, in);
-            }
-            if (kap) cp_async_f64(t.dk + w.q, kap + gi, in);
-        }
-        const float *sd;
-        stage_up_region<NC>(F, g, t, cu0, cu1, cu_shared, m, &sd);
-        mark(65);
-        staged_sweeps<NC>(g, n, h2, t.su0, t.su1, t.sf0, t.sf1, sd, 2 * nu2, F.omega);
-        mark(66);
-        const int RX = g.RX;
-        for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
-            const int x = tx0 + w.col, y = ty0 + w.row;
-            if (x >= n || y >= n) continue;
-            const int li = (y - g.oy) * RX + (x - g.ox);
-            const int gi = y * n + x;
-            const int nw = qsmg::walls(x, y, n);
-            const double kk = kap ? t.dk[w.q] : 0.0;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const float *e = c ? t.su1 : t.su0;
-                const double ec = (double)e[li];
-                double nb = 0.0;
-                if (x > 0) nb += (double)e[li - 1];
-                if (x < n - 1) nb += (double)e[li + 1];
-                if (y > 0) nb += (double)e[li - RX];
-                if (y < n - 1) nb += (double)e[li + RX];
-                const double ae = (nb - (double)(4 + nw) * ec) * inv_h2 - kk * ec;
-                const double u = (c ? t.du1 : t.du0)[w.q] + ec;
-                const double r = (c ? t.dr1 : t.dr0)[w.q] - ae;
-                (c ? u64_1 : u64_0)[gi] = u;
-                (c ? r64_1 : r64_0)[gi] = r;
-                (c ? r32_1 : r32_0)[gi] = (float)r;
-                norms[c] += r * r;
-                norms[2 + c] += u * u;
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Up cascade: the up legs of every staged level and the fused level-0 update
 // in one grid phase.
@@ -491,7 +316,7 @@ __device__ void up_level0_fused(const Lvl<float> F, const float *cu0, const floa
 // cells that the finer region prolongs from; it stages that window plus a
 // halo of 2 nu2 (pre-smoothed u, f, inverse diagonal), adds the prolongated
 // correction, sweeps, and keeps the window, which is exact.  The level-0
-// region is the tile plus a halo 2 nu2 + 1, as in up_level0_fused.
+// region is the tile plus a halo 2 nu2 + 1 (see Fused above).
 // ---------------------------------------------------------------------------
 
 // coarse window of an in-domain box [ax, bx] x [ay, by] at a level of side m

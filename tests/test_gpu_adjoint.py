@@ -106,8 +106,9 @@ def test_checkpoint_interval_does_not_change_the_gradient(qs):
     for K in (1, 3, 14):
         got = _gpu_gradient(qs, wl, P, theta, table, checkpoint_every=K)
         assert _rel(got[1], ref[1]) <= 1e-9 and _rel(got[2], ref[2]) <= 1e-9, K
-    # checkpoints stored by the forward step itself (no replay in the adjoint)
-    for K in (4, 32):
+    # checkpoints stored by the forward step itself (no replay in the adjoint);
+    # K >= n_xi keeps every slice, so the adjoint recomputes nothing
+    for K in (4, 14, 32):
         got = _gpu_gradient(qs, wl, P, theta, table, checkpoint_every=0, stored=K)
         assert _rel(got[1], ref[1]) <= 1e-9 and _rel(got[2], ref[2]) <= 1e-9, ("stored", K)
 
@@ -228,3 +229,24 @@ def test_fullsize_refined_gradient_follows_the_fp64_gradient(qs):
     scale = max(np.abs(g64).max(), np.abs(t64).max())
     assert np.max(np.abs(g32 - g64)) <= 1e-4 * scale, (g32, g64)
     assert np.max(np.abs(t32 - t64)) <= 1e-4 * scale, (t32, t64)
+
+
+def test_slice_store_overflow_falls_back_to_recompute(qs):
+    """With every slice kept by the forward step (checkpoint_every >= n_xi),
+    a schedule with more sub-steps than the store holds (two per base slice)
+    is recomputed from the checkpoint instead: same cotangents as without a
+    store."""
+    wl = _workload(True)
+    beams = [qs.Beam(W.sample_beam(b)) for b in wl.beams]
+    sched = [3] * wl.n_xi
+    outs = []
+    for K in (0, 14):
+        ctx = qs.Context(qs.config_from_workload(wl, mg_tol=1e-12, checkpoint_every=K))
+        ctx.init_plasma(wl.ppc, list(wl.profile[0]), wl.profile[1])
+        st = ctx.step3d(beams, schedule=sched)
+        assert st["slices"] == 3 * (wl.n_xi - 1) + 1
+        d_hist = torch.zeros((5, wl.n_xi, wl.n, wl.n), dtype=torch.float64, device="cuda")
+        ctx.beam_gain(beams[1], wl.dt, d_hist)
+        outs.append([t.cpu().numpy() for t in ctx.step3d_adjoint(d_hist)[:3]])
+    for a, b in zip(*outs):
+        assert np.max(np.abs(a - b)) <= 1e-9 * max(np.max(np.abs(b)), 1e-300)
