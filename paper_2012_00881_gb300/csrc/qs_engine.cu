@@ -78,7 +78,7 @@ template <typename P>
 __device__ void phase_deposit_n(const EngineArgs &A, const PS<P> &Q, double *ng, Thr T) {
     const double s = A.inv_h * A.inv_h;
     for (int64_t p = T.t0; p < A.np; p += T.nt) {
-        const Cic c = cic_stencil(Q.x[p], Q.y[p], A.x_min, A.y_min, A.h, A.N);
+        const Cic c = cic_stencil_inv(Q.x[p], Q.y[p], A.x_min, A.y_min, A.inv_h, A.N);
         cic_deposit(ng, c, Q.wd[p] * s);
     }
 }
@@ -152,7 +152,7 @@ __device__ void phase_moments(const EngineArgs &A, const PS<P> &Q, Thr T) {
     const P s = (P)(A.inv_h * A.inv_h);
     unsigned hits = 0;
     for (int64_t p = T.t0; p < A.np; p += T.nt) {
-        const Cic cd = cic_stencil(Q.x[p], Q.y[p], A.x_min, A.y_min, A.h, A.N);
+        const Cic cd = cic_stencil_inv(Q.x[p], Q.y[p], A.x_min, A.y_min, A.inv_h, A.N);
         const CicP<P> c = cic_p<P>(cd);
         const double a = guard(1.0 + cic_gather(A.psi, cd), A.psi_floor, hits);
         const P px = Q.px[p], py = Q.py[p];
@@ -335,7 +335,7 @@ __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, b
     double vmax = 0.0;
     for (int64_t p = T.t0; p < A.np; p += T.nt) {
         const double x = Q.x[p], y = Q.y[p];
-        const Cic cd = cic_stencil(x, y, A.x_min, A.y_min, A.h, A.N);
+        const Cic cd = cic_stencil_inv(x, y, A.x_min, A.y_min, A.inv_h, A.N);
         const CicP<P> c = cic_p<P>(cd);
         const double a = guard(1.0 + cic_gather(A.psi, cd), A.psi_floor, hits);
         const double ia = 1.0 / a;
@@ -368,7 +368,7 @@ __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, b
         Q.px[p] = px;
         Q.py[p] = py;
         vmax = fmax(vmax, sqrt((double)px * px + (double)py * py) * ia);
-        const Cic c2 = cic_stencil(nx, ny, A.x_min, A.y_min, A.h, A.N);
+        const Cic c2 = cic_stencil_inv(nx, ny, A.x_min, A.y_min, A.inv_h, A.N);
         cic_deposit(nnext, c2, Q.wd[p] * s);
     }
     add_hits(A.sc, hits);

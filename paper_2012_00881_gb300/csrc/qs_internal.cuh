@@ -202,6 +202,26 @@ __device__ __forceinline__ Cic cic_stencil(double x, double y, double x_min, dou
     return c;
 }
 
+// The same stencil from the reciprocal cell size (no float64 divide: the
+// slice loop evaluates it several times per particle and slice).
+__device__ __forceinline__ Cic cic_stencil_inv(double x, double y, double x_min, double y_min,
+                                               double inv_h, int n) {
+    int ix0, ix1, iy0, iy1;
+    double wx0, wx1, wy0, wy1;
+    cic_axis((x - x_min) * inv_h, n, ix0, ix1, wx0, wx1);
+    cic_axis((y - y_min) * inv_h, n, iy0, iy1, wy0, wy1);
+    Cic c;
+    c.i00 = iy0 * n + ix0;
+    c.i01 = iy0 * n + ix1;
+    c.i10 = iy1 * n + ix0;
+    c.i11 = iy1 * n + ix1;
+    c.w00 = wy0 * wx0;
+    c.w01 = wy0 * wx1;
+    c.w10 = wy1 * wx0;
+    c.w11 = wy1 * wx1;
+    return c;
+}
+
 __device__ __forceinline__ double cic_gather(const double *u, const Cic &c) {
     return u[c.i00] * c.w00 + u[c.i01] * c.w01 + u[c.i10] * c.w10 + u[c.i11] * c.w11;
 }

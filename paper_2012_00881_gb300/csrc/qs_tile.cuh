@@ -319,6 +319,17 @@ struct Fused {
 // region is the tile plus a halo 2 nu2 + 1 (see Fused above).
 // ---------------------------------------------------------------------------
 
+// hi + lo += v with hi + lo kept exact up to the rounding of lo (TwoSum of
+// hi and v; the round-to-nearest intrinsics keep the compiler from fusing
+// or reassociating the steps).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bv = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(v, bv));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
 // coarse window of an in-domain box [ax, bx] x [ay, by] at a level of side m
 __device__ __forceinline__ void coarse_window(const Region &g, int m, int &wx0, int &wy0,
                                               int &wx1, int &wy1) {
@@ -440,32 +451,45 @@ __device__ void up_cascade_fused(const qsmg::Hier<float> &Hh, int lg, const floa
                           2 * nu2, F.omega);
         mark(66);
         const int RX = g.RX;
+        float nrm32[4] = {0.f, 0.f, 0.f, 0.f};
         for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
             const int x = tx0 + w.col, y = ty0 + w.row;
             if (x >= n || y >= n) continue;
             const int li = (y - g.oy) * RX + (x - g.ox);
             const int gi = y * n + x;
-            const int nw = qsmg::walls(x, y, n);
+            const float cw = (float)(4 + qsmg::walls(x, y, n));
             const double kk = kap ? t.dk[w.q] : 0.0;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const float *e = c ? t.su1 : t.su0;
-                const double ec = (double)e[li];
-                double nb = 0.0;
-                if (x > 0) nb += (double)e[li - 1];
-                if (x < n - 1) nb += (double)e[li + 1];
-                if (y > 0) nb += (double)e[li - RX];
-                if (y < n - 1) nb += (double)e[li + RX];
-                const double ae = (nb - (double)(4 + nw) * ec) * inv_h2 - kk * ec;
+                const float ef = e[li];
+                // the 5-point sum of the float32 e, exact as an unevaluated
+                // float32 pair (hi, lo) by error-free sums (Knuth's TwoSum)
+                // and product (FMA): only the pair is widened to float64
+                float hi = 0.f, lo = 0.f;
+                if (x > 0) two_sum_acc(hi, lo, e[li - 1]);
+                if (x < n - 1) two_sum_acc(hi, lo, e[li + 1]);
+                if (y > 0) two_sum_acc(hi, lo, e[li - RX]);
+                if (y < n - 1) two_sum_acc(hi, lo, e[li + RX]);
+                const float pc = __fmul_rn(cw, ef);
+                const float pe = __fmaf_rn(cw, ef, -pc);  // cw ef = pc + pe exactly
+                two_sum_acc(hi, lo, -pc);
+                lo = __fsub_rn(lo, pe);
+                const double ec = (double)ef;
+                const double ae = ((double)hi + (double)lo) * inv_h2 - kk * ec;
                 const double u = (c ? t.du1 : t.du0)[w.q] + ec;
                 const double r = (c ? t.dr1 : t.dr0)[w.q] - ae;
+                const float rf = (float)r, uf = (float)u;
                 (c ? u64_1 : u64_0)[gi] = u;
                 (c ? r64_1 : r64_0)[gi] = r;
-                (c ? r32_1 : r32_0)[gi] = (float)r;
-                norms[c] += r * r;
-                norms[2 + c] += u * u;
+                (c ? r32_1 : r32_0)[gi] = rf;
+                // the convergence test needs the norms to a few digits only
+                nrm32[c] = __fmaf_rn(rf, rf, nrm32[c]);
+                nrm32[2 + c] = __fmaf_rn(uf, uf, nrm32[2 + c]);
             }
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) norms[k] += (double)nrm32[k];
         __syncthreads();
     }
 }
