@@ -147,7 +147,7 @@ __device__ void adj_prepare(const EngineArgs &A, const AdjArgs &D, const Slice &
         const int iy = i / n, ix = i - iy * n;
         double a = 1.0 + S.psi[i];
         if (a < A.psi_floor) a = A.psi_floor;
-        const double kap = S.n[i] / a;
+        const double kap = S.n[i] * (1.0 / a);
         A.kap[i] = kap;
         const int nw = qsmg::walls(ix, iy, n);
         if (A.precision == QS_FP32_REFINED) {
@@ -185,23 +185,24 @@ __device__ void adj_push(const EngineArgs &A, const AdjArgs &D, const Slice &S, 
         double a = 1.0 + Gp.v;
         const bool act = a >= A.psi_floor;
         if (!act) a = A.psi_floor;
+        const double ia = 1.0 / a, ia2 = ia * ia;  // one divide per particle
         const double gx = Ggx.v, gy = Ggy.v, bx = Gbx.v, by = Gby.v, bz = Gbz.v;
         // forward
-        const double gam = (1.0 + px * px + py * py + a * a) / (2.0 * a);
-        const double pxm = px + half * (gam * gx / a - by);
-        const double pym = py + half * (gam * gy / a + bx);
-        const double tau = half * bz / a;
+        const double gam = (1.0 + px * px + py * py + a * a) * (0.5 * ia);
+        const double pxm = px + half * (gam * gx * ia - by);
+        const double pym = py + half * (gam * gy * ia + bx);
+        const double tau = half * bz * ia;
         const double pxp = pxm - tau * pym;
         const double pyp = pym + tau * pxm;
         const double t2 = 1.0 + tau * tau;
         const double sr = 2.0 * tau / t2;
         const double pxr = pxm - sr * pyp;
         const double pyr = pym + sr * pxp;
-        const double gam2 = (1.0 + pxr * pxr + pyr * pyr + a * a) / (2.0 * a);
-        const double px2 = pxr + half * (gam2 * gx / a - by);
-        const double py2 = pyr + half * (gam2 * gy / a + bx);
-        const double nx0 = x + dxi * px2 / a;
-        const double ny0 = y + dxi * py2 / a;
+        const double gam2 = (1.0 + pxr * pxr + pyr * pyr + a * a) * (0.5 * ia);
+        const double px2 = pxr + half * (gam2 * gx * ia - by);
+        const double py2 = pyr + half * (gam2 * gy * ia + bx);
+        const double nx0 = x + dxi * px2 * ia;
+        const double ny0 = y + dxi * py2 * ia;
         int fx = 0, fy = 0;  // reflections at the walls (each flips position and momentum)
         {
             double v = nx0;
@@ -217,21 +218,21 @@ __device__ void adj_push(const EngineArgs &A, const AdjArgs &D, const Slice &S, 
         double l_px2 = sx * D.lpx[p], l_py2 = sy * D.lpy[p];
         double l_x = l_nx, l_y = l_ny;
         double ab = 0.0, gxb = 0.0, gyb = 0.0, bxb = 0.0, byb = 0.0, bzb = 0.0;
-        l_px2 += l_nx * dxi / a;
-        l_py2 += l_ny * dxi / a;
-        ab -= (l_nx * px2 + l_ny * py2) * dxi / (a * a);
+        l_px2 += l_nx * dxi * ia;
+        l_py2 += l_ny * dxi * ia;
+        ab -= (l_nx * px2 + l_ny * py2) * dxi * ia2;
         // second half kick
         double l_pxr = l_px2, l_pyr = l_py2;
-        double g2b = half * (l_px2 * gx + l_py2 * gy) / a;
-        gxb += l_px2 * half * gam2 / a;
-        gyb += l_py2 * half * gam2 / a;
-        ab -= half * gam2 * (l_px2 * gx + l_py2 * gy) / (a * a);
+        double g2b = half * (l_px2 * gx + l_py2 * gy) * ia;
+        gxb += l_px2 * half * gam2 * ia;
+        gyb += l_py2 * half * gam2 * ia;
+        ab -= half * gam2 * (l_px2 * gx + l_py2 * gy) * ia2;
         byb -= l_px2 * half;
         bxb += l_py2 * half;
         // gamma2
-        l_pxr += g2b * pxr / a;
-        l_pyr += g2b * pyr / a;
-        ab += g2b * (0.5 - (1.0 + pxr * pxr + pyr * pyr) / (2.0 * a * a));
+        l_pxr += g2b * pxr * ia;
+        l_pyr += g2b * pyr * ia;
+        ab += g2b * (0.5 - (1.0 + pxr * pxr + pyr * pyr) * (0.5 * ia2));
         // rotation
         double l_pxm = l_pxr, l_pym = l_pyr;
         double srb = -l_pxr * pyp + l_pyr * pxp;
@@ -244,19 +245,19 @@ __device__ void adj_push(const EngineArgs &A, const AdjArgs &D, const Slice &S, 
         taub += l_pyp * pxm;
         l_pxm += l_pyp * tau;
         taub += srb * 2.0 * (1.0 - tau * tau) / (t2 * t2);
-        bzb += taub * half / a;
-        ab -= taub * tau / a;
+        bzb += taub * half * ia;
+        ab -= taub * tau * ia;
         // first half kick
         double l_px = l_pxm, l_py = l_pym;
-        const double g1b = half * (l_pxm * gx + l_pym * gy) / a;
-        gxb += l_pxm * half * gam / a;
-        gyb += l_pym * half * gam / a;
-        ab -= half * gam * (l_pxm * gx + l_pym * gy) / (a * a);
+        const double g1b = half * (l_pxm * gx + l_pym * gy) * ia;
+        gxb += l_pxm * half * gam * ia;
+        gyb += l_pym * half * gam * ia;
+        ab -= half * gam * (l_pxm * gx + l_pym * gy) * ia2;
         byb -= l_pxm * half;
         bxb += l_pym * half;
-        l_px += g1b * px / a;
-        l_py += g1b * py / a;
-        ab += g1b * (0.5 - (1.0 + px * px + py * py) / (2.0 * a * a));
+        l_px += g1b * px * ia;
+        l_py += g1b * py * ia;
+        ab += g1b * (0.5 - (1.0 + px * px + py * py) * (0.5 * ia2));
         if (!act) ab = 0.0;
         // gathers: slopes into the position cotangent, values scattered
         l_x += (ab * Gp.dx + gxb * Ggx.dx + gyb * Ggy.dx + bxb * Gbx.dx + byb * Gby.dx +
@@ -310,7 +311,7 @@ __device__ void adj_source(const EngineArgs &A, const AdjArgs &D, const Slice &S
         double a = 1.0 + S.psi[i];
         const bool act = a >= A.psi_floor;
         if (!act) a = A.psi_floor;
-        const double a2 = a * a, a3 = a2 * a;
+        const double ia = 1.0 / a, ia2 = ia * ia, ia3 = ia2 * ia;
         const double sxb = -D.mu_y[i], syb = D.mu_x[i];
         const double jx = S.jx[i], jy = S.jy[i], txx = S.txx[i], txy = S.txy[i],
                      tyy = S.tyy[i], G = S.G[i], nv = S.n[i], ez = S.ez[i], bz = S.bz[i];
@@ -323,24 +324,24 @@ __device__ void adj_source(const EngineArgs &A, const AdjArgs &D, const Slice &S
         const double dsy_y = cdy0(D.mu_x, n, iy, i);
         const double jzb_ = -(dsx_x + dsy_y) * inv2h;  // dL/dj_z
         // pointwise terms of S
-        const double jyb = -sxb * bz / a - syb * ez / a;
-        const double jxb = -sxb * ez / a + syb * bz / a;
-        const double bzb = (-sxb * jy + syb * jx) / a;
-        const double ezb = -(sxb * jx + syb * jy) / a;
-        double Gb = (sxb * gx + syb * gy) / a2;
-        const double gxb = sxb * (G / a2 - txx / a) - syb * txy / a;
-        const double gyb = syb * (G / a2 - tyy / a) - sxb * txy / a;
-        const double txxb = -sxb * gx / a + dsx_x * inv2h;
-        const double txyb = -(sxb * gy + syb * gx) / a + (dsx_y + dsy_x) * inv2h;
-        const double tyyb = -syb * gy / a + dsy_y * inv2h;
-        double ab = sxb * (jy * bz / a2 - 2.0 * G * gx / a3 + jx * ez / a2 +
-                           (txx * gx + txy * gy) / a2) +
-                    syb * (-jx * bz / a2 - 2.0 * G * gy / a3 + jy * ez / a2 +
-                           (txy * gx + tyy * gy) / a2);
+        const double jyb = -sxb * bz * ia - syb * ez * ia;
+        const double jxb = -sxb * ez * ia + syb * bz * ia;
+        const double bzb = (-sxb * jy + syb * jx) * ia;
+        const double ezb = -(sxb * jx + syb * jy) * ia;
+        double Gb = (sxb * gx + syb * gy) * ia2;
+        const double gxb = sxb * (G * ia2 - txx * ia) - syb * txy * ia;
+        const double gyb = syb * (G * ia2 - tyy * ia) - sxb * txy * ia;
+        const double txxb = -sxb * gx * ia + dsx_x * inv2h;
+        const double txyb = -(sxb * gy + syb * gx) * ia + (dsx_y + dsy_x) * inv2h;
+        const double tyyb = -syb * gy * ia + dsy_y * inv2h;
+        double ab = sxb * (jy * bz * ia2 - 2.0 * G * gx * ia3 + jx * ez * ia2 +
+                           (txx * gx + txy * gy) * ia2) +
+                    syb * (-jx * bz * ia2 - 2.0 * G * gy * ia3 + jy * ez * ia2 +
+                           (txy * gx + tyy * gy) * ia2);
         // j_z and kappa
-        Gb += jzb_ / a;
-        const double nb = -jzb_ + kapb / a;
-        ab += -jzb_ * G / a2 - kapb * nv / a2;
+        Gb += jzb_ * ia;
+        const double nb = -jzb_ + kapb * ia;
+        ab += -jzb_ * G * ia2 - kapb * nv * ia2;
         if (!act) ab = 0.0;
         J0[i] += (S.q == 0 ? 1.0 : 1.0 - frac) * jzb_;
         if (S.q != 0 && J1) J1[i] += frac * jzb_;
@@ -391,8 +392,9 @@ __device__ void adj_moments(const EngineArgs &A, const AdjArgs &D, const Slice &
         double a = 1.0 + Gp.v;
         const bool act = a >= A.psi_floor;
         if (!act) a = A.psi_floor;
-        const double vx = px / a, vy = py / a;
-        const double gam = (1.0 + px * px + py * py + a * a) / (2.0 * a);
+        const double ia = 1.0 / a, ia2 = ia * ia;
+        const double vx = px * ia, vy = py * ia;
+        const double gam = (1.0 + px * px + py * py + a * a) * (0.5 * ia);
         const GatherD Gjx = gather_d(D.g_jx, c), Gjy = gather_d(D.g_jy, c),
                       Gxx = gather_d(D.g_txx, c), Gxy = gather_d(D.g_txy, c),
                       Gyy = gather_d(D.g_tyy, c), GG = gather_d(D.g_G, c);
@@ -403,11 +405,11 @@ __device__ void adj_moments(const EngineArgs &A, const AdjArgs &D, const Slice &
         const double vxb = w * s2 * (Gjx.v + 2.0 * vx * Gxx.v + vy * Gxy.v);
         const double vyb = w * s2 * (Gjy.v + vx * Gxy.v + 2.0 * vy * Gyy.v);
         const double gb = w * s2 * GG.v;
-        double ab = -(vxb * px + vyb * py) / (a * a) +
-                    gb * (0.5 - (1.0 + px * px + py * py) / (2.0 * a * a));
+        double ab = -(vxb * px + vyb * py) * ia2 +
+                    gb * (0.5 - (1.0 + px * px + py * py) * (0.5 * ia2));
         if (!act) ab = 0.0;
-        D.lpx[p] += vxb / a + gb * px / a;
-        D.lpy[p] += vyb / a + gb * py / a;
+        D.lpx[p] += vxb * ia + gb * px * ia;
+        D.lpy[p] += vyb * ia + gb * py * ia;
         const double wq = w * s2 * ih;
         D.lx[p] += wq * (qjx * Gjx.dx + qjy * Gjy.dx + qxx * Gxx.dx + qxy * Gxy.dx +
                          qyy * Gyy.dx + qG * GG.dx) + ab * Gp.dx * ih;
