@@ -107,7 +107,7 @@ def tune(wls: Sequence, precision: str = "fp32r", n_slices: int = 16,
 
 
 def tune_team(wls: Sequence, per_size: Dict, precision: str = "fp32r", n_slices: int = 16,
-              teams: Sequence[int] = (0, 6, 12, 19), verbose: bool = False) -> int:
+              teams: Sequence[int] = (0, 4, 6, 8, 12, 19), verbose: bool = False) -> int:
     """Blocks per team (0 = one team per instance) that minimise the time of
     the whole truncated batch with the per-size settings `per_size`."""
     beams_cache: Dict = {}
