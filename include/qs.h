@@ -196,8 +196,9 @@ int qs_step3d_schedule(qs_ctx *ctx, const qs_beam *beams, int n_beams,
  * contexts, which may differ in size, window, drivers, tiles and sweeps, in a
  * single persistent launch.  The launch is split into teams of `team_blocks`
  * thread blocks (0 = as many blocks per team as leave every instance its own
- * team); each team takes the next context from a device-side queue and runs
- * its whole slice loop behind the team's own barrier.  All contexts must use
+ * team); each team takes the next context from a device-side queue (largest
+ * first: cells plus particles, times slices) and runs its whole slice loop
+ * behind the team's own barrier.  All contexts must use
  * one precision and one device; the launch is queued on the first context's
  * stream and the call synchronises it.  beams[i] / n_beams[i] give context
  * i's drivers (DEVICE arrays; both lists may be NULL for no drivers).

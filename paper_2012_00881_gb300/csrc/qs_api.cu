@@ -712,19 +712,29 @@ int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const i
     qs_ctx *c = ctxs[0];
     if (team_blocks < 0) return fail(c, QS_ERR_ARG, "team_blocks must be >= 0");
     cudaStream_t st = c->st;
+    // the device queue hands out instances in list order: largest first
+    // (cells x particles x slices), so that the last ones to start are short
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto cost = [&](int i) {
+        const qs_ctx *x = ctxs[i];
+        return ((double)x->N * x->N + (double)x->np) * (double)x->cfg.n_xi;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
     std::vector<EngineArgs> list(n);
     size_t smem = 0;
-    for (int i = 0; i < n; ++i) {
+    for (int k = 0; k < n; ++k) {
+        const int i = order[k];
         ctxs[i]->ckpt_valid = false;  // the batched step stores no checkpoints
         ctxs[i]->store_valid = false;
         const int r = step_prepare(ctxs[i], beams ? beams[i] : nullptr, n_beams ? n_beams[i] : 0,
-                                   nullptr, st, list[i]);
+                                   nullptr, st, list[k]);
         if (r != QS_OK) {
             if (i > 0) fail(c, r, "context %d: %s", i, ctxs[i]->msg);
             return r;
         }
-        list[i].trace = nullptr;
-        list[i].trace_cap = 0;
+        list[k].trace = nullptr;
+        list[k].trace_cap = 0;
         if (ctxs[i]->engine_smem > smem) smem = ctxs[i]->engine_smem;
     }
     int total = 0;
