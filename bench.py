@@ -108,11 +108,12 @@ def engine_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, workload: str, form: str):
+def measured_traffic(kernel: str, workload: str, form: str, profiles_dir: str = None,
+                     source_hash: str = None):
     """DRAM bytes per launch from the committed ncu summary of this kernel and
     workload, if it was captured on the current engine source; else None."""
-    d = os.path.join(ROOT, "profiles")
-    want = engine_source_hash()
+    d = profiles_dir or os.path.join(ROOT, "profiles")
+    want = source_hash or engine_source_hash()
     if not os.path.isdir(d):
         return None
     for fn in sorted(os.listdir(d)):

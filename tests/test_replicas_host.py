@@ -62,3 +62,20 @@ def test_single_process_needs_no_group():
     assert not dist.is_initialized()
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.job_rate(100, 1, 2.0) == 50.0
+
+
+def test_traffic_lines_are_matched_per_line_and_source(tmp_path):
+    """The roofline's measured traffic comes from a `<!-- traffic ... -->`
+    line of a profile summary whose source hash matches the engine's; every
+    line of a file is a candidate."""
+    import bench
+    (tmp_path / "a.md").write_text(
+        "text\n"
+        "<!-- traffic kernel=k workload=w form=fp32r source_sha256=abc bytes_per_launch=10 -->\n"
+        "<!-- traffic kernel=k workload=w form=fp64 source_sha256=abc bytes_per_launch=20 -->\n")
+    d = str(tmp_path)
+    assert bench.measured_traffic("k", "w", "fp32r", d, "abc") == 10.0
+    assert bench.measured_traffic("k", "w", "fp64", d, "abc") == 20.0
+    assert bench.measured_traffic("k", "w", "fp64", d, "other") is None
+    assert bench.measured_traffic("k", "x", "fp64", d, "abc") is None
+    assert len(bench.engine_source_hash()) == 16
