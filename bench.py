@@ -99,10 +99,10 @@ def _workload_desc(wl):
 ENGINE_SOURCES = ("qs_engine.cu", "qs_solve.cuh", "qs_mg.cuh", "qs_tile.cuh", "qs_internal.cuh")
 
 
-def engine_source_hash() -> str:
+def engine_source_hash(sources=ENGINE_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ENGINE_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2012_00881_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -577,6 +577,170 @@ def run_batched(args):
 
 
 # ---------------------------------------------------------------- oracle timing
+# ---------------------------------------------------------------- nonuniform grid
+NONUNI = "nonuni255"
+NONUNI_SOURCES = ("qs_nonuniform.cu",)
+# FP64 flops per finest node, field and V-cycle: four Gauss-Seidel sweeps of
+# the 9-point corrected operator (65 flops a node), one residual (63) and the
+# grid transfers (13), times 4/3 for the coarse levels, plus the residual of
+# the convergence test (63).
+NONUNI_FLOPS_PER_NODE_CYCLE = 4.0 / 3.0 * (4 * 65 + 63 + 13) + 63
+# The five solves of one slice, grouped as the slice advance groups them:
+# psi; E_z and B_z (one Poisson pair); B_x and B_y (one screened pair).
+NONUNI_GROUPS = ((("psi",), False), (("ez", "bz"), False), (("bx", "by"), True))
+
+
+def _nonuni_inputs(wl):
+    import numpy as np
+    from workloads.nonuniform import bubble_sources
+    xn = wl.axis()
+    src = bubble_sources(xn, xn, wl.bubble_radius)
+    groups = [(np.stack([src[k] for k in keys]), src["m"] if screened else None)
+              for keys, screened in NONUNI_GROUPS]
+    return xn, groups
+
+
+def _nonuni_desc(wl, xn):
+    import numpy as np
+    h = np.diff(xn)
+    return (f"{wl.name}: {wl.n}x{wl.n} nodes over [-{wl.half_width:g},{wl.half_width:g}]^2, "
+            f"three-region spacing {h.min():.4f}..{h.max():.4f}, 9-point operator with the "
+            f"third-order correction, the five field solves of one blowout slice "
+            f"(psi; E_z+B_z; B_x+B_y screened) from a zero guess to mg_tol={wl.mg_tol:g}")
+
+
+def run_nonuniform(args):
+    """The field solves of one xi-slice on the nonuniform transverse grid of
+    the nonuniform-grid section (255^2 nodes, three-region spacing): psi, the
+    E_z/B_z pair and the screened B_x/B_y pair, each from a zero initial guess.
+    A step is that set of five solves."""
+    import numpy as np
+    import torch
+
+    import paper_2012_00881_gb300 as qs
+    from workloads.nonuniform import nonuniform_workload
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("nccl")
+    wl = nonuniform_workload(NONUNI)
+    xn, groups = _nonuni_inputs(wl)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        solver = qs.NonuniformSolver(xn, xn, correction=True, stream=stream)
+        dev = [(torch.tensor(j, device="cuda"), None if m is None else torch.tensor(m, device="cuda"))
+               for j, m in groups]
+        outs = [torch.zeros_like(j) for j, _ in dev]
+    n_fields = sum(int(j.shape[0]) for j, _ in dev)
+    launch_ms, cycles_seen = [], []
+
+    def step(record):
+        for (j, m), u in zip(dev, outs):
+            u.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, cyc, _ = solver.solve(j, u=u, m=m, tol=wl.mg_tol, max_cycles=100)
+            e1.record(stream)
+            if record:
+                launch_ms.append((e0, e1, int(j.shape[0]), cyc))
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(False)
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        t1.record(stream)
+        stream.synchronize()
+        clocks = sampler.stop()
+    ms = max_over_ranks(t0.elapsed_time(t1)) / args.steps
+    value = job_rate(args.steps, world, ms * args.steps / 1e3)
+    # dominant kernel: the solve launch; flops counted from the cycles it ran
+    flops = sum(NONUNI_FLOPS_PER_NODE_CYCLE * wl.n * wl.n * nr * cyc for _, _, nr, cyc in launch_ms)
+    dur = sum(a.elapsed_time(b) for a, b, _, _ in launch_ms) / 1e3
+    cycles = [c for _, _, _, c in launch_ms[:len(dev)]]
+    fp64_peak = 1250.0  # GFLOP/s: 152 SMs x 2.07 GHz x 2 FP64 FMA per clock per SM (nominal)
+    achieved = flops / dur / 1e9
+    traffic = measured_traffic("nu_solve_kernel", NONUNI, "fp64",
+                               source_hash=engine_source_hash(NONUNI_SOURCES))
+
+    # end to end through the public API from pinned host buffers
+    host_j = [torch.tensor(j).pin_memory() for j, _ in groups]
+    host_m = [None if m is None else torch.tensor(m).pin_memory() for _, m in groups]
+    host_u = [torch.empty(j.shape, dtype=torch.float64).pin_memory() for j, _ in groups]
+    h2d = sum(t.numel() * 8 for t in host_j) + sum(t.numel() * 8 for t in host_m if t is not None)
+    d2h = sum(t.numel() * 8 for t in host_u)
+
+    def e2e_step():
+        for k, (j, m) in enumerate(dev):
+            j.copy_(host_j[k], non_blocking=True)
+            if m is not None:
+                m.copy_(host_m[k], non_blocking=True)
+            outs[k].zero_()
+            solver.solve(j, u=outs[k], m=m, tol=wl.mg_tol, max_cycles=100)
+            host_u[k].copy_(outs[k], non_blocking=True)
+        stream.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        stream.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    out = {
+        "metric": "nonuniform_slice_field_solves_per_s", "value": value,
+        "unit": "slice field sets/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _nonuni_desc(wl, xn), "fields_per_step": n_fields,
+                   "v_cycles": cycles, "l2": "working set (about 12 MB) is L2-resident; "
+                   "every step restarts the solves from zero"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                     "unit": "GFLOP/s (FP64, nominal peak)", "frac": achieved / fp64_peak,
+                     "traffic": traffic},
+        "e2e": {"value": job_rate(args.steps, world, e2e_ms * args.steps / 1e3),
+                "unit": "slice field sets/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": len(dev) * args.steps,  # one solve kernel per qs_nu_solve
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = nonuni_cpu_baseline(wl, args.cpu_seconds)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def nonuni_cpu_baseline(wl, seconds: float):
+    """The oracle's sparse-LU solves of the same five fields (one thread)."""
+    from oracle import qs_nonuniform as onu
+    xn, groups = _nonuni_inputs(wl)
+    t0 = time.perf_counter()
+    sets = 0
+    while True:
+        for j, m in groups:
+            for c in range(j.shape[0]):
+                onu.solve(xn, xn, j[c], m)
+        sets += 1
+        if time.perf_counter() - t0 > seconds / 3:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": sets / dt, "unit": "slice field sets/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sets} full sets of the five solves of {wl.name} with scipy sparse LU "
+                      f"(SuperLU), FP64, single thread"}
+
+
 def _oracle_sample(wl, seconds: float):
     """Time the FP64 oracle on the first base slices of one 3D step of the
     workload, growing the slice count until about `seconds` of CPU work."""
@@ -613,6 +777,8 @@ def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
         return
+    if args.workload == NONUNI:
+        return run_reference_nonuniform(args, world)
     wl = _load_workload(args)
     if wl is None:  # the scan: time the oracle on its 256^2 instances
         import workloads as W
@@ -638,6 +804,29 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_reference_nonuniform(args, world):
+    from workloads.nonuniform import nonuniform_workload
+    wl = nonuniform_workload(NONUNI)
+    per_step = max(2.0, args.cpu_seconds / 2)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        b = nonuni_cpu_baseline(wl, per_step)
+        if i >= args.warmup:
+            vals.append(b["value"])
+    v = statistics.mean(vals)
+    xn, _ = _nonuni_inputs(wl)
+    out = {"impl": "reference", "metric": "nonuniform_slice_field_solves_per_s", "value": v,
+           "unit": "slice field sets/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": _nonuni_desc(wl, xn), "form": "oracle"},
+           "cpu_baseline": {"value": v, "unit": "slice field sets/s", "cores": 1,
+                            "kind": "oracle", "sample": b["sample"]},
+           "e2e": {"value": v, "unit": "slice field sets/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
@@ -646,5 +835,7 @@ if __name__ == "__main__":
         run_batched(a)
     elif a.workload == GRAD:
         run_grad(a)
+    elif a.workload == NONUNI:
+        run_nonuniform(a)
     else:
         run_native(a)

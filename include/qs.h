@@ -369,6 +369,77 @@ int qs_cell_sort_noalloc(int n, double x_min, double y_min, double h, const doub
                          const double *y, const int32_t *id, int64_t np, int32_t *cell,
                          int32_t *count, int32_t *offset, int32_t *perm, void *cuda_stream);
 
+/* ---- Field solver on a nonuniform transverse grid ----------------------
+ * Sec. "Multigrid Solver with Nonuniform Grids": (d_xx + d_yy) Psi + M Psi = J
+ * on a tensor-product grid of nodes x_i, y_j, discretised with the
+ * three-point second differences of Eq. 2D_Laplac and, with the correction
+ * on, the third-order terms replaced as in Eq. 2D_Laplac_3rd (the mixed
+ * third derivatives as the three-point first difference of the other axis'
+ * second difference, d(lap) as that first difference of J - M Psi).  The
+ * discrete system is A Psi = J' with
+ *   A  = D2x + D2y + M + cx (D1x D2y + D1x M) + cy (D1y D2x + D1y M),
+ *   J' = J + (cx D1x + cy D1y) J,   c = (h^+ - h^-) / 3 per node and axis,
+ * a 9-point, non-symmetric operator (c = 0 with the correction off).  The
+ * third-order term is subtracted (Taylor expansion of the three-point
+ * difference) and the y bracket carries h_y^b.  Walls are nodes where Psi = 0
+ * and J = 0.  Arrays are [iy][ix] with ix fastest, float64.
+ *
+ * The solver is a multigrid V(2,2) cycle: coarse levels keep every other
+ * node and rediscretise A there, prolongation is linear interpolation in
+ * physical coordinates, restriction its dual-length-weighted transpose (also
+ * applied to M), the smoother four-colour Gauss-Seidel over-relaxed by 1.3,
+ * the 3 x 3 level is solved exactly.  The paper cites the transfer weights without giving
+ * them; these are the readings. */
+typedef struct qs_nu_solver qs_nu_solver;
+
+/* Build the hierarchy for n interior nodes per side, n = 2^k - 1 with
+ * 2 <= k <= 12 (3 .. 4095).  x_nodes, y_nodes: HOST arrays of n + 2 strictly
+ * increasing coordinates, the first and the last being the walls; copied (the
+ * caller keeps them).  correction: 1 = with the third-order correction, 0 =
+ * the plain three-point scheme.  cuda_stream: the cudaStream_t every call of
+ * this solver queues on (NULL = legacy default stream).  The solver owns its
+ * device memory (about 8 * 3.3 * n^2 * 4 bytes) until qs_nu_destroy.
+ * Argument checks come before any CUDA call.  Errors: QS_ERR_ARG (n not
+ * 2^k - 1, axes not increasing, bad flag), QS_ERR_OOM, QS_ERR_CUDA. */
+int qs_nu_create(int n, const double *x_nodes, const double *y_nodes, int correction,
+                 void *cuda_stream, qs_nu_solver **out);
+
+/* Solve A Psi = J' for nrhs (1 .. 4) fields that share M.
+ * d_m: DEVICE n*n screening M, or NULL for M = 0 (Poisson).  M <= 0 keeps the
+ *      operator elliptic (the screened equation of B_perp has M = -kappa).
+ * d_j: DEVICE [nrhs][n][n] sources J (not J'); J' is formed inside.
+ * d_u: DEVICE [nrhs][n][n]; in: initial guess, out: the solution (the last
+ *      iterate when the cycle cap is hit).  Caller-owned, written in place.
+ * Stops when every field has ||J' - A u||_2 <= tol ||J'||_2 (a field with
+ * J' = 0 gets u = 0), or after max_cycles V-cycles.  cycles (HOST, may be
+ * NULL) receives the V-cycles done; relres (HOST, nrhs, may be NULL) the
+ * final relative residuals.  Synchronises the solver's stream.
+ * Errors: QS_ERR_ARG, QS_ERR_NOT_CONVERGED (cap hit), QS_ERR_TIMEOUT (a grid
+ * barrier wait ran out; the kernel returned), QS_ERR_CUDA. */
+int qs_nu_solve(qs_nu_solver *s, const double *d_m, int nrhs, const double *d_j, double *d_u,
+                double tol, int max_cycles, int *cycles, double *relres);
+
+/* Cycle of the following solves: pre_sweeps and post_sweeps (0 .. 8,
+ * sum >= 1) four-colour Gauss-Seidel sweeps per level, relaxed by omega
+ * (0 < omega < 2; 1 = plain Gauss-Seidel); levels of side <= coarse_block_n
+ * are relaxed by one thread block, the larger ones by the whole GPU
+ * (0 = default).  Defaults 2, 2, 1.3, 15.  Host only.  Errors: QS_ERR_ARG. */
+int qs_nu_set_cycle(qs_nu_solver *s, int pre_sweeps, int post_sweeps, double omega,
+                    int coarse_block_n);
+
+/* d_out = A d_u for one field (DEVICE, n*n each; d_m as in qs_nu_solve).
+ * Queued on the solver's stream without waiting.  Errors: QS_ERR_ARG,
+ * QS_ERR_CUDA. */
+int qs_nu_apply(qs_nu_solver *s, const double *d_m, const double *d_u, double *d_out);
+
+/* d_out = J' = J + (cx D1x + cy D1y) J for one field (DEVICE, n*n each).
+ * Queued on the solver's stream without waiting.  Errors: QS_ERR_ARG,
+ * QS_ERR_CUDA. */
+int qs_nu_source(qs_nu_solver *s, const double *d_j, double *d_out);
+
+/* Free the solver and its device memory (NULL is a no-op). */
+void qs_nu_destroy(qs_nu_solver *s);
+
 /* Name of a status code (static string). */
 const char *qs_strerror(int status);
 

@@ -100,6 +100,12 @@ PROTOTYPES = {
     "qs_profile_adjoint": (_I, [_P, _P, _P, _I, _D, _P]),
     "qs_bigaussian_beam": (_I, [_P, _P, _I64, _D, _P, _P]),
     "qs_bigaussian_adjoint": (_I, [_P, _P, _I64, _P, _P, _P, _P, _P, _P]),
+    "qs_nu_create": (_I, [_I, _P, _P, _I, _P, ctypes.POINTER(_P)]),
+    "qs_nu_solve": (_I, [_P, _P, _I, _P, _P, _D, _I, _P, _P]),
+    "qs_nu_set_cycle": (_I, [_P, _I, _I, _D, _I]),
+    "qs_nu_apply": (_I, [_P, _P, _P, _P]),
+    "qs_nu_source": (_I, [_P, _P, _P]),
+    "qs_nu_destroy": (None, [_P]),
     "qs_strerror": (ctypes.c_char_p, [_I]),
     "qs_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -460,3 +466,88 @@ def bigaussian_adjoint(theta: Sequence[float], z, d_x, d_y, d_xi, d_w):
     if rc != QS_OK:
         raise QsError(rc, "qs_bigaussian_adjoint: " + lib.qs_strerror(rc).decode())
     return out
+
+
+class NonuniformSolver:
+    """qs_nu_* on a nonuniform tensor-product grid (float64 CUDA tensors).
+
+    x_nodes, y_nodes: n + 2 increasing coordinates, walls first and last
+    (array-likes, copied by the library).  correction=True selects the 9-point
+    operator with the third-order correction."""
+
+    def __init__(self, x_nodes, y_nodes, correction: bool = True, stream=None):
+        import numpy as np
+        import torch
+        self._lib = load_library()
+        self.h = None
+        xn = np.ascontiguousarray(x_nodes, dtype=np.float64)
+        yn = np.ascontiguousarray(y_nodes, dtype=np.float64)
+        if xn.size != yn.size:
+            raise QsError(QS_ERR_ARG, "x_nodes and y_nodes differ in length")
+        self.n = int(xn.size) - 2
+        self._stream = torch.cuda.current_stream() if stream is None else stream
+        h = _P()
+        rc = self._lib.qs_nu_create(self.n, xn.ctypes.data, yn.ctypes.data, int(bool(correction)),
+                                    _P(self._stream.cuda_stream), ctypes.byref(h))
+        if rc != QS_OK:
+            raise QsError(rc, "qs_nu_create: " + self._lib.qs_strerror(rc).decode())
+        self.h = h.value
+
+    def _check(self, rc: int, what: str):
+        if rc != QS_OK:
+            raise QsError(rc, f"{what}: " + self._lib.qs_strerror(rc).decode())
+
+    def solve(self, j, u=None, m=None, tol: float = 1e-10, max_cycles: int = 50,
+              raise_on_error: bool = True):
+        """Solve for j of shape [n, n] or [nrhs, n, n]; u (same shape) is the
+        initial guess and receives the solution.  Returns (u, cycles, relres)."""
+        import torch
+        squeeze = j.dim() == 2
+        jj = j.reshape(-1, self.n, self.n).contiguous()
+        if u is None:
+            u = torch.zeros_like(jj)
+        uu = u.reshape(-1, self.n, self.n)
+        nrhs = int(jj.shape[0])
+        cycles = ctypes.c_int(0)
+        relres = (ctypes.c_double * 4)()
+        rc = self._lib.qs_nu_solve(self.h, _ptr(m), nrhs, _ptr(jj), _ptr(uu), float(tol),
+                                   int(max_cycles), ctypes.byref(cycles),
+                                   ctypes.cast(relres, _P))
+        self.status = rc
+        if raise_on_error:
+            self._check(rc, "qs_nu_solve")
+        out = uu[0] if squeeze else uu
+        return out, cycles.value, [relres[c] for c in range(nrhs)]
+
+    def set_cycle(self, pre_sweeps: int = 2, post_sweeps: int = 2, omega: float = 1.3,
+                  coarse_block_n: int = 0):
+        """Sweeps per level, Gauss-Seidel relaxation and the one-block level
+        size of later solves (0 = default)."""
+        self._check(self._lib.qs_nu_set_cycle(self.h, int(pre_sweeps), int(post_sweeps),
+                                              float(omega), int(coarse_block_n)),
+                    "qs_nu_set_cycle")
+
+    def apply(self, u, m=None):
+        import torch
+        out = torch.empty_like(u)
+        self._check(self._lib.qs_nu_apply(self.h, _ptr(m), _ptr(u), _ptr(out)), "qs_nu_apply")
+        self._stream.synchronize()
+        return out
+
+    def source(self, j):
+        import torch
+        out = torch.empty_like(j)
+        self._check(self._lib.qs_nu_source(self.h, _ptr(j), _ptr(out)), "qs_nu_source")
+        self._stream.synchronize()
+        return out
+
+    def close(self):
+        if self.h:
+            self._lib.qs_nu_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,894 @@
+// Multigrid field solver on a nonuniform transverse grid (Sec. "Multigrid
+// Solver with Nonuniform Grids").
+//
+// Operator.  On nodes x_i with spacings h^- = x_i - x_{i-1}, h^+ = x_{i+1} - x_i
+// the equation (d_xx + d_yy) Psi + M Psi = J is discretised with the
+// three-point second difference D2 of Eq. 2D_Laplac and its third-order term
+// replaced as in Eq. 2D_Laplac_3rd (mixed third derivatives as the first
+// difference D1 of the other axis' D2, d(lap) as D1 of J - M Psi):
+//     A   = D2x + D2y + M + cx (D1x D2y + D1x M) + cy (D1y D2x + D1y M)
+//     J'  = J + (cx D1x + cy D1y) J,           c = (h^+ - h^-) / 3.
+// The third-order term enters with a minus sign (the Taylor expansion of D2 is
+// d^2 + (h^b/3) d^3), and the y bracket carries h_y^b.  With correction off,
+// c = 0.  Walls are nodes with Psi = 0 and J = 0.  A couples the 3x3
+// neighbourhood of a node and is not symmetric.
+//
+// Multigrid.  n = 2^k - 1 nodes per side; a coarse level keeps every other
+// node (the walls stay), so its spacings are sums of two fine ones and its
+// operator is the same 9-point formula on the coarse nodes.  Prolongation is
+// linear interpolation in physical coordinates (tensor product); restriction
+// is its dual-volume-weighted transpose (every row sums to 1) and also carries
+// M down.  The smoother is four-colour Gauss-Seidel: colour (i & 1, j & 1),
+// since the corner couplings of the 9-point stencil would join points of one
+// red-black colour; it is over-relaxed (omega = 1.3 by default, which halves
+// the cycles on grids with 3:1 cells, where point smoothing is weakest).  The
+// coarsest level (3 x 3) is solved exactly with its inverse, formed once per
+// solve.
+//
+// Execution.  One persistent cooperative launch per solve: 152 blocks on a
+// bounded software grid barrier for the levels larger than local_n, one block
+// on __syncthreads for the rest.  FP64 runs at a small fraction of the FP32
+// rate on this GPU, so one SM's share is slow: only the smallest levels
+// (side <= 15 by default) stay in one block.  Every wait is bounded; a timeout sets an
+// error word that ends the kernel at the next barrier.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qs.h"
+
+namespace {
+
+constexpr int kMaxLevels = 12;      // n <= 4095
+constexpr int kMaxRhs = 4;
+constexpr int kThreads = 512;
+constexpr int kDefaultLocalN = 15;  // levels this small run in one block
+constexpr int kDefaultNu1 = 2, kDefaultNu2 = 2;  // V(2,2)
+constexpr double kDefaultOmega = 1.3;
+constexpr long long kBarrierLimit = 4000000000LL;  // clock cycles, ~2 s
+
+// Per-node coefficients of one axis: D2 (at i-1, i, i+1), D1 (same), c.
+struct AxisCoef {
+    double d2[3];
+    double d1[3];
+    double c;
+    double pad;
+};
+
+struct NuLevel {
+    int n;
+    const AxisCoef *ax, *ay;  // n each
+    const double *pwx, *pwy;  // prolongation weights (2 per node; even nodes used)
+    const double *rwx, *rwy;  // restriction weights of the next coarser level (3 per coarse node)
+    double *u, *f, *r;        // kMaxRhs * n * n (level 0: u is the caller's buffer)
+    double *m, *idiag;        // n * n
+};
+
+struct NuScalars {
+    unsigned long long bar;
+    int err;
+    int err_where;
+    int cycles;
+    int converged;
+    double norm[3][kMaxRhs];  // rotating residual-norm slots
+    double fnorm[kMaxRhs];
+    double relres[kMaxRhs];
+};
+
+struct NuArgs {
+    NuLevel lv[kMaxLevels];
+    int levels;
+    int nrhs;
+    int has_m;
+    int max_cycles;
+    int nu1, nu2;             // pre- and post-smoothing sweeps
+    double omega;             // Gauss-Seidel relaxation factor (folded into idiag)
+    int local_n;              // levels of side <= local_n run in block 0 alone
+    double tol;
+    const double *j;          // caller's sources (solve) / input (apply, source)
+    const double *m_in;       // caller's M or nullptr
+    double *coarse_inv;       // 81 doubles: inverse of the 3 x 3 level's matrix
+    NuScalars *sc;
+};
+
+__device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
+__device__ __forceinline__ double vload(const double *p) { return *(const volatile double *)p; }
+
+__device__ __forceinline__ unsigned long long acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid-wide barrier of all blocks of the launch; false once any block has
+// recorded an error (then every block leaves the kernel).
+struct GridBarrier {
+    NuScalars *sc;
+    unsigned long long *epoch;  // shared-memory count of this block's barriers
+    __device__ bool operator()(int where) const {
+        __shared__ int s_ok;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int ok = vload(&sc->err) == 0;
+            if (ok) {
+                const unsigned long long target = (*epoch + 1) * gridDim.x;
+                *epoch += 1;
+                release_add_u64(&sc->bar, 1ull);
+                const long long t0 = clock64();
+                while (acquire_u64(&sc->bar) < target) {
+                    if (vload(&sc->err) != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (clock64() - t0 > kBarrierLimit) {
+                        if (atomicCAS(&sc->err, 0, QS_ERR_TIMEOUT) == 0) sc->err_where = where;
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        return s_ok != 0;
+    }
+};
+
+// Threads taking part in a phase: the whole grid, or block 0 alone.
+struct Team {
+    int t, nt;
+};
+
+__device__ __forceinline__ double at(const double *u, int n, int i, int j) {
+    return (i < 0 || j < 0 || i >= n || j >= n) ? 0.0 : u[j * n + i];
+}
+
+// (A u)(i, j) of one field; mrow/mcol are M at (i+a, j) and (i, j+b).
+template <bool CORR>
+__device__ __forceinline__ double apply_point(const AxisCoef &cx, const AxisCoef &cy,
+                                              const double (&v)[3][3], const double (&mrow)[3],
+                                              const double (&mcol)[3], double m0) {
+    double lx[3], ly[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+        lx[b] = cx.d2[0] * v[b][0] + cx.d2[1] * v[b][1] + cx.d2[2] * v[b][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        ly[a] = cy.d2[0] * v[0][a] + cy.d2[1] * v[1][a] + cy.d2[2] * v[2][a];
+    double s = lx[1] + ly[1] + m0 * v[1][1];
+    if (CORR) {
+        double tx = 0.0, ty = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) tx += cx.d1[a] * (ly[a] + mrow[a] * v[1][a]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) ty += cy.d1[b] * (lx[b] + mcol[b] * v[b][1]);
+        s += cx.c * tx + cy.c * ty;
+    }
+    return s;
+}
+
+__device__ __forceinline__ void load_m(const double *m, int n, int i, int j, double (&mrow)[3],
+                                       double (&mcol)[3], double &m0) {
+    if (m) {
+        m0 = m[j * n + i];
+        mrow[0] = at(m, n, i - 1, j);
+        mrow[1] = m0;
+        mrow[2] = at(m, n, i + 1, j);
+        mcol[0] = at(m, n, i, j - 1);
+        mcol[1] = m0;
+        mcol[2] = at(m, n, i, j + 1);
+    } else {
+        m0 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) mrow[k] = mcol[k] = 0.0;
+    }
+}
+
+__device__ __forceinline__ void load_v(const double *u, int n, int i, int j, double (&v)[3][3]) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[b][a] = at(u, n, i + a - 1, j + b - 1);
+}
+
+// Diagonal of A at (i, j): the coefficient of u(i, j) in apply_point.
+template <bool CORR>
+__device__ __forceinline__ double diag_point(const AxisCoef &cx, const AxisCoef &cy, double m0) {
+    double d = cx.d2[1] + cy.d2[1] + m0;
+    if (CORR) d += cx.c * cx.d1[1] * (cy.d2[1] + m0) + cy.c * cy.d1[1] * (cx.d2[1] + m0);
+    return d;
+}
+
+// One colour of Gauss-Seidel on all fields: points with (i & 1, j & 1) = (ci, cj).
+template <bool CORR>
+__device__ void gs_colour(const NuLevel &L, int nrhs, int ci, int cj, Team tm) {
+    const int n = L.n;
+    const int ni = (n - ci + 1) / 2, nj = (n - cj + 1) / 2;
+    const int cnt = ni * nj;
+    for (int p = tm.t; p < cnt; p += tm.nt) {
+        const int jj = p / ni;
+        const int i = 2 * (p - jj * ni) + ci, j = 2 * jj + cj;
+        const AxisCoef &cx = L.ax[i], &cy = L.ay[j];
+        double mrow[3], mcol[3], m0;
+        load_m(L.m, n, i, j, mrow, mcol, m0);
+        const double id = L.idiag[j * n + i];
+        for (int c = 0; c < nrhs; ++c) {
+            double *u = L.u + (size_t)c * n * n;
+            double v[3][3];
+            load_v(u, n, i, j, v);
+            const double res = L.f[(size_t)c * n * n + j * n + i] -
+                               apply_point<CORR>(cx, cy, v, mrow, mcol, m0);
+            u[j * n + i] = v[1][1] + res * id;
+        }
+    }
+}
+
+template <bool CORR, typename Sync>
+__device__ bool smooth(const NuLevel &L, int nrhs, int sweeps, Team tm, const Sync &sync,
+                       int where) {
+    for (int s = 0; s < sweeps; ++s)
+        for (int col = 0; col < 4; ++col) {
+            gs_colour<CORR>(L, nrhs, col & 1, col >> 1, tm);
+            if (!sync(where)) return false;
+        }
+    return true;
+}
+
+// r = f - A u on a level; optionally accumulates |r|^2 per field into acc.
+template <bool CORR>
+__device__ void residual(const NuLevel &L, int nrhs, Team tm, double *acc) {
+    const int n = L.n;
+    for (int p = tm.t; p < n * n; p += tm.nt) {
+        const int j = p / n, i = p - j * n;
+        double mrow[3], mcol[3], m0;
+        load_m(L.m, n, i, j, mrow, mcol, m0);
+        for (int c = 0; c < nrhs; ++c) {
+            double v[3][3];
+            load_v(L.u + (size_t)c * n * n, n, i, j, v);
+            const double r = L.f[(size_t)c * n * n + p] -
+                             apply_point<CORR>(L.ax[i], L.ay[j], v, mrow, mcol, m0);
+            L.r[(size_t)c * n * n + p] = r;
+            if (acc) acc[c] += r * r;
+        }
+    }
+}
+
+// Coarse f = R r (dual-volume-weighted full weighting), coarse u = 0.
+__device__ void restrict_residual(const NuLevel &F, const NuLevel &C, int nrhs, Team tm) {
+    const int nc = C.n, nf = F.n;
+    for (int p = tm.t; p < nc * nc; p += tm.nt) {
+        const int J = p / nc, I = p - J * nc;
+        const int i = 2 * I + 1, j = 2 * J + 1;
+        const double *wx = F.rwx + 3 * I, *wy = F.rwy + 3 * J;
+        for (int c = 0; c < nrhs; ++c) {
+            const double *r = F.r + (size_t)c * nf * nf;
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const double *row = r + (size_t)(j + b - 1) * nf + i - 1;
+                s += wy[b] * (wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2]);
+            }
+            C.f[(size_t)c * nc * nc + p] = s;
+            C.u[(size_t)c * nc * nc + p] = 0.0;
+        }
+    }
+}
+
+// Fine u += P (coarse u): bilinear interpolation in physical coordinates.
+__device__ void prolong_correct(const NuLevel &F, const NuLevel &C, int nrhs, Team tm) {
+    const int nf = F.n, nc = C.n;
+    for (int p = tm.t; p < nf * nf; p += tm.nt) {
+        const int j = p / nf, i = p - j * nf;
+        // x: odd i is coarse node (i-1)/2; even i lies between (i-2)/2 and i/2
+        int ix0, ix1, iy0, iy1;
+        double wx0, wx1, wy0, wy1;
+        if (i & 1) {
+            ix0 = ix1 = (i - 1) / 2;
+            wx0 = 1.0;
+            wx1 = 0.0;
+        } else {
+            ix0 = (i - 2) / 2;
+            ix1 = i / 2;
+            wx0 = F.pwx[2 * i];
+            wx1 = F.pwx[2 * i + 1];
+        }
+        if (j & 1) {
+            iy0 = iy1 = (j - 1) / 2;
+            wy0 = 1.0;
+            wy1 = 0.0;
+        } else {
+            iy0 = (j - 2) / 2;
+            iy1 = j / 2;
+            wy0 = F.pwy[2 * j];
+            wy1 = F.pwy[2 * j + 1];
+        }
+        for (int c = 0; c < nrhs; ++c) {
+            const double *e = C.u + (size_t)c * nc * nc;
+            const double v = wy0 * (wx0 * at(e, nc, ix0, iy0) + wx1 * at(e, nc, ix1, iy0)) +
+                             wy1 * (wx0 * at(e, nc, ix0, iy1) + wx1 * at(e, nc, ix1, iy1));
+            F.u[(size_t)c * nf * nf + p] += v;
+        }
+    }
+}
+
+// M on the next coarser level (same weights as the residual) and 1/diag.
+template <bool CORR>
+__device__ void level_setup(const NuArgs &A, int l, Team tm) {
+    const NuLevel &L = A.lv[l];
+    const int n = L.n;
+    if (l > 0 && A.has_m) {
+        const NuLevel &F = A.lv[l - 1];
+        const int nf = F.n;
+        for (int p = tm.t; p < n * n; p += tm.nt) {
+            const int J = p / n, I = p - J * n;
+            const int i = 2 * I + 1, j = 2 * J + 1;
+            const double *wx = F.rwx + 3 * I, *wy = F.rwy + 3 * J;
+            double s = 0.0;
+            for (int b = 0; b < 3; ++b) {
+                const double *row = F.m + (size_t)(j + b - 1) * nf + i - 1;
+                s += wy[b] * (wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2]);
+            }
+            L.m[p] = s;
+        }
+    }
+}
+
+// omega / diag(A): the Gauss-Seidel update is u += omega (f - A u) / diag.
+template <bool CORR>
+__device__ void level_idiag(const NuLevel &L, double omega, Team tm) {
+    const int n = L.n;
+    for (int p = tm.t; p < n * n; p += tm.nt) {
+        const int j = p / n, i = p - j * n;
+        const double m0 = L.m ? L.m[p] : 0.0;
+        L.idiag[p] = omega / diag_point<CORR>(L.ax[i], L.ay[j], m0);
+    }
+}
+
+// Inverse of the 3 x 3 level's 9 x 9 matrix by Gauss-Jordan with partial
+// pivoting (one thread; the columns are A applied to unit vectors).
+template <bool CORR>
+__device__ void coarse_inverse(const NuLevel &L, double *inv) {
+    double a[9][18];
+    for (int q = 0; q < 9; ++q) {
+        const int j = q / 3, i = q - 3 * j;
+        double mrow[3], mcol[3], m0;
+        load_m(L.m, 3, i, j, mrow, mcol, m0);
+        for (int col = 0; col < 9; ++col) {
+            double v[3][3];
+            for (int b = 0; b < 3; ++b)
+                for (int aa = 0; aa < 3; ++aa) {
+                    const int ii = i + aa - 1, jj = j + b - 1;
+                    v[b][aa] = (ii >= 0 && jj >= 0 && ii < 3 && jj < 3 && jj * 3 + ii == col) ? 1.0
+                                                                                           : 0.0;
+                }
+            a[q][col] = apply_point<CORR>(L.ax[i], L.ay[j], v, mrow, mcol, m0);
+            a[q][9 + col] = (q == col) ? 1.0 : 0.0;
+        }
+    }
+    for (int k = 0; k < 9; ++k) {
+        int piv = k;
+        for (int q = k + 1; q < 9; ++q)
+            if (fabs(a[q][k]) > fabs(a[piv][k])) piv = q;
+        if (piv != k)
+            for (int col = 0; col < 18; ++col) {
+                const double t = a[k][col];
+                a[k][col] = a[piv][col];
+                a[piv][col] = t;
+            }
+        const double ip = 1.0 / a[k][k];
+        for (int col = 0; col < 18; ++col) a[k][col] *= ip;
+        for (int q = 0; q < 9; ++q) {
+            if (q == k) continue;
+            const double f = a[q][k];
+            if (f != 0.0)
+                for (int col = 0; col < 18; ++col) a[q][col] -= f * a[k][col];
+        }
+    }
+    for (int q = 0; q < 9; ++q)
+        for (int col = 0; col < 9; ++col) inv[q * 9 + col] = a[q][9 + col];
+}
+
+__device__ void coarse_solve(const NuLevel &L, const double *inv, int nrhs, Team tm) {
+    for (int p = tm.t; p < 9 * nrhs; p += tm.nt) {
+        const int c = p / 9, q = p - 9 * c;
+        const double *f = L.f + 9 * c;
+        double s = 0.0;
+        for (int k = 0; k < 9; ++k) s += inv[q * 9 + k] * f[k];
+        L.u[9 * c + q] = s;
+    }
+}
+
+struct BlockSync {
+    __device__ bool operator()(int) const {
+        __syncthreads();
+        return true;
+    }
+};
+
+__device__ void block_reduce_add(double *vals, int nrhs, double *dst) {
+    __shared__ double red[kThreads / 32][kMaxRhs];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c = 0; c < nrhs; ++c) {
+        double v = vals[c];
+        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = 0; c < nrhs; ++c) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w][c];
+            atomicAdd(&dst[c], s);
+        }
+    __syncthreads();
+}
+
+// Descends from level `from` to the coarsest and back up (team `tm`, `sync`).
+template <bool CORR, typename Sync>
+__device__ bool vcycle_part(const NuArgs &A, int from, int to, Team tm, const Sync &sync) {
+    const int nr = A.nrhs;
+    for (int l = from; l < to; ++l) {
+        if (!smooth<CORR>(A.lv[l], nr, A.nu1, tm, sync, 10 + l)) return false;
+        residual<CORR>(A.lv[l], nr, tm, nullptr);
+        if (!sync(30 + l)) return false;
+        restrict_residual(A.lv[l], A.lv[l + 1], nr, tm);
+        if (!sync(50 + l)) return false;
+    }
+    return true;
+}
+
+template <bool CORR, typename Sync>
+__device__ bool upcycle_part(const NuArgs &A, int from, int to, Team tm, const Sync &sync) {
+    const int nr = A.nrhs;
+    for (int l = from; l >= to; --l) {
+        prolong_correct(A.lv[l], A.lv[l + 1], nr, tm);
+        if (!sync(70 + l)) return false;
+        if (!smooth<CORR>(A.lv[l], nr, A.nu2, tm, sync, 90 + l)) return false;
+    }
+    return true;
+}
+
+template <bool CORR>
+__global__ void __launch_bounds__(kThreads, 1) nu_solve_kernel(const __grid_constant__ NuArgs P) {
+    __shared__ NuArgs A;
+    __shared__ unsigned long long epoch;
+    if (threadIdx.x == 0) {
+        A = P;
+        epoch = 0;
+    }
+    __syncthreads();
+    GridBarrier gsync{A.sc, &epoch};
+    const Team grid{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x)};
+    const Team blk{(int)threadIdx.x, (int)blockDim.x};
+    NuScalars *sc = A.sc;
+    const int nr = A.nrhs, Lc = A.levels - 1;
+    // first level handled by block 0 alone
+    int loc = 0;
+    while (loc < Lc && A.lv[loc].n > A.local_n) ++loc;
+
+    // setup: M hierarchy and inverse diagonals (each level by the team that
+    // smooths it), then J' and the initial residual
+    level_idiag<CORR>(A.lv[0], A.omega, grid);
+    for (int l = 1; l <= Lc; ++l) {
+        if (l <= loc) {
+            level_setup<CORR>(A, l, grid);
+            if (!gsync(1)) return;
+            level_idiag<CORR>(A.lv[l], A.omega, grid);
+        } else if (blockIdx.x == 0) {
+            level_setup<CORR>(A, l, blk);
+            __syncthreads();
+            level_idiag<CORR>(A.lv[l], A.omega, blk);
+            __syncthreads();
+        }
+    }
+    {
+        const NuLevel &L = A.lv[0];
+        const int n = L.n;
+        double fn[kMaxRhs] = {0, 0, 0, 0}, rn[kMaxRhs] = {0, 0, 0, 0};
+        for (int p = grid.t; p < n * n; p += grid.nt) {
+            const int j = p / n, i = p - j * n;
+            double mrow[3], mcol[3], m0;
+            load_m(L.m, n, i, j, mrow, mcol, m0);
+            for (int c = 0; c < nr; ++c) {
+                const double *jc = A.j + (size_t)c * n * n;
+                double fv = jc[p];
+                if (CORR) {
+                    const AxisCoef &cx = L.ax[i], &cy = L.ay[j];
+                    const double dx = cx.d1[0] * at(jc, n, i - 1, j) + cx.d1[1] * fv +
+                                      cx.d1[2] * at(jc, n, i + 1, j);
+                    const double dy = cy.d1[0] * at(jc, n, i, j - 1) + cy.d1[1] * fv +
+                                      cy.d1[2] * at(jc, n, i, j + 1);
+                    fv += cx.c * dx + cy.c * dy;
+                }
+                L.f[(size_t)c * n * n + p] = fv;
+                double v[3][3];
+                load_v(L.u + (size_t)c * n * n, n, i, j, v);
+                const double r = fv - apply_point<CORR>(L.ax[i], L.ay[j], v, mrow, mcol, m0);
+                fn[c] += fv * fv;
+                rn[c] += r * r;
+            }
+        }
+        block_reduce_add(fn, nr, sc->fnorm);
+        block_reduce_add(rn, nr, sc->norm[0]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) coarse_inverse<CORR>(A.lv[Lc], A.coarse_inv);
+    if (!gsync(2)) return;
+
+    double fn2[kMaxRhs];
+    for (int c = 0; c < nr; ++c) fn2[c] = vload(&sc->fnorm[c]);
+    for (int cyc = 0;; ++cyc) {
+        // convergence test on the residual left by the previous cycle (slot cyc % 3)
+        bool conv = true;
+        for (int c = 0; c < nr; ++c) {
+            const double rn = vload(&sc->norm[cyc % 3][c]);
+            if (fn2[c] > 0.0 && rn > A.tol * A.tol * fn2[c]) conv = false;
+        }
+        if (conv || cyc >= A.max_cycles) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                sc->cycles = cyc;
+                sc->converged = conv ? 1 : 0;
+                for (int c = 0; c < nr; ++c)
+                    sc->relres[c] =
+                        fn2[c] > 0.0 ? sqrt(vload(&sc->norm[cyc % 3][c]) / fn2[c]) : 0.0;
+            }
+            // a field whose source is zero has the solution zero
+            const int n = A.lv[0].n;
+            for (int c = 0; c < nr; ++c)
+                if (fn2[c] == 0.0)
+                    for (int p = grid.t; p < n * n; p += grid.nt)
+                        A.lv[0].u[(size_t)c * n * n + p] = 0.0;
+            break;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            for (int c = 0; c < kMaxRhs; ++c) sc->norm[(cyc + 1) % 3][c] = 0.0;
+        if (Lc == 0) {
+            if (blockIdx.x == 0) coarse_solve(A.lv[0], A.coarse_inv, nr, blk);
+            if (!gsync(3)) return;
+        } else {
+            if (!vcycle_part<CORR>(A, 0, loc, grid, gsync)) return;
+            if (blockIdx.x == 0) {
+                const BlockSync bs;
+                vcycle_part<CORR>(A, loc, Lc, blk, bs);
+                coarse_solve(A.lv[Lc], A.coarse_inv, nr, blk);
+                __syncthreads();
+                upcycle_part<CORR>(A, Lc - 1, loc, blk, bs);
+            }
+            if (!gsync(3)) return;
+            if (loc > 0 && !upcycle_part<CORR>(A, loc - 1, 0, grid, gsync)) return;
+        }
+        // residual of the finest level for the next test
+        {
+            double rn[kMaxRhs] = {0, 0, 0, 0};
+            residual<CORR>(A.lv[0], nr, grid, rn);
+            block_reduce_add(rn, nr, sc->norm[(cyc + 1) % 3]);
+        }
+        if (!gsync(4)) return;
+    }
+}
+
+// Operator and corrected source of level 0 for one field (tests, diagnostics).
+template <bool CORR>
+__global__ void nu_apply_kernel(const __grid_constant__ NuArgs A, const double *u, double *out,
+                                int source) {
+    const NuLevel &L = A.lv[0];
+    const int n = L.n;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n * n; p += gridDim.x * blockDim.x) {
+        const int j = p / n, i = p - j * n;
+        const AxisCoef &cx = L.ax[i], &cy = L.ay[j];
+        if (source) {
+            double fv = u[p];
+            if (CORR) {
+                const double dx = cx.d1[0] * at(u, n, i - 1, j) + cx.d1[1] * fv +
+                                  cx.d1[2] * at(u, n, i + 1, j);
+                const double dy = cy.d1[0] * at(u, n, i, j - 1) + cy.d1[1] * fv +
+                                  cy.d1[2] * at(u, n, i, j + 1);
+                fv += cx.c * dx + cy.c * dy;
+            }
+            out[p] = fv;
+        } else {
+            double mrow[3], mcol[3], m0, v[3][3];
+            load_m(A.m_in, n, i, j, mrow, mcol, m0);
+            load_v(u, n, i, j, v);
+            out[p] = apply_point<CORR>(cx, cy, v, mrow, mcol, m0);
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct qs_nu_solver {
+    int n = 0, levels = 0, correction = 0;
+    cudaStream_t stream = nullptr;
+    int grid_blocks = 0;
+    NuArgs args{};
+    void *dev = nullptr;       // one allocation: coefficients, level arrays, scalars
+    void *pinned = nullptr;    // host copy of NuScalars
+};
+
+namespace {
+
+void axis_coefficients(const std::vector<double> &x, int correction, std::vector<AxisCoef> &out) {
+    const int n = (int)x.size() - 2;
+    out.resize(n);
+    for (int i = 0; i < n; ++i) {
+        const double hm = x[i + 1] - x[i], hp = x[i + 2] - x[i + 1], ha = hm + hp;
+        AxisCoef c{};
+        c.d2[0] = 2.0 / (hm * ha);
+        c.d2[1] = -2.0 / (hm * hp);
+        c.d2[2] = 2.0 / (hp * ha);
+        const double fw = hm / (ha * hp), bw = hp / (ha * hm);
+        c.d1[0] = -bw;
+        c.d1[1] = bw - fw;
+        c.d1[2] = fw;
+        c.c = correction ? (hp - hm) / 3.0 : 0.0;
+        out[i] = c;
+    }
+}
+
+// Prolongation weights of the fine nodes (pairs; used at even 0-based nodes,
+// which lie between the coarse nodes or a coarse node and a wall).
+void prolong_weights(const std::vector<double> &x, std::vector<double> &out) {
+    const int n = (int)x.size() - 2;
+    out.assign(2 * n, 0.0);
+    for (int i = 0; i < n; i += 2) {
+        const int f = i + 1;  // index with the wall at 0
+        const double span = x[f + 1] - x[f - 1];
+        out[2 * i] = (x[f + 1] - x[f]) / span;       // weight of the left coarse node
+        out[2 * i + 1] = (x[f] - x[f - 1]) / span;   // weight of the right coarse node
+    }
+}
+
+// Restriction weights of each coarse node: the transpose of the prolongation
+// scaled by fine dual lengths over the coarse dual length (rows sum to 1).
+void restrict_weights(const std::vector<double> &x, const std::vector<double> &pw,
+                      std::vector<double> &out) {
+    const int n = (int)x.size() - 2, nc = (n - 1) / 2;
+    out.assign(3 * nc, 0.0);
+    auto dual = [&](int f) { return 0.5 * (x[f + 1] - x[f - 1]); };
+    for (int I = 0; I < nc; ++I) {
+        const int i = 2 * I + 1, f = i + 1;
+        const double vc = 0.5 * (x[f + 2] - x[f - 2]);
+        out[3 * I + 0] = pw[2 * (i - 1) + 1] * dual(f - 1) / vc;
+        out[3 * I + 1] = dual(f) / vc;
+        out[3 * I + 2] = pw[2 * (i + 1)] * dual(f + 1) / vc;
+    }
+}
+
+bool valid_axis(const double *x, int n) {
+    if (!x) return false;
+    for (int i = 0; i < n + 1; ++i)
+        if (!(x[i + 1] > x[i])) return false;  // also rejects NaN
+    return true;
+}
+
+int levels_for(int n) {
+    int l = 1;
+    while (n > 3) {
+        if ((n & 1) == 0) return 0;
+        n = (n - 1) / 2;
+        ++l;
+    }
+    return n == 3 ? l : 0;
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return QS_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? QS_ERR_OOM : QS_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" int qs_nu_create(int n, const double *x_nodes, const double *y_nodes, int correction,
+                            void *cuda_stream, qs_nu_solver **out) {
+    if (!out) return QS_ERR_ARG;
+    *out = nullptr;
+    if (n < 3 || n > 4095 || (correction != 0 && correction != 1)) return QS_ERR_ARG;
+    const int levels = levels_for(n);
+    if (levels < 1 || levels > kMaxLevels) return QS_ERR_ARG;
+    if (!valid_axis(x_nodes, n) || !valid_axis(y_nodes, n)) return QS_ERR_ARG;
+
+    qs_nu_solver *s = new (std::nothrow) qs_nu_solver();
+    if (!s) return QS_ERR_OOM;
+    s->n = n;
+    s->levels = levels;
+    s->correction = correction;
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+
+    // host tables per level, then one device allocation laid out as
+    // [scalars][coarse inverse][per level: ax, ay, pwx, pwy, rwx, rwy, u, f, r, m, idiag]
+    std::vector<double> xs(x_nodes, x_nodes + n + 2), ys(y_nodes, y_nodes + n + 2);
+    struct HostLevel {
+        int n;
+        std::vector<AxisCoef> ax, ay;
+        std::vector<double> pwx, pwy, rwx, rwy;
+    };
+    std::vector<HostLevel> hl(levels);
+    for (int l = 0; l < levels; ++l) {
+        HostLevel &h = hl[l];
+        h.n = (int)xs.size() - 2;
+        axis_coefficients(xs, correction, h.ax);
+        axis_coefficients(ys, correction, h.ay);
+        prolong_weights(xs, h.pwx);
+        prolong_weights(ys, h.pwy);
+        if (l + 1 < levels) {
+            restrict_weights(xs, h.pwx, h.rwx);
+            restrict_weights(ys, h.pwy, h.rwy);
+            std::vector<double> cx, cy;
+            for (size_t k = 0; k < xs.size(); k += 2) cx.push_back(xs[k]);
+            for (size_t k = 0; k < ys.size(); k += 2) cy.push_back(ys[k]);
+            xs.swap(cx);
+            ys.swap(cy);
+        }
+    }
+    auto align = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t bytes = align(sizeof(NuScalars)) + align(81 * sizeof(double));
+    for (int l = 0; l < levels; ++l) {
+        const size_t nn = (size_t)hl[l].n * hl[l].n;
+        bytes += 2 * align(hl[l].n * sizeof(AxisCoef));
+        bytes += align(hl[l].pwx.size() * 8) + align(hl[l].pwy.size() * 8);
+        bytes += align(hl[l].rwx.size() * 8) + align(hl[l].rwy.size() * 8);
+        bytes += 3 * align(kMaxRhs * nn * 8) + 2 * align(nn * 8);
+    }
+    int st = cuda_status(cudaMalloc(&s->dev, bytes));
+    if (st == QS_OK) st = cuda_status(cudaMallocHost(&s->pinned, sizeof(NuScalars)));
+    if (st != QS_OK) {
+        qs_nu_destroy(s);
+        return st;
+    }
+    char *base = static_cast<char *>(s->dev);
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        void *p = base + off;
+        off += align(b);
+        return p;
+    };
+    std::vector<char> host(bytes, 0);
+    auto put = [&](void *dst, const void *src, size_t b) {
+        if (b) std::memcpy(host.data() + (static_cast<char *>(dst) - base), src, b);
+    };
+    NuArgs &A = s->args;
+    A.nu1 = kDefaultNu1;
+    A.nu2 = kDefaultNu2;
+    A.omega = kDefaultOmega;
+    A.local_n = kDefaultLocalN;
+    A.sc = static_cast<NuScalars *>(take(sizeof(NuScalars)));
+    A.coarse_inv = static_cast<double *>(take(81 * sizeof(double)));
+    A.levels = levels;
+    for (int l = 0; l < levels; ++l) {
+        const HostLevel &h = hl[l];
+        const size_t nn = (size_t)h.n * h.n;
+        NuLevel &L = A.lv[l];
+        L.n = h.n;
+        L.ax = static_cast<AxisCoef *>(take(h.n * sizeof(AxisCoef)));
+        L.ay = static_cast<AxisCoef *>(take(h.n * sizeof(AxisCoef)));
+        put((void *)L.ax, h.ax.data(), h.n * sizeof(AxisCoef));
+        put((void *)L.ay, h.ay.data(), h.n * sizeof(AxisCoef));
+        L.pwx = static_cast<double *>(take(h.pwx.size() * 8));
+        L.pwy = static_cast<double *>(take(h.pwy.size() * 8));
+        put((void *)L.pwx, h.pwx.data(), h.pwx.size() * 8);
+        put((void *)L.pwy, h.pwy.data(), h.pwy.size() * 8);
+        L.rwx = static_cast<double *>(take(h.rwx.size() * 8));
+        L.rwy = static_cast<double *>(take(h.rwy.size() * 8));
+        put((void *)L.rwx, h.rwx.data(), h.rwx.size() * 8);
+        put((void *)L.rwy, h.rwy.data(), h.rwy.size() * 8);
+        L.u = static_cast<double *>(take(kMaxRhs * nn * 8));
+        L.f = static_cast<double *>(take(kMaxRhs * nn * 8));
+        L.r = static_cast<double *>(take(kMaxRhs * nn * 8));
+        L.m = static_cast<double *>(take(nn * 8));
+        L.idiag = static_cast<double *>(take(nn * 8));
+    }
+    st = cuda_status(cudaMemcpyAsync(s->dev, host.data(), bytes, cudaMemcpyHostToDevice, s->stream));
+    if (st == QS_OK) st = cuda_status(cudaStreamSynchronize(s->stream));
+    if (st != QS_OK) {
+        qs_nu_destroy(s);
+        return st;
+    }
+    // one block per SM (co-resident: the cooperative launch checks it)
+    int dev = 0, sms = 0, per_sm = 0;
+    st = cuda_status(cudaGetDevice(&dev));
+    if (st == QS_OK) st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (st == QS_OK)
+        st = cuda_status(correction ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                          &per_sm, nu_solve_kernel<true>, kThreads, 0)
+                                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                          &per_sm, nu_solve_kernel<false>, kThreads, 0));
+    if (st == QS_OK && per_sm < 1) st = QS_ERR_CUDA;
+    if (st != QS_OK) {
+        qs_nu_destroy(s);
+        return st;
+    }
+    s->grid_blocks = sms;
+    *out = s;
+    return QS_OK;
+}
+
+extern "C" int qs_nu_solve(qs_nu_solver *s, const double *d_m, int nrhs, const double *d_j,
+                           double *d_u, double tol, int max_cycles, int *cycles, double *relres) {
+    if (!s || !d_j || !d_u || nrhs < 1 || nrhs > kMaxRhs || max_cycles < 1) return QS_ERR_ARG;
+    if (!(tol > 0.0)) return QS_ERR_ARG;
+    NuArgs A = s->args;
+    A.nrhs = nrhs;
+    A.has_m = d_m != nullptr;
+    A.max_cycles = max_cycles;
+    A.tol = tol;
+    A.j = d_j;
+    A.m_in = d_m;
+    // level 0 works in place on the caller's u and reads the caller's M
+    // (never written); coarser levels hold the restricted M
+    A.lv[0].u = d_u;
+    A.lv[0].m = const_cast<double *>(d_m);
+    for (int l = 1; l < A.levels; ++l)
+        if (!d_m) A.lv[l].m = nullptr;
+    int st = cuda_status(cudaMemsetAsync(A.sc, 0, sizeof(NuScalars), s->stream));
+    if (st != QS_OK) return st;
+    void *params[] = {&A};
+    const void *fn = s->correction ? (const void *)nu_solve_kernel<true>
+                                   : (const void *)nu_solve_kernel<false>;
+    st = cuda_status(cudaLaunchCooperativeKernel(fn, dim3(s->grid_blocks), dim3(kThreads), params,
+                                                 0, s->stream));
+    if (st != QS_OK) return st;
+    st = cuda_status(cudaMemcpyAsync(s->pinned, A.sc, sizeof(NuScalars), cudaMemcpyDeviceToHost,
+                                     s->stream));
+    if (st == QS_OK) st = cuda_status(cudaStreamSynchronize(s->stream));
+    if (st != QS_OK) return st;
+    const NuScalars *h = static_cast<const NuScalars *>(s->pinned);
+    if (h->err) return h->err;
+    if (cycles) *cycles = h->cycles;
+    if (relres)
+        for (int c = 0; c < nrhs; ++c) relres[c] = h->relres[c];
+    return h->converged ? QS_OK : QS_ERR_NOT_CONVERGED;
+}
+
+extern "C" int qs_nu_set_cycle(qs_nu_solver *s, int pre_sweeps, int post_sweeps, double omega,
+                               int coarse_block_n) {
+    if (!s || pre_sweeps < 0 || post_sweeps < 0 || pre_sweeps > 8 || post_sweeps > 8 ||
+        pre_sweeps + post_sweeps < 1 || !(omega > 0.0 && omega < 2.0) || coarse_block_n < 0)
+        return QS_ERR_ARG;
+    s->args.nu1 = pre_sweeps;
+    s->args.nu2 = post_sweeps;
+    s->args.omega = omega;
+    s->args.local_n = coarse_block_n ? coarse_block_n : kDefaultLocalN;
+    return QS_OK;
+}
+
+extern "C" int qs_nu_apply(qs_nu_solver *s, const double *d_m, const double *d_u, double *d_out) {
+    if (!s || !d_u || !d_out) return QS_ERR_ARG;
+    NuArgs A = s->args;
+    A.m_in = d_m;
+    const int nn = s->n * s->n;
+    const int blocks = (nn + 255) / 256;
+    if (s->correction)
+        nu_apply_kernel<true><<<blocks, 256, 0, s->stream>>>(A, d_u, d_out, 0);
+    else
+        nu_apply_kernel<false><<<blocks, 256, 0, s->stream>>>(A, d_u, d_out, 0);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" int qs_nu_source(qs_nu_solver *s, const double *d_j, double *d_out) {
+    if (!s || !d_j || !d_out) return QS_ERR_ARG;
+    const int nn = s->n * s->n;
+    const int blocks = (nn + 255) / 256;
+    if (s->correction)
+        nu_apply_kernel<true><<<blocks, 256, 0, s->stream>>>(s->args, d_j, d_out, 1);
+    else
+        nu_apply_kernel<false><<<blocks, 256, 0, s->stream>>>(s->args, d_j, d_out, 1);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" void qs_nu_destroy(qs_nu_solver *s) {
+    if (!s) return;
+    if (s->dev) cudaFree(s->dev);
+    if (s->pinned) cudaFreeHost(s->pinned);
+    delete s;
+}

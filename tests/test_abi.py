@@ -70,3 +70,34 @@ def test_invalid_config_rejected_without_gpu(lib):
         cfg = qs.default_config(**bad)
         assert l.qs_create(ctypes.byref(cfg), None, ctypes.byref(h)) == qs.QS_ERR_ARG, bad
     assert l.qs_create(None, None, ctypes.byref(h)) == qs.QS_ERR_ARG
+
+
+def test_nonuniform_solver_arguments_rejected_without_gpu(lib):
+    """qs_nu_create validates n and the axes before any device call."""
+    import numpy as np
+    import paper_2012_00881_gb300 as qs
+    l = qs.load_library()
+    h = ctypes.c_void_p()
+
+    def create(n, xn, yn, corr=1):
+        xa = np.ascontiguousarray(xn, dtype=np.float64)
+        ya = np.ascontiguousarray(yn, dtype=np.float64)
+        return l.qs_nu_create(n, xa.ctypes.data, ya.ctypes.data, corr, None, ctypes.byref(h))
+
+    good = np.linspace(-1.0, 1.0, 17)
+    for n in (0, 1, 2, 4, 5, 6, 14, 16, 4096, 8191):
+        axis = np.linspace(-1.0, 1.0, max(n, 1) + 2)
+        assert create(n, axis, axis) == qs.QS_ERR_ARG, n
+    bad = good.copy()
+    bad[5] = bad[4]                       # repeated node
+    assert create(15, bad, good) == qs.QS_ERR_ARG
+    assert create(15, good, bad[::-1].copy()) == qs.QS_ERR_ARG
+    nan = good.copy()
+    nan[3] = float("nan")
+    assert create(15, nan, good) == qs.QS_ERR_ARG
+    assert create(15, good, good, corr=2) == qs.QS_ERR_ARG
+    assert l.qs_nu_create(15, None, None, 1, None, ctypes.byref(h)) == qs.QS_ERR_ARG
+    assert l.qs_nu_create(15, good.ctypes.data, good.ctypes.data, 1, None, None) == qs.QS_ERR_ARG
+    for args in ((None, None, 1, None, None, 1e-10, 10, None, None),):
+        assert l.qs_nu_solve(*args) == qs.QS_ERR_ARG
+    l.qs_nu_destroy(None)
