@@ -396,13 +396,17 @@ typedef struct qs_nu_solver qs_nu_solver;
  * 2 <= k <= 12 (3 .. 4095).  x_nodes, y_nodes: HOST arrays of n + 2 strictly
  * increasing coordinates, the first and the last being the walls; copied (the
  * caller keeps them).  correction: 1 = with the third-order correction, 0 =
- * the plain three-point scheme.  cuda_stream: the cudaStream_t every call of
- * this solver queues on (NULL = legacy default stream).  The solver owns its
- * device memory (about 8 * 3.3 * n^2 * 4 bytes) until qs_nu_destroy.
- * Argument checks come before any CUDA call.  Errors: QS_ERR_ARG (n not
- * 2^k - 1, axes not increasing, bad flag), QS_ERR_OOM, QS_ERR_CUDA. */
+ * the plain three-point scheme.  precision: QS_FP64 (every cycle in float64)
+ * or QS_FP32_REFINED (float32 V-cycles correct a float64 solution from its
+ * float64 residual each cycle; the stopping test and the result are those of
+ * float64).  cuda_stream: the cudaStream_t every call of this solver queues
+ * on (NULL = legacy default stream).  The solver owns its device memory
+ * (about 14 * 4/3 * n^2 elements of its precision, plus 5 n^2 float64 for
+ * the refined form) until qs_nu_destroy.  Argument checks come before any
+ * CUDA call.  Errors: QS_ERR_ARG (n not 2^k - 1, axes not increasing, bad
+ * flag), QS_ERR_OOM, QS_ERR_CUDA. */
 int qs_nu_create(int n, const double *x_nodes, const double *y_nodes, int correction,
-                 void *cuda_stream, qs_nu_solver **out);
+                 int precision, void *cuda_stream, qs_nu_solver **out);
 
 /* Solve A Psi = J' for nrhs (1 .. 4) fields that share M.
  * d_m: DEVICE n*n screening M, or NULL for M = 0 (Poisson).  M <= 0 keeps the
@@ -423,7 +427,7 @@ int qs_nu_solve(qs_nu_solver *s, const double *d_m, int nrhs, const double *d_j,
  * sum >= 1) four-colour Gauss-Seidel sweeps per level, relaxed by omega
  * (0 < omega < 2; 1 = plain Gauss-Seidel); levels of side <= coarse_block_n
  * are relaxed by one thread block, the larger ones by the whole GPU
- * (0 = default).  Defaults 2, 2, 1.3, 15.  Host only.  Errors: QS_ERR_ARG. */
+ * (0 = default).  Defaults 2, 2, 1.3, 31.  Host only.  Errors: QS_ERR_ARG. */
 int qs_nu_set_cycle(qs_nu_solver *s, int pre_sweeps, int post_sweeps, double omega,
                     int coarse_block_n);
 

@@ -100,7 +100,7 @@ PROTOTYPES = {
     "qs_profile_adjoint": (_I, [_P, _P, _P, _I, _D, _P]),
     "qs_bigaussian_beam": (_I, [_P, _P, _I64, _D, _P, _P]),
     "qs_bigaussian_adjoint": (_I, [_P, _P, _I64, _P, _P, _P, _P, _P, _P]),
-    "qs_nu_create": (_I, [_I, _P, _P, _I, _P, ctypes.POINTER(_P)]),
+    "qs_nu_create": (_I, [_I, _P, _P, _I, _I, _P, ctypes.POINTER(_P)]),
     "qs_nu_solve": (_I, [_P, _P, _I, _P, _P, _D, _I, _P, _P]),
     "qs_nu_set_cycle": (_I, [_P, _I, _I, _D, _I]),
     "qs_nu_apply": (_I, [_P, _P, _P, _P]),
@@ -473,9 +473,11 @@ class NonuniformSolver:
 
     x_nodes, y_nodes: n + 2 increasing coordinates, walls first and last
     (array-likes, copied by the library).  correction=True selects the 9-point
-    operator with the third-order correction."""
+    operator with the third-order correction; precision "fp64" or "fp32r"
+    (float32 cycles refining a float64 solution)."""
 
-    def __init__(self, x_nodes, y_nodes, correction: bool = True, stream=None):
+    def __init__(self, x_nodes, y_nodes, correction: bool = True, precision: str = "fp64",
+                 stream=None):
         import numpy as np
         import torch
         self._lib = load_library()
@@ -487,8 +489,11 @@ class NonuniformSolver:
         self.n = int(xn.size) - 2
         self._stream = torch.cuda.current_stream() if stream is None else stream
         h = _P()
+        if precision not in ("fp64", "fp32r"):
+            raise QsError(QS_ERR_ARG, f"precision {precision!r}")
+        prec = QS_FP64 if precision == "fp64" else QS_FP32_REFINED
         rc = self._lib.qs_nu_create(self.n, xn.ctypes.data, yn.ctypes.data, int(bool(correction)),
-                                    _P(self._stream.cuda_stream), ctypes.byref(h))
+                                    prec, _P(self._stream.cuda_stream), ctypes.byref(h))
         if rc != QS_OK:
             raise QsError(rc, "qs_nu_create: " + self._lib.qs_strerror(rc).decode())
         self.h = h.value

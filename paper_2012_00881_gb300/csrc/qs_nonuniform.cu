@@ -27,10 +27,18 @@
 //
 // Execution.  One persistent cooperative launch per solve: 152 blocks on a
 // bounded software grid barrier for the levels larger than local_n, one block
-// on __syncthreads for the rest.  FP64 runs at a small fraction of the FP32
-// rate on this GPU, so one SM's share is slow: only the smallest levels
-// (side <= 15 by default) stay in one block.  Every wait is bounded; a timeout sets an
-// error word that ends the kernel at the next barrier.
+// on __syncthreads for the rest (side <= 31 by default: below that a level's
+// work is too small to pay for ~20 grid barriers, above it one SM's share
+// of the work, which FP64 makes slow on this GPU, costs more than they do).
+//
+// Forms.  FP64 cycles on a float64 hierarchy.  The refined form keeps the
+// solution, J' and the residual in float64 and cycles in float32 on the
+// residual equation (iterative refinement): every outer step is one float32
+// V-cycle for the correction, u += e, then the float64 residual, which is
+// also the stopping test, so both forms stop at the same float64 accuracy.
+//
+// Every wait is bounded; a timeout sets an error word that ends the kernel at
+// the next barrier.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,26 +53,29 @@ namespace {
 constexpr int kMaxLevels = 12;      // n <= 4095
 constexpr int kMaxRhs = 4;
 constexpr int kThreads = 512;
-constexpr int kDefaultLocalN = 15;  // levels this small run in one block
+constexpr int kDefaultLocalN = 31;  // levels this small run in one block
 constexpr int kDefaultNu1 = 2, kDefaultNu2 = 2;  // V(2,2)
 constexpr double kDefaultOmega = 1.3;
 constexpr long long kBarrierLimit = 4000000000LL;  // clock cycles, ~2 s
 
 // Per-node coefficients of one axis: D2 (at i-1, i, i+1), D1 (same), c.
+template <typename T>
 struct AxisCoef {
-    double d2[3];
-    double d1[3];
-    double c;
-    double pad;
+    T d2[3];
+    T d1[3];
+    T c;
+    T pad;
 };
 
-struct NuLevel {
+// One level of a hierarchy in precision T.
+template <typename T>
+struct Level {
     int n;
-    const AxisCoef *ax, *ay;  // n each
-    const double *pwx, *pwy;  // prolongation weights (2 per node; even nodes used)
-    const double *rwx, *rwy;  // restriction weights of the next coarser level (3 per coarse node)
-    double *u, *f, *r;        // kMaxRhs * n * n (level 0: u is the caller's buffer)
-    double *m, *idiag;        // n * n
+    const AxisCoef<T> *ax, *ay;  // n each
+    const T *pwx, *pwy;          // prolongation weights (2 per node; even nodes used)
+    const T *rwx, *rwy;          // restriction weights to the next coarser level (3 per coarse node)
+    T *u, *f, *r;                // kMaxRhs * n * n
+    T *m, *idiag;                // n * n (m: nullptr when M = 0)
 };
 
 struct NuScalars {
@@ -79,7 +90,13 @@ struct NuScalars {
 };
 
 struct NuArgs {
-    NuLevel lv[kMaxLevels];
+    // The float64 finest level: the caller's u and M, J' and float64
+    // coefficients.  The FP64 form cycles on h64 (whose level 0 is `top`
+    // with residual and diagonal arrays); the refined form keeps `top` for
+    // the residual and the update and cycles on h32.
+    Level<double> top;
+    Level<double> h64[kMaxLevels];
+    Level<float> h32[kMaxLevels];
     int levels;
     int nrhs;
     int has_m;
@@ -90,9 +107,17 @@ struct NuArgs {
     double tol;
     const double *j;          // caller's sources (solve) / input (apply, source)
     const double *m_in;       // caller's M or nullptr
-    double *coarse_inv;       // 81 doubles: inverse of the 3 x 3 level's matrix
+    double *coarse_inv;       // 81 entries (double or float): inverse of the 3 x 3 level
     NuScalars *sc;
 };
+
+template <typename T> __device__ __forceinline__ const Level<T> *hier(const NuArgs &A);
+template <> __device__ __forceinline__ const Level<double> *hier<double>(const NuArgs &A) {
+    return A.h64;
+}
+template <> __device__ __forceinline__ const Level<float> *hier<float>(const NuArgs &A) {
+    return A.h32;
+}
 
 __device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
 __device__ __forceinline__ double vload(const double *p) { return *(const volatile double *)p; }
@@ -141,30 +166,38 @@ struct GridBarrier {
     }
 };
 
+struct BlockSync {
+    __device__ bool operator()(int) const {
+        __syncthreads();
+        return true;
+    }
+};
+
 // Threads taking part in a phase: the whole grid, or block 0 alone.
 struct Team {
     int t, nt;
 };
 
-__device__ __forceinline__ double at(const double *u, int n, int i, int j) {
-    return (i < 0 || j < 0 || i >= n || j >= n) ? 0.0 : u[j * n + i];
+template <typename T>
+__device__ __forceinline__ T at(const T *u, int n, int i, int j) {
+    return (i < 0 || j < 0 || i >= n || j >= n) ? T(0) : u[j * n + i];
 }
 
 // (A u)(i, j) of one field; mrow/mcol are M at (i+a, j) and (i, j+b).
-template <bool CORR>
-__device__ __forceinline__ double apply_point(const AxisCoef &cx, const AxisCoef &cy,
-                                              const double (&v)[3][3], const double (&mrow)[3],
-                                              const double (&mcol)[3], double m0) {
-    double lx[3], ly[3];
+template <bool CORR, typename T>
+__device__ __forceinline__ T apply_point(const AxisCoef<T> &cx, const AxisCoef<T> &cy,
+                                         const T (&v)[3][3], const T (&mrow)[3],
+                                         const T (&mcol)[3], T m0) {
+    T lx[3], ly[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
         lx[b] = cx.d2[0] * v[b][0] + cx.d2[1] * v[b][1] + cx.d2[2] * v[b][2];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         ly[a] = cy.d2[0] * v[0][a] + cy.d2[1] * v[1][a] + cy.d2[2] * v[2][a];
-    double s = lx[1] + ly[1] + m0 * v[1][1];
+    T s = lx[1] + ly[1] + m0 * v[1][1];
     if (CORR) {
-        double tx = 0.0, ty = 0.0;
+        T tx = T(0), ty = T(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) tx += cx.d1[a] * (ly[a] + mrow[a] * v[1][a]);
 #pragma unroll
@@ -174,8 +207,9 @@ __device__ __forceinline__ double apply_point(const AxisCoef &cx, const AxisCoef
     return s;
 }
 
-__device__ __forceinline__ void load_m(const double *m, int n, int i, int j, double (&mrow)[3],
-                                       double (&mcol)[3], double &m0) {
+template <typename T>
+__device__ __forceinline__ void load_m(const T *m, int n, int i, int j, T (&mrow)[3],
+                                       T (&mcol)[3], T &m0) {
     if (m) {
         m0 = m[j * n + i];
         mrow[0] = at(m, n, i - 1, j);
@@ -185,13 +219,14 @@ __device__ __forceinline__ void load_m(const double *m, int n, int i, int j, dou
         mcol[1] = m0;
         mcol[2] = at(m, n, i, j + 1);
     } else {
-        m0 = 0.0;
+        m0 = T(0);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) mrow[k] = mcol[k] = 0.0;
+        for (int k = 0; k < 3; ++k) mrow[k] = mcol[k] = T(0);
     }
 }
 
-__device__ __forceinline__ void load_v(const double *u, int n, int i, int j, double (&v)[3][3]) {
+template <typename T>
+__device__ __forceinline__ void load_v(const T *u, int n, int i, int j, T (&v)[3][3]) {
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
@@ -199,39 +234,56 @@ __device__ __forceinline__ void load_v(const double *u, int n, int i, int j, dou
 }
 
 // Diagonal of A at (i, j): the coefficient of u(i, j) in apply_point.
-template <bool CORR>
-__device__ __forceinline__ double diag_point(const AxisCoef &cx, const AxisCoef &cy, double m0) {
-    double d = cx.d2[1] + cy.d2[1] + m0;
+template <bool CORR, typename T>
+__device__ __forceinline__ T diag_point(const AxisCoef<T> &cx, const AxisCoef<T> &cy, T m0) {
+    T d = cx.d2[1] + cy.d2[1] + m0;
     if (CORR) d += cx.c * cx.d1[1] * (cy.d2[1] + m0) + cy.c * cy.d1[1] * (cx.d2[1] + m0);
     return d;
 }
 
-// One colour of Gauss-Seidel on all fields: points with (i & 1, j & 1) = (ci, cj).
+// J' = J + (cx D1x + cy D1y) J at (i, j) of one field.
 template <bool CORR>
-__device__ void gs_colour(const NuLevel &L, int nrhs, int ci, int cj, Team tm) {
+__device__ __forceinline__ double corrected_source(const Level<double> &L, const double *jc,
+                                                   int i, int j) {
+    const int n = L.n;
+    double fv = jc[j * n + i];
+    if (CORR) {
+        const AxisCoef<double> &cx = L.ax[i], &cy = L.ay[j];
+        const double dx =
+            cx.d1[0] * at(jc, n, i - 1, j) + cx.d1[1] * fv + cx.d1[2] * at(jc, n, i + 1, j);
+        const double dy =
+            cy.d1[0] * at(jc, n, i, j - 1) + cy.d1[1] * fv + cy.d1[2] * at(jc, n, i, j + 1);
+        fv += cx.c * dx + cy.c * dy;
+    }
+    return fv;
+}
+
+// One colour of Gauss-Seidel on all fields: points with (i & 1, j & 1) = (ci, cj).
+template <bool CORR, typename T>
+__device__ void gs_colour(const Level<T> &L, int nrhs, int ci, int cj, Team tm) {
     const int n = L.n;
     const int ni = (n - ci + 1) / 2, nj = (n - cj + 1) / 2;
     const int cnt = ni * nj;
     for (int p = tm.t; p < cnt; p += tm.nt) {
         const int jj = p / ni;
         const int i = 2 * (p - jj * ni) + ci, j = 2 * jj + cj;
-        const AxisCoef &cx = L.ax[i], &cy = L.ay[j];
-        double mrow[3], mcol[3], m0;
+        const AxisCoef<T> &cx = L.ax[i], &cy = L.ay[j];
+        T mrow[3], mcol[3], m0;
         load_m(L.m, n, i, j, mrow, mcol, m0);
-        const double id = L.idiag[j * n + i];
+        const T id = L.idiag[j * n + i];
         for (int c = 0; c < nrhs; ++c) {
-            double *u = L.u + (size_t)c * n * n;
-            double v[3][3];
+            T *u = L.u + (size_t)c * n * n;
+            T v[3][3];
             load_v(u, n, i, j, v);
-            const double res = L.f[(size_t)c * n * n + j * n + i] -
-                               apply_point<CORR>(cx, cy, v, mrow, mcol, m0);
+            const T res = L.f[(size_t)c * n * n + j * n + i] -
+                          apply_point<CORR>(cx, cy, v, mrow, mcol, m0);
             u[j * n + i] = v[1][1] + res * id;
         }
     }
 }
 
-template <bool CORR, typename Sync>
-__device__ bool smooth(const NuLevel &L, int nrhs, int sweeps, Team tm, const Sync &sync,
+template <bool CORR, typename T, typename Sync>
+__device__ bool smooth(const Level<T> &L, int nrhs, int sweeps, Team tm, const Sync &sync,
                        int where) {
     for (int s = 0; s < sweeps; ++s)
         for (int col = 0; col < 4; ++col) {
@@ -241,58 +293,58 @@ __device__ bool smooth(const NuLevel &L, int nrhs, int sweeps, Team tm, const Sy
     return true;
 }
 
-// r = f - A u on a level; optionally accumulates |r|^2 per field into acc.
-template <bool CORR>
-__device__ void residual(const NuLevel &L, int nrhs, Team tm, double *acc) {
+// r = f - A u on a level.
+template <bool CORR, typename T>
+__device__ void residual(const Level<T> &L, int nrhs, Team tm) {
     const int n = L.n;
     for (int p = tm.t; p < n * n; p += tm.nt) {
         const int j = p / n, i = p - j * n;
-        double mrow[3], mcol[3], m0;
+        T mrow[3], mcol[3], m0;
         load_m(L.m, n, i, j, mrow, mcol, m0);
         for (int c = 0; c < nrhs; ++c) {
-            double v[3][3];
+            T v[3][3];
             load_v(L.u + (size_t)c * n * n, n, i, j, v);
-            const double r = L.f[(size_t)c * n * n + p] -
-                             apply_point<CORR>(L.ax[i], L.ay[j], v, mrow, mcol, m0);
-            L.r[(size_t)c * n * n + p] = r;
-            if (acc) acc[c] += r * r;
+            L.r[(size_t)c * n * n + p] = L.f[(size_t)c * n * n + p] -
+                                         apply_point<CORR>(L.ax[i], L.ay[j], v, mrow, mcol, m0);
         }
     }
 }
 
-// Coarse f = R r (dual-volume-weighted full weighting), coarse u = 0.
-__device__ void restrict_residual(const NuLevel &F, const NuLevel &C, int nrhs, Team tm) {
+// Coarse f = R r (dual-length-weighted full weighting), coarse u = 0.
+template <typename T>
+__device__ void restrict_residual(const Level<T> &F, const Level<T> &C, int nrhs, Team tm) {
     const int nc = C.n, nf = F.n;
     for (int p = tm.t; p < nc * nc; p += tm.nt) {
         const int J = p / nc, I = p - J * nc;
         const int i = 2 * I + 1, j = 2 * J + 1;
-        const double *wx = F.rwx + 3 * I, *wy = F.rwy + 3 * J;
+        const T *wx = F.rwx + 3 * I, *wy = F.rwy + 3 * J;
         for (int c = 0; c < nrhs; ++c) {
-            const double *r = F.r + (size_t)c * nf * nf;
-            double s = 0.0;
+            const T *r = F.r + (size_t)c * nf * nf;
+            T s = T(0);
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                const double *row = r + (size_t)(j + b - 1) * nf + i - 1;
+                const T *row = r + (size_t)(j + b - 1) * nf + i - 1;
                 s += wy[b] * (wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2]);
             }
             C.f[(size_t)c * nc * nc + p] = s;
-            C.u[(size_t)c * nc * nc + p] = 0.0;
+            C.u[(size_t)c * nc * nc + p] = T(0);
         }
     }
 }
 
 // Fine u += P (coarse u): bilinear interpolation in physical coordinates.
-__device__ void prolong_correct(const NuLevel &F, const NuLevel &C, int nrhs, Team tm) {
+template <typename T>
+__device__ void prolong_correct(const Level<T> &F, const Level<T> &C, int nrhs, Team tm) {
     const int nf = F.n, nc = C.n;
     for (int p = tm.t; p < nf * nf; p += tm.nt) {
         const int j = p / nf, i = p - j * nf;
-        // x: odd i is coarse node (i-1)/2; even i lies between (i-2)/2 and i/2
+        // odd i is coarse node (i-1)/2; even i lies between (i-2)/2 and i/2
         int ix0, ix1, iy0, iy1;
-        double wx0, wx1, wy0, wy1;
+        T wx0, wx1, wy0, wy1;
         if (i & 1) {
             ix0 = ix1 = (i - 1) / 2;
-            wx0 = 1.0;
-            wx1 = 0.0;
+            wx0 = T(1);
+            wx1 = T(0);
         } else {
             ix0 = (i - 2) / 2;
             ix1 = i / 2;
@@ -301,8 +353,8 @@ __device__ void prolong_correct(const NuLevel &F, const NuLevel &C, int nrhs, Te
         }
         if (j & 1) {
             iy0 = iy1 = (j - 1) / 2;
-            wy0 = 1.0;
-            wy1 = 0.0;
+            wy0 = T(1);
+            wy1 = T(0);
         } else {
             iy0 = (j - 2) / 2;
             iy1 = j / 2;
@@ -310,65 +362,61 @@ __device__ void prolong_correct(const NuLevel &F, const NuLevel &C, int nrhs, Te
             wy1 = F.pwy[2 * j + 1];
         }
         for (int c = 0; c < nrhs; ++c) {
-            const double *e = C.u + (size_t)c * nc * nc;
-            const double v = wy0 * (wx0 * at(e, nc, ix0, iy0) + wx1 * at(e, nc, ix1, iy0)) +
-                             wy1 * (wx0 * at(e, nc, ix0, iy1) + wx1 * at(e, nc, ix1, iy1));
+            const T *e = C.u + (size_t)c * nc * nc;
+            const T v = wy0 * (wx0 * at(e, nc, ix0, iy0) + wx1 * at(e, nc, ix1, iy0)) +
+                        wy1 * (wx0 * at(e, nc, ix0, iy1) + wx1 * at(e, nc, ix1, iy1));
             F.u[(size_t)c * nf * nf + p] += v;
         }
     }
 }
 
-// M on the next coarser level (same weights as the residual) and 1/diag.
-template <bool CORR>
-__device__ void level_setup(const NuArgs &A, int l, Team tm) {
-    const NuLevel &L = A.lv[l];
-    const int n = L.n;
-    if (l > 0 && A.has_m) {
-        const NuLevel &F = A.lv[l - 1];
-        const int nf = F.n;
-        for (int p = tm.t; p < n * n; p += tm.nt) {
-            const int J = p / n, I = p - J * n;
-            const int i = 2 * I + 1, j = 2 * J + 1;
-            const double *wx = F.rwx + 3 * I, *wy = F.rwy + 3 * J;
-            double s = 0.0;
-            for (int b = 0; b < 3; ++b) {
-                const double *row = F.m + (size_t)(j + b - 1) * nf + i - 1;
-                s += wy[b] * (wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2]);
-            }
-            L.m[p] = s;
+// M of level l from level l - 1 (same weights as the residual).
+template <typename T>
+__device__ void restrict_m(const Level<T> &F, const Level<T> &L, Team tm) {
+    const int n = L.n, nf = F.n;
+    for (int p = tm.t; p < n * n; p += tm.nt) {
+        const int J = p / n, I = p - J * n;
+        const int i = 2 * I + 1, j = 2 * J + 1;
+        const T *wx = F.rwx + 3 * I, *wy = F.rwy + 3 * J;
+        T s = T(0);
+        for (int b = 0; b < 3; ++b) {
+            const T *row = F.m + (size_t)(j + b - 1) * nf + i - 1;
+            s += wy[b] * (wx[0] * row[0] + wx[1] * row[1] + wx[2] * row[2]);
         }
+        L.m[p] = s;
     }
 }
 
 // omega / diag(A): the Gauss-Seidel update is u += omega (f - A u) / diag.
-template <bool CORR>
-__device__ void level_idiag(const NuLevel &L, double omega, Team tm) {
+template <bool CORR, typename T>
+__device__ void level_idiag(const Level<T> &L, double omega, Team tm) {
     const int n = L.n;
     for (int p = tm.t; p < n * n; p += tm.nt) {
         const int j = p / n, i = p - j * n;
-        const double m0 = L.m ? L.m[p] : 0.0;
-        L.idiag[p] = omega / diag_point<CORR>(L.ax[i], L.ay[j], m0);
+        const T m0 = L.m ? L.m[p] : T(0);
+        L.idiag[p] = T(omega / (double)diag_point<CORR>(L.ax[i], L.ay[j], m0));
     }
 }
 
 // Inverse of the 3 x 3 level's 9 x 9 matrix by Gauss-Jordan with partial
-// pivoting (one thread; the columns are A applied to unit vectors).
-template <bool CORR>
-__device__ void coarse_inverse(const NuLevel &L, double *inv) {
+// pivoting, in double (one thread; the columns are A applied to unit vectors).
+template <bool CORR, typename T>
+__device__ void coarse_inverse(const Level<T> &L, T *inv) {
     double a[9][18];
     for (int q = 0; q < 9; ++q) {
         const int j = q / 3, i = q - 3 * j;
-        double mrow[3], mcol[3], m0;
+        T mrow[3], mcol[3], m0;
         load_m(L.m, 3, i, j, mrow, mcol, m0);
         for (int col = 0; col < 9; ++col) {
-            double v[3][3];
+            T v[3][3];
             for (int b = 0; b < 3; ++b)
                 for (int aa = 0; aa < 3; ++aa) {
                     const int ii = i + aa - 1, jj = j + b - 1;
-                    v[b][aa] = (ii >= 0 && jj >= 0 && ii < 3 && jj < 3 && jj * 3 + ii == col) ? 1.0
-                                                                                           : 0.0;
+                    v[b][aa] = (ii >= 0 && jj >= 0 && ii < 3 && jj < 3 && jj * 3 + ii == col)
+                                   ? T(1)
+                                   : T(0);
                 }
-            a[q][col] = apply_point<CORR>(L.ax[i], L.ay[j], v, mrow, mcol, m0);
+            a[q][col] = (double)apply_point<CORR>(L.ax[i], L.ay[j], v, mrow, mcol, m0);
             a[q][9 + col] = (q == col) ? 1.0 : 0.0;
         }
     }
@@ -392,27 +440,21 @@ __device__ void coarse_inverse(const NuLevel &L, double *inv) {
         }
     }
     for (int q = 0; q < 9; ++q)
-        for (int col = 0; col < 9; ++col) inv[q * 9 + col] = a[q][9 + col];
+        for (int col = 0; col < 9; ++col) inv[q * 9 + col] = T(a[q][9 + col]);
 }
 
-__device__ void coarse_solve(const NuLevel &L, const double *inv, int nrhs, Team tm) {
+template <typename T>
+__device__ void coarse_solve(const Level<T> &L, const T *inv, int nrhs, Team tm) {
     for (int p = tm.t; p < 9 * nrhs; p += tm.nt) {
         const int c = p / 9, q = p - 9 * c;
-        const double *f = L.f + 9 * c;
-        double s = 0.0;
+        const T *f = L.f + 9 * c;
+        T s = T(0);
         for (int k = 0; k < 9; ++k) s += inv[q * 9 + k] * f[k];
         L.u[9 * c + q] = s;
     }
 }
 
-struct BlockSync {
-    __device__ bool operator()(int) const {
-        __syncthreads();
-        return true;
-    }
-};
-
-__device__ void block_reduce_add(double *vals, int nrhs, double *dst) {
+__device__ void block_reduce_add(const double *vals, int nrhs, double *dst) {
     __shared__ double red[kThreads / 32][kMaxRhs];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = 0; c < nrhs; ++c) {
@@ -430,33 +472,62 @@ __device__ void block_reduce_add(double *vals, int nrhs, double *dst) {
     __syncthreads();
 }
 
-// Descends from level `from` to the coarsest and back up (team `tm`, `sync`).
-template <bool CORR, typename Sync>
-__device__ bool vcycle_part(const NuArgs &A, int from, int to, Team tm, const Sync &sync) {
-    const int nr = A.nrhs;
+// Levels from..to-1: pre-smooth, residual, restrict (team `tm`, `sync`).
+template <bool CORR, typename T, typename Sync>
+__device__ bool down_legs(const Level<T> *H, int nr, int nu1, int from, int to, Team tm,
+                          const Sync &sync) {
     for (int l = from; l < to; ++l) {
-        if (!smooth<CORR>(A.lv[l], nr, A.nu1, tm, sync, 10 + l)) return false;
-        residual<CORR>(A.lv[l], nr, tm, nullptr);
+        if (!smooth<CORR>(H[l], nr, nu1, tm, sync, 10 + l)) return false;
+        residual<CORR>(H[l], nr, tm);
         if (!sync(30 + l)) return false;
-        restrict_residual(A.lv[l], A.lv[l + 1], nr, tm);
+        restrict_residual(H[l], H[l + 1], nr, tm);
         if (!sync(50 + l)) return false;
     }
     return true;
 }
 
-template <bool CORR, typename Sync>
-__device__ bool upcycle_part(const NuArgs &A, int from, int to, Team tm, const Sync &sync) {
-    const int nr = A.nrhs;
+// Levels from down to `to`: prolongate-correct, post-smooth.
+template <bool CORR, typename T, typename Sync>
+__device__ bool up_legs(const Level<T> *H, int nr, int nu2, int from, int to, Team tm,
+                        const Sync &sync) {
     for (int l = from; l >= to; --l) {
-        prolong_correct(A.lv[l], A.lv[l + 1], nr, tm);
+        prolong_correct(H[l], H[l + 1], nr, tm);
         if (!sync(70 + l)) return false;
-        if (!smooth<CORR>(A.lv[l], nr, A.nu2, tm, sync, 90 + l)) return false;
+        if (!smooth<CORR>(H[l], nr, nu2, tm, sync, 90 + l)) return false;
     }
     return true;
 }
 
-template <bool CORR>
+// One V-cycle on hierarchy H: the grid-wide levels 0..loc-1, then block 0
+// alone from loc to the exact coarsest solve and back.
+template <bool CORR, typename T>
+__device__ bool vcycle(const NuArgs &A, const Level<T> *H, int loc, Team grid, Team blk,
+                       const GridBarrier &gsync) {
+    const int nr = A.nrhs, Lc = A.levels - 1;
+    const T *inv = reinterpret_cast<const T *>(A.coarse_inv);
+    if (Lc == 0) {
+        if (blockIdx.x == 0) coarse_solve(H[0], inv, nr, blk);
+        return gsync(3);
+    }
+    if (!down_legs<CORR>(H, nr, A.nu1, 0, loc, grid, gsync)) return false;
+    if (blockIdx.x == 0) {
+        const BlockSync bs;
+        down_legs<CORR>(H, nr, A.nu1, loc, Lc, blk, bs);
+        coarse_solve(H[Lc], inv, nr, blk);
+        __syncthreads();
+        up_legs<CORR>(H, nr, A.nu2, Lc - 1, loc, blk, bs);
+    }
+    if (!gsync(3)) return false;
+    return loc == 0 || up_legs<CORR>(H, nr, A.nu2, loc - 1, 0, grid, gsync);
+}
+
+// FP64 form (T = double): every cycle in float64 on h64.
+// Refined form (T = float): the float64 residual of `top` drives float32
+// V-cycles on h32 for the correction, added to the float64 solution
+// (iterative refinement; the stopping test is on the float64 residual).
+template <bool CORR, typename T>
 __global__ void __launch_bounds__(kThreads, 1) nu_solve_kernel(const __grid_constant__ NuArgs P) {
+    constexpr bool REF = sizeof(T) == 4;
     __shared__ NuArgs A;
     __shared__ unsigned long long epoch;
     if (threadIdx.x == 0) {
@@ -468,49 +539,50 @@ __global__ void __launch_bounds__(kThreads, 1) nu_solve_kernel(const __grid_cons
     const Team grid{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x)};
     const Team blk{(int)threadIdx.x, (int)blockDim.x};
     NuScalars *sc = A.sc;
-    const int nr = A.nrhs, Lc = A.levels - 1;
+    const Level<T> *H = hier<T>(A);
+    const Level<double> &top = A.top;
+    const int nr = A.nrhs, Lc = A.levels - 1, n = top.n;
     // first level handled by block 0 alone
     int loc = 0;
-    while (loc < Lc && A.lv[loc].n > A.local_n) ++loc;
+    while (loc < Lc && H[loc].n > A.local_n) ++loc;
 
     // setup: M hierarchy and inverse diagonals (each level by the team that
-    // smooths it), then J' and the initial residual
-    level_idiag<CORR>(A.lv[0], A.omega, grid);
+    // smooths it)
+    if (REF && A.has_m) {
+        for (int p = grid.t; p < n * n; p += grid.nt) H[0].m[p] = T(A.m_in[p]);
+        if (!gsync(1)) return;
+    }
+    level_idiag<CORR>(H[0], A.omega, grid);
     for (int l = 1; l <= Lc; ++l) {
         if (l <= loc) {
-            level_setup<CORR>(A, l, grid);
+            if (A.has_m) restrict_m(H[l - 1], H[l], grid);
             if (!gsync(1)) return;
-            level_idiag<CORR>(A.lv[l], A.omega, grid);
+            level_idiag<CORR>(H[l], A.omega, grid);
         } else if (blockIdx.x == 0) {
-            level_setup<CORR>(A, l, blk);
+            if (A.has_m) restrict_m(H[l - 1], H[l], blk);
             __syncthreads();
-            level_idiag<CORR>(A.lv[l], A.omega, blk);
+            level_idiag<CORR>(H[l], A.omega, blk);
             __syncthreads();
         }
     }
+    // J' and the initial float64 residual (the refined form hands it to h32
+    // as the right-hand side of the first correction, from zero)
     {
-        const NuLevel &L = A.lv[0];
-        const int n = L.n;
         double fn[kMaxRhs] = {0, 0, 0, 0}, rn[kMaxRhs] = {0, 0, 0, 0};
         for (int p = grid.t; p < n * n; p += grid.nt) {
             const int j = p / n, i = p - j * n;
             double mrow[3], mcol[3], m0;
-            load_m(L.m, n, i, j, mrow, mcol, m0);
+            load_m(A.m_in, n, i, j, mrow, mcol, m0);
             for (int c = 0; c < nr; ++c) {
-                const double *jc = A.j + (size_t)c * n * n;
-                double fv = jc[p];
-                if (CORR) {
-                    const AxisCoef &cx = L.ax[i], &cy = L.ay[j];
-                    const double dx = cx.d1[0] * at(jc, n, i - 1, j) + cx.d1[1] * fv +
-                                      cx.d1[2] * at(jc, n, i + 1, j);
-                    const double dy = cy.d1[0] * at(jc, n, i, j - 1) + cy.d1[1] * fv +
-                                      cy.d1[2] * at(jc, n, i, j + 1);
-                    fv += cx.c * dx + cy.c * dy;
-                }
-                L.f[(size_t)c * n * n + p] = fv;
+                const double fv = corrected_source<CORR>(top, A.j + (size_t)c * n * n, i, j);
+                top.f[(size_t)c * n * n + p] = fv;
                 double v[3][3];
-                load_v(L.u + (size_t)c * n * n, n, i, j, v);
-                const double r = fv - apply_point<CORR>(L.ax[i], L.ay[j], v, mrow, mcol, m0);
+                load_v(top.u + (size_t)c * n * n, n, i, j, v);
+                const double r = fv - apply_point<CORR>(top.ax[i], top.ay[j], v, mrow, mcol, m0);
+                if (REF) {
+                    H[0].f[(size_t)c * n * n + p] = T(r);
+                    H[0].u[(size_t)c * n * n + p] = T(0);
+                }
                 fn[c] += fv * fv;
                 rn[c] += r * r;
             }
@@ -518,13 +590,15 @@ __global__ void __launch_bounds__(kThreads, 1) nu_solve_kernel(const __grid_cons
         block_reduce_add(fn, nr, sc->fnorm);
         block_reduce_add(rn, nr, sc->norm[0]);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) coarse_inverse<CORR>(A.lv[Lc], A.coarse_inv);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        coarse_inverse<CORR>(H[Lc], reinterpret_cast<T *>(A.coarse_inv));
     if (!gsync(2)) return;
 
     double fn2[kMaxRhs];
     for (int c = 0; c < nr; ++c) fn2[c] = vload(&sc->fnorm[c]);
     for (int cyc = 0;; ++cyc) {
-        // convergence test on the residual left by the previous cycle (slot cyc % 3)
+        // convergence test on the float64 residual left by the previous
+        // cycle (slot cyc % 3)
         bool conv = true;
         for (int c = 0; c < nr; ++c) {
             const double rn = vload(&sc->norm[cyc % 3][c]);
@@ -539,64 +613,60 @@ __global__ void __launch_bounds__(kThreads, 1) nu_solve_kernel(const __grid_cons
                         fn2[c] > 0.0 ? sqrt(vload(&sc->norm[cyc % 3][c]) / fn2[c]) : 0.0;
             }
             // a field whose source is zero has the solution zero
-            const int n = A.lv[0].n;
             for (int c = 0; c < nr; ++c)
                 if (fn2[c] == 0.0)
                     for (int p = grid.t; p < n * n; p += grid.nt)
-                        A.lv[0].u[(size_t)c * n * n + p] = 0.0;
+                        top.u[(size_t)c * n * n + p] = 0.0;
             break;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0)
             for (int c = 0; c < kMaxRhs; ++c) sc->norm[(cyc + 1) % 3][c] = 0.0;
-        if (Lc == 0) {
-            if (blockIdx.x == 0) coarse_solve(A.lv[0], A.coarse_inv, nr, blk);
-            if (!gsync(3)) return;
-        } else {
-            if (!vcycle_part<CORR>(A, 0, loc, grid, gsync)) return;
-            if (blockIdx.x == 0) {
-                const BlockSync bs;
-                vcycle_part<CORR>(A, loc, Lc, blk, bs);
-                coarse_solve(A.lv[Lc], A.coarse_inv, nr, blk);
-                __syncthreads();
-                upcycle_part<CORR>(A, Lc - 1, loc, blk, bs);
+        if (!vcycle<CORR>(A, H, loc, grid, blk, gsync)) return;
+        if (REF) {
+            // u += e (float64), then the new float64 residual
+            for (int p = grid.t; p < n * n; p += grid.nt)
+                for (int c = 0; c < nr; ++c)
+                    top.u[(size_t)c * n * n + p] += (double)H[0].u[(size_t)c * n * n + p];
+            if (!gsync(5)) return;
+        }
+        double rn[kMaxRhs] = {0, 0, 0, 0};
+        for (int p = grid.t; p < n * n; p += grid.nt) {
+            const int j = p / n, i = p - j * n;
+            double mrow[3], mcol[3], m0;
+            load_m(A.m_in, n, i, j, mrow, mcol, m0);
+            for (int c = 0; c < nr; ++c) {
+                double v[3][3];
+                load_v(top.u + (size_t)c * n * n, n, i, j, v);
+                const double r = top.f[(size_t)c * n * n + p] -
+                                 apply_point<CORR>(top.ax[i], top.ay[j], v, mrow, mcol, m0);
+                if (REF) {
+                    H[0].f[(size_t)c * n * n + p] = T(r);
+                    H[0].u[(size_t)c * n * n + p] = T(0);
+                }
+                rn[c] += r * r;
             }
-            if (!gsync(3)) return;
-            if (loc > 0 && !upcycle_part<CORR>(A, loc - 1, 0, grid, gsync)) return;
         }
-        // residual of the finest level for the next test
-        {
-            double rn[kMaxRhs] = {0, 0, 0, 0};
-            residual<CORR>(A.lv[0], nr, grid, rn);
-            block_reduce_add(rn, nr, sc->norm[(cyc + 1) % 3]);
-        }
+        block_reduce_add(rn, nr, sc->norm[(cyc + 1) % 3]);
         if (!gsync(4)) return;
     }
 }
 
-// Operator and corrected source of level 0 for one field (tests, diagnostics).
+// Operator and corrected source of the finest level for one field (tests,
+// diagnostics), in float64.
 template <bool CORR>
 __global__ void nu_apply_kernel(const __grid_constant__ NuArgs A, const double *u, double *out,
                                 int source) {
-    const NuLevel &L = A.lv[0];
+    const Level<double> &L = A.top;
     const int n = L.n;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n * n; p += gridDim.x * blockDim.x) {
         const int j = p / n, i = p - j * n;
-        const AxisCoef &cx = L.ax[i], &cy = L.ay[j];
         if (source) {
-            double fv = u[p];
-            if (CORR) {
-                const double dx = cx.d1[0] * at(u, n, i - 1, j) + cx.d1[1] * fv +
-                                  cx.d1[2] * at(u, n, i + 1, j);
-                const double dy = cy.d1[0] * at(u, n, i, j - 1) + cy.d1[1] * fv +
-                                  cy.d1[2] * at(u, n, i, j + 1);
-                fv += cx.c * dx + cy.c * dy;
-            }
-            out[p] = fv;
+            out[p] = corrected_source<CORR>(L, u, i, j);
         } else {
             double mrow[3], mcol[3], m0, v[3][3];
             load_m(A.m_in, n, i, j, mrow, mcol, m0);
             load_v(u, n, i, j, v);
-            out[p] = apply_point<CORR>(cx, cy, v, mrow, mcol, m0);
+            out[p] = apply_point<CORR>(L.ax[i], L.ay[j], v, mrow, mcol, m0);
         }
     }
 }
@@ -607,7 +677,7 @@ __global__ void nu_apply_kernel(const __grid_constant__ NuArgs A, const double *
 // Host side
 // ---------------------------------------------------------------------------
 struct qs_nu_solver {
-    int n = 0, levels = 0, correction = 0;
+    int n = 0, levels = 0, correction = 0, precision = QS_FP64;
     cudaStream_t stream = nullptr;
     int grid_blocks = 0;
     NuArgs args{};
@@ -617,12 +687,13 @@ struct qs_nu_solver {
 
 namespace {
 
-void axis_coefficients(const std::vector<double> &x, int correction, std::vector<AxisCoef> &out) {
+void axis_coefficients(const std::vector<double> &x, int correction,
+                       std::vector<AxisCoef<double>> &out) {
     const int n = (int)x.size() - 2;
     out.resize(n);
     for (int i = 0; i < n; ++i) {
         const double hm = x[i + 1] - x[i], hp = x[i + 2] - x[i + 1], ha = hm + hp;
-        AxisCoef c{};
+        AxisCoef<double> c{};
         c.d2[0] = 2.0 / (hm * ha);
         c.d2[1] = -2.0 / (hm * hp);
         c.d2[2] = 2.0 / (hp * ha);
@@ -687,13 +758,100 @@ int cuda_status(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? QS_ERR_OOM : QS_ERR_CUDA;
 }
 
+struct HostLevel {
+    int n;
+    std::vector<AxisCoef<double>> ax, ay;
+    std::vector<double> pwx, pwy, rwx, rwy;
+};
+
+// Carves one device allocation into arrays and fills a host image of it.
+struct Arena {
+    char *base = nullptr;
+    size_t off = 0;
+    std::vector<char> *image = nullptr;  // null while sizing
+    static size_t align(size_t b) { return (b + 255) & ~(size_t)255; }
+    template <typename T>
+    T *take(size_t count) {
+        T *p = reinterpret_cast<T *>(base + off);
+        off += align(count * sizeof(T));
+        return p;
+    }
+    template <typename T, typename S>
+    const T *put(const std::vector<S> &src) {
+        T *p = take<T>(src.size());
+        if (image)
+            for (size_t k = 0; k < src.size(); ++k)
+                reinterpret_cast<T *>(image->data() + (reinterpret_cast<char *>(p) - base))[k] =
+                    static_cast<T>(src[k]);
+        return p;
+    }
+    template <typename T>
+    const AxisCoef<T> *put_axis(const std::vector<AxisCoef<double>> &src) {
+        AxisCoef<T> *p = take<AxisCoef<T>>(src.size());
+        if (image)
+            for (size_t k = 0; k < src.size(); ++k) {
+                AxisCoef<T> c{};
+                for (int q = 0; q < 3; ++q) {
+                    c.d2[q] = static_cast<T>(src[k].d2[q]);
+                    c.d1[q] = static_cast<T>(src[k].d1[q]);
+                }
+                c.c = static_cast<T>(src[k].c);
+                std::memcpy(image->data() + (reinterpret_cast<char *>(p) - base) +
+                                k * sizeof(AxisCoef<T>),
+                            &c, sizeof(c));
+            }
+        return p;
+    }
+};
+
+// Lays out a whole hierarchy in precision T (level 0 included).
+template <typename T>
+void lay_hierarchy(Arena &ar, const std::vector<HostLevel> &hl, Level<T> *H) {
+    for (size_t l = 0; l < hl.size(); ++l) {
+        const HostLevel &h = hl[l];
+        const size_t nn = (size_t)h.n * h.n;
+        Level<T> &L = H[l];
+        L.n = h.n;
+        L.ax = ar.put_axis<T>(h.ax);
+        L.ay = ar.put_axis<T>(h.ay);
+        L.pwx = ar.put<T>(h.pwx);
+        L.pwy = ar.put<T>(h.pwy);
+        L.rwx = ar.put<T>(h.rwx);
+        L.rwy = ar.put<T>(h.rwy);
+        L.u = ar.take<T>(kMaxRhs * nn);
+        L.f = ar.take<T>(kMaxRhs * nn);
+        L.r = ar.take<T>(kMaxRhs * nn);
+        L.m = ar.take<T>(nn);
+        L.idiag = ar.take<T>(nn);
+    }
+}
+
+// The float64 finest level of both forms, then the cycling hierarchy.
+void lay_out(Arena &ar, const std::vector<HostLevel> &hl, int precision, NuArgs &A) {
+    A.sc = ar.take<NuScalars>(1);
+    A.coarse_inv = ar.take<double>(81);
+    const size_t nn = (size_t)hl[0].n * hl[0].n;
+    A.top = Level<double>{};
+    A.top.n = hl[0].n;
+    if (precision == QS_FP64) {
+        lay_hierarchy<double>(ar, hl, A.h64);
+        A.top = A.h64[0];
+    } else {
+        A.top.ax = ar.put_axis<double>(hl[0].ax);
+        A.top.ay = ar.put_axis<double>(hl[0].ay);
+        A.top.f = ar.take<double>(kMaxRhs * nn);
+        lay_hierarchy<float>(ar, hl, A.h32);
+    }
+}
+
 }  // namespace
 
 extern "C" int qs_nu_create(int n, const double *x_nodes, const double *y_nodes, int correction,
-                            void *cuda_stream, qs_nu_solver **out) {
+                            int precision, void *cuda_stream, qs_nu_solver **out) {
     if (!out) return QS_ERR_ARG;
     *out = nullptr;
     if (n < 3 || n > 4095 || (correction != 0 && correction != 1)) return QS_ERR_ARG;
+    if (precision != QS_FP64 && precision != QS_FP32_REFINED) return QS_ERR_ARG;
     const int levels = levels_for(n);
     if (levels < 1 || levels > kMaxLevels) return QS_ERR_ARG;
     if (!valid_axis(x_nodes, n) || !valid_axis(y_nodes, n)) return QS_ERR_ARG;
@@ -703,16 +861,11 @@ extern "C" int qs_nu_create(int n, const double *x_nodes, const double *y_nodes,
     s->n = n;
     s->levels = levels;
     s->correction = correction;
+    s->precision = precision;
     s->stream = static_cast<cudaStream_t>(cuda_stream);
 
-    // host tables per level, then one device allocation laid out as
-    // [scalars][coarse inverse][per level: ax, ay, pwx, pwy, rwx, rwy, u, f, r, m, idiag]
+    // host tables per level (coarse nodes: every other node, walls kept)
     std::vector<double> xs(x_nodes, x_nodes + n + 2), ys(y_nodes, y_nodes + n + 2);
-    struct HostLevel {
-        int n;
-        std::vector<AxisCoef> ax, ay;
-        std::vector<double> pwx, pwy, rwx, rwy;
-    };
     std::vector<HostLevel> hl(levels);
     for (int l = 0; l < levels; ++l) {
         HostLevel &h = hl[l];
@@ -731,64 +884,30 @@ extern "C" int qs_nu_create(int n, const double *x_nodes, const double *y_nodes,
             ys.swap(cy);
         }
     }
-    auto align = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    size_t bytes = align(sizeof(NuScalars)) + align(81 * sizeof(double));
-    for (int l = 0; l < levels; ++l) {
-        const size_t nn = (size_t)hl[l].n * hl[l].n;
-        bytes += 2 * align(hl[l].n * sizeof(AxisCoef));
-        bytes += align(hl[l].pwx.size() * 8) + align(hl[l].pwy.size() * 8);
-        bytes += align(hl[l].rwx.size() * 8) + align(hl[l].rwy.size() * 8);
-        bytes += 3 * align(kMaxRhs * nn * 8) + 2 * align(nn * 8);
-    }
+    // size the layout, allocate, lay it out again with a host image
+    NuArgs &A = s->args;
+    Arena sizing;
+    lay_out(sizing, hl, precision, A);
+    const size_t bytes = sizing.off;
     int st = cuda_status(cudaMalloc(&s->dev, bytes));
     if (st == QS_OK) st = cuda_status(cudaMallocHost(&s->pinned, sizeof(NuScalars)));
     if (st != QS_OK) {
         qs_nu_destroy(s);
         return st;
     }
-    char *base = static_cast<char *>(s->dev);
-    size_t off = 0;
-    auto take = [&](size_t b) {
-        void *p = base + off;
-        off += align(b);
-        return p;
-    };
-    std::vector<char> host(bytes, 0);
-    auto put = [&](void *dst, const void *src, size_t b) {
-        if (b) std::memcpy(host.data() + (static_cast<char *>(dst) - base), src, b);
-    };
-    NuArgs &A = s->args;
+    std::vector<char> image(bytes, 0);
+    Arena ar;
+    ar.base = static_cast<char *>(s->dev);
+    ar.image = &image;
+    A = NuArgs{};
+    lay_out(ar, hl, precision, A);
+    A.levels = levels;
     A.nu1 = kDefaultNu1;
     A.nu2 = kDefaultNu2;
     A.omega = kDefaultOmega;
     A.local_n = kDefaultLocalN;
-    A.sc = static_cast<NuScalars *>(take(sizeof(NuScalars)));
-    A.coarse_inv = static_cast<double *>(take(81 * sizeof(double)));
-    A.levels = levels;
-    for (int l = 0; l < levels; ++l) {
-        const HostLevel &h = hl[l];
-        const size_t nn = (size_t)h.n * h.n;
-        NuLevel &L = A.lv[l];
-        L.n = h.n;
-        L.ax = static_cast<AxisCoef *>(take(h.n * sizeof(AxisCoef)));
-        L.ay = static_cast<AxisCoef *>(take(h.n * sizeof(AxisCoef)));
-        put((void *)L.ax, h.ax.data(), h.n * sizeof(AxisCoef));
-        put((void *)L.ay, h.ay.data(), h.n * sizeof(AxisCoef));
-        L.pwx = static_cast<double *>(take(h.pwx.size() * 8));
-        L.pwy = static_cast<double *>(take(h.pwy.size() * 8));
-        put((void *)L.pwx, h.pwx.data(), h.pwx.size() * 8);
-        put((void *)L.pwy, h.pwy.data(), h.pwy.size() * 8);
-        L.rwx = static_cast<double *>(take(h.rwx.size() * 8));
-        L.rwy = static_cast<double *>(take(h.rwy.size() * 8));
-        put((void *)L.rwx, h.rwx.data(), h.rwx.size() * 8);
-        put((void *)L.rwy, h.rwy.data(), h.rwy.size() * 8);
-        L.u = static_cast<double *>(take(kMaxRhs * nn * 8));
-        L.f = static_cast<double *>(take(kMaxRhs * nn * 8));
-        L.r = static_cast<double *>(take(kMaxRhs * nn * 8));
-        L.m = static_cast<double *>(take(nn * 8));
-        L.idiag = static_cast<double *>(take(nn * 8));
-    }
-    st = cuda_status(cudaMemcpyAsync(s->dev, host.data(), bytes, cudaMemcpyHostToDevice, s->stream));
+    st = cuda_status(cudaMemcpyAsync(s->dev, image.data(), bytes, cudaMemcpyHostToDevice,
+                                     s->stream));
     if (st == QS_OK) st = cuda_status(cudaStreamSynchronize(s->stream));
     if (st != QS_OK) {
         qs_nu_destroy(s);
@@ -796,13 +915,17 @@ extern "C" int qs_nu_create(int n, const double *x_nodes, const double *y_nodes,
     }
     // one block per SM (co-resident: the cooperative launch checks it)
     int dev = 0, sms = 0, per_sm = 0;
+    const void *fn = nullptr;
+    if (precision == QS_FP64)
+        fn = correction ? (const void *)nu_solve_kernel<true, double>
+                        : (const void *)nu_solve_kernel<false, double>;
+    else
+        fn = correction ? (const void *)nu_solve_kernel<true, float>
+                        : (const void *)nu_solve_kernel<false, float>;
     st = cuda_status(cudaGetDevice(&dev));
     if (st == QS_OK) st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (st == QS_OK)
-        st = cuda_status(correction ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                          &per_sm, nu_solve_kernel<true>, kThreads, 0)
-                                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                          &per_sm, nu_solve_kernel<false>, kThreads, 0));
+        st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0));
     if (st == QS_OK && per_sm < 1) st = QS_ERR_CUDA;
     if (st != QS_OK) {
         qs_nu_destroy(s);
@@ -824,17 +947,26 @@ extern "C" int qs_nu_solve(qs_nu_solver *s, const double *d_m, int nrhs, const d
     A.tol = tol;
     A.j = d_j;
     A.m_in = d_m;
-    // level 0 works in place on the caller's u and reads the caller's M
-    // (never written); coarser levels hold the restricted M
-    A.lv[0].u = d_u;
-    A.lv[0].m = const_cast<double *>(d_m);
-    for (int l = 1; l < A.levels; ++l)
-        if (!d_m) A.lv[l].m = nullptr;
+    // the float64 finest level works in place on the caller's u and reads the
+    // caller's M (never written); the cycling levels hold their own M
+    A.top.u = d_u;
+    A.top.m = const_cast<double *>(d_m);
+    if (s->precision == QS_FP64) {
+        A.h64[0].u = d_u;
+        A.h64[0].m = A.top.m;
+    }
+    if (!d_m)
+        for (int l = 0; l < A.levels; ++l) A.h64[l].m = nullptr, A.h32[l].m = nullptr;
     int st = cuda_status(cudaMemsetAsync(A.sc, 0, sizeof(NuScalars), s->stream));
     if (st != QS_OK) return st;
     void *params[] = {&A};
-    const void *fn = s->correction ? (const void *)nu_solve_kernel<true>
-                                   : (const void *)nu_solve_kernel<false>;
+    const void *fn = nullptr;
+    if (s->precision == QS_FP64)
+        fn = s->correction ? (const void *)nu_solve_kernel<true, double>
+                           : (const void *)nu_solve_kernel<false, double>;
+    else
+        fn = s->correction ? (const void *)nu_solve_kernel<true, float>
+                           : (const void *)nu_solve_kernel<false, float>;
     st = cuda_status(cudaLaunchCooperativeKernel(fn, dim3(s->grid_blocks), dim3(kThreads), params,
                                                  0, s->stream));
     if (st != QS_OK) return st;

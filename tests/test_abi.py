@@ -79,10 +79,11 @@ def test_nonuniform_solver_arguments_rejected_without_gpu(lib):
     l = qs.load_library()
     h = ctypes.c_void_p()
 
-    def create(n, xn, yn, corr=1):
+    def create(n, xn, yn, corr=1, prec=0):
         xa = np.ascontiguousarray(xn, dtype=np.float64)
         ya = np.ascontiguousarray(yn, dtype=np.float64)
-        return l.qs_nu_create(n, xa.ctypes.data, ya.ctypes.data, corr, None, ctypes.byref(h))
+        return l.qs_nu_create(n, xa.ctypes.data, ya.ctypes.data, corr, prec, None,
+                              ctypes.byref(h))
 
     good = np.linspace(-1.0, 1.0, 17)
     for n in (0, 1, 2, 4, 5, 6, 14, 16, 4096, 8191):
@@ -96,8 +97,9 @@ def test_nonuniform_solver_arguments_rejected_without_gpu(lib):
     nan[3] = float("nan")
     assert create(15, nan, good) == qs.QS_ERR_ARG
     assert create(15, good, good, corr=2) == qs.QS_ERR_ARG
-    assert l.qs_nu_create(15, None, None, 1, None, ctypes.byref(h)) == qs.QS_ERR_ARG
-    assert l.qs_nu_create(15, good.ctypes.data, good.ctypes.data, 1, None, None) == qs.QS_ERR_ARG
+    assert create(15, good, good, prec=2) == qs.QS_ERR_ARG
+    assert l.qs_nu_create(15, None, None, 1, 0, None, ctypes.byref(h)) == qs.QS_ERR_ARG
+    assert l.qs_nu_create(15, good.ctypes.data, good.ctypes.data, 1, 0, None, None) == qs.QS_ERR_ARG
     for args in ((None, None, 1, None, None, 1e-10, 10, None, None),):
         assert l.qs_nu_solve(*args) == qs.QS_ERR_ARG
     l.qs_nu_destroy(None)

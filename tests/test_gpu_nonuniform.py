@@ -60,7 +60,8 @@ def test_operator_and_source_match_oracle(qs, kind, correction, n):
     src = bubble_sources(xn, yn, radius=1.5)
     rng = np.random.default_rng(7)
     u = rng.standard_normal((n, n))
-    s = qs.NonuniformSolver(xn, yn, correction=correction)
+    s = qs.NonuniformSolver(xn, yn, correction=correction,
+                            precision="fp64" if n == 31 else "fp32r")
     for m in (None, src["m"]):
         got = s.apply(_t(u), None if m is None else _t(m)).cpu().numpy()
         ref = nu.apply(xn, yn, u, m, correction)
@@ -71,12 +72,14 @@ def test_operator_and_source_match_oracle(qs, kind, correction, n):
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
 @pytest.mark.parametrize("kind", ["three_region", "alternating", "random"])
 @pytest.mark.parametrize("n", [7, 63, 255])
-def test_solve_matches_oracle(qs, kind, n):
+def test_solve_matches_oracle(qs, kind, n, precision):
+    """Both forms stop on the float64 residual, so both meet the same bound."""
     xn, yn = _axes(kind, n)
     src = bubble_sources(xn, yn, radius=3.0 if kind == "three_region" else 1.5)
-    s = qs.NonuniformSolver(xn, yn, correction=True)
+    s = qs.NonuniformSolver(xn, yn, correction=True, precision=precision)
     j = np.stack([src["psi"], src["bx"]])
     # Poisson (M = 0) and screened (M = -kappa) solves, two fields each
     for m in (None, src["m"]):
@@ -89,35 +92,39 @@ def test_solve_matches_oracle(qs, kind, n):
             assert _rel(got[c], ref) < PARITY, (c, _rel(got[c], ref))
 
 
-def test_plain_scheme_solve_matches_oracle(qs):
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_plain_scheme_solve_matches_oracle(qs, precision):
     xn, yn = _axes("alternating", 127)
     src = bubble_sources(xn, yn, radius=1.5)
-    s = qs.NonuniformSolver(xn, yn, correction=False)
+    s = qs.NonuniformSolver(xn, yn, correction=False, precision=precision)
     u, _, _ = s.solve(_t(src["by"]), m=_t(src["m"]), tol=_solve_tol(127), max_cycles=60)
     ref = nu.solve(xn, yn, src["by"], src["m"], correction=False)
     assert _rel(u.cpu().numpy(), ref) < PARITY
 
 
-def test_coarsest_only_grid(qs):
-    """n = 3: the exact coarse solve is the whole method."""
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_coarsest_only_grid(qs, precision):
+    """n = 3: the exact coarse solve is the whole method (one float32 solve
+    plus float64 refinement in the refined form)."""
     xn = np.array([-1.0, -0.7, 0.1, 0.4, 1.0])
     yn = np.array([-2.0, -0.5, 0.0, 1.5, 2.0])
     j = np.arange(9.0).reshape(3, 3) - 3.0
     m = -np.linspace(0.5, 1.5, 9).reshape(3, 3)
-    s = qs.NonuniformSolver(xn, yn, correction=True)
-    u, cycles, relres = s.solve(_t(j), m=_t(m), tol=1e-14, max_cycles=3)
-    assert cycles == 1
+    s = qs.NonuniformSolver(xn, yn, correction=True, precision=precision)
+    u, cycles, relres = s.solve(_t(j), m=_t(m), tol=1e-14, max_cycles=4)
+    assert cycles == 1 if precision == "fp64" else cycles <= 3
     np.testing.assert_allclose(u.cpu().numpy(), nu.solve(xn, yn, j, m), rtol=1e-13, atol=1e-14)
 
 
-def test_convergence_rate_and_warm_start(qs):
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_convergence_rate_and_warm_start(qs, precision):
     """Per V-cycle residual reduction on the three-region demonstration grid
     (cells up to 3:1 in aspect, which slows point smoothing), and a converged
     initial guess costs no cycle."""
     wl = nonuniform_workload("nonuni255")
     xn = wl.axis()
     src = bubble_sources(xn, xn, wl.bubble_radius)
-    s = qs.NonuniformSolver(xn, xn, correction=True)
+    s = qs.NonuniformSolver(xn, xn, correction=True, precision=precision)
     for key, m in (("psi", None), ("bx", src["m"])):
         mt = None if m is None else _t(m)
         u, cycles, relres = s.solve(_t(src[key]), m=mt, tol=1e-10, max_cycles=40)
@@ -128,11 +135,12 @@ def test_convergence_rate_and_warm_start(qs):
         np.testing.assert_array_equal(u2.cpu().numpy(), u.cpu().numpy())
 
 
-def test_fields_are_independent(qs):
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_fields_are_independent(qs, precision):
     """A batch of fields gives what each gives alone; a zero source gives zero."""
     xn, yn = _axes("random", 63)
     src = bubble_sources(xn, yn, radius=1.5)
-    s = qs.NonuniformSolver(xn, yn, correction=True)
+    s = qs.NonuniformSolver(xn, yn, correction=True, precision=precision)
     j = np.stack([src["ez"], np.zeros_like(src["ez"]), src["bz"], src["by"]])
     u4, _, relres = s.solve(_t(j), u=_t(np.ones_like(j)), m=_t(src["m"]), tol=1e-12,
                             max_cycles=60)
@@ -168,12 +176,13 @@ def test_solver_rejects_bad_calls(qs):
     assert lib.qs_nu_solve(s.h, None, 1, j.data_ptr(), j.data_ptr(), 1e-10, 0, None, None) == qs.QS_ERR_ARG
 
 
-def test_cycle_settings(qs):
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_cycle_settings(qs, precision):
     """Other sweep counts and relaxation reach the same solution; bad settings
     are rejected."""
     xn, yn = _axes("three_region", 127)
     src = bubble_sources(xn, yn)
-    s = qs.NonuniformSolver(xn, yn)
+    s = qs.NonuniformSolver(xn, yn, precision=precision)
     ref = nu.solve(xn, yn, src["bx"], src["m"])
     for pre, post, omega, blk in ((1, 1, 1.0, 0), (3, 2, 1.2, 3), (0, 2, 1.1, 63),
                                   (2, 0, 1.0, 127), (2, 2, 1.3, 4095)):
