@@ -427,9 +427,14 @@ int qs_nu_solve(qs_nu_solver *s, const double *d_m, int nrhs, const double *d_j,
  * sum >= 1) four-colour Gauss-Seidel sweeps per level, relaxed by omega
  * (0 < omega < 2; 1 = plain Gauss-Seidel); levels of side <= coarse_block_n
  * are relaxed by one thread block, the larger ones by the whole GPU
- * (0 = default).  Defaults 2, 2, 1.3, 31.  Host only.  Errors: QS_ERR_ARG. */
+ * (0 = default).  staged: 1 = the larger levels are smoothed in
+ * shared-memory tiles with recomputed halos (one grid barrier per level and
+ * leg; used when a tile's region fits in 200 KB, else 0), 0 = grid-wide
+ * colour sweeps (a barrier per colour).  Both give the same iterates up to
+ * rounding.
+ * Defaults 2, 2, 1.3, 31, 1.  Host only.  Errors: QS_ERR_ARG. */
 int qs_nu_set_cycle(qs_nu_solver *s, int pre_sweeps, int post_sweeps, double omega,
-                    int coarse_block_n);
+                    int coarse_block_n, int staged);
 
 /* d_out = A d_u for one field (DEVICE, n*n each; d_m as in qs_nu_solve).
  * Queued on the solver's stream without waiting.  Errors: QS_ERR_ARG,

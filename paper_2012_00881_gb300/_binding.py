@@ -102,7 +102,7 @@ PROTOTYPES = {
     "qs_bigaussian_adjoint": (_I, [_P, _P, _I64, _P, _P, _P, _P, _P, _P]),
     "qs_nu_create": (_I, [_I, _P, _P, _I, _I, _P, ctypes.POINTER(_P)]),
     "qs_nu_solve": (_I, [_P, _P, _I, _P, _P, _D, _I, _P, _P]),
-    "qs_nu_set_cycle": (_I, [_P, _I, _I, _D, _I]),
+    "qs_nu_set_cycle": (_I, [_P, _I, _I, _D, _I, _I]),
     "qs_nu_apply": (_I, [_P, _P, _P, _P]),
     "qs_nu_source": (_I, [_P, _P, _P]),
     "qs_nu_destroy": (None, [_P]),
@@ -525,12 +525,12 @@ class NonuniformSolver:
         return out, cycles.value, [relres[c] for c in range(nrhs)]
 
     def set_cycle(self, pre_sweeps: int = 2, post_sweeps: int = 2, omega: float = 1.3,
-                  coarse_block_n: int = 0):
-        """Sweeps per level, Gauss-Seidel relaxation and the one-block level
-        size of later solves (0 = default)."""
+                  coarse_block_n: int = 0, staged: bool = True):
+        """Sweeps per level, Gauss-Seidel relaxation, the one-block level size
+        (0 = default) and shared-memory staged smoothing of later solves."""
         self._check(self._lib.qs_nu_set_cycle(self.h, int(pre_sweeps), int(post_sweeps),
-                                              float(omega), int(coarse_block_n)),
-                    "qs_nu_set_cycle")
+                                              float(omega), int(coarse_block_n),
+                                              int(bool(staged))), "qs_nu_set_cycle")
 
     def apply(self, u, m=None):
         import torch

@@ -26,10 +26,13 @@
 // solve.
 //
 // Execution.  One persistent cooperative launch per solve: 152 blocks on a
-// bounded software grid barrier for the levels larger than local_n, one block
-// on __syncthreads for the rest (side <= 31 by default: below that a level's
-// work is too small to pay for ~20 grid barriers, above it one SM's share
-// of the work, which FP64 makes slow on this GPU, costs more than they do).
+// bounded software grid barrier for the levels larger than local_n (31 by
+// default), block 0 on __syncthreads for the rest.  Smoothing is staged in
+// shared memory: a level's down leg (pre-sweeps, residual, restriction) and up
+// leg (prolongation, post-sweeps) each run on tiles with a recomputed halo of
+// 4 max(nu1, nu2) + 2 nodes, one grid barrier per leg instead of one per
+// colour; the block-0 levels are staged whole.  Grid-wide colour sweeps (a
+// barrier per colour) remain for settings whose tiles do not fit.
 //
 // Forms.  FP64 cycles on a float64 hierarchy.  The refined form keeps the
 // solution, J' and the residual in float64 and cycles in float32 on the
@@ -56,6 +59,7 @@ constexpr int kThreads = 512;
 constexpr int kDefaultLocalN = 31;  // levels this small run in one block
 constexpr int kDefaultNu1 = 2, kDefaultNu2 = 2;  // V(2,2)
 constexpr double kDefaultOmega = 1.3;
+constexpr size_t kStageSmemMax = 200 * 1024;  // dynamic shared memory of staged tiles
 constexpr long long kBarrierLimit = 4000000000LL;  // clock cycles, ~2 s
 
 // Per-node coefficients of one axis: D2 (at i-1, i, i+1), D1 (same), c.
@@ -104,6 +108,9 @@ struct NuArgs {
     int nu1, nu2;             // pre- and post-smoothing sweeps
     double omega;             // Gauss-Seidel relaxation factor (folded into idiag)
     int local_n;              // levels of side <= local_n run in block 0 alone
+    int staged;               // levels smoothed in shared-memory tiles
+    int halo;                 // staged tiles' halo: 4 max(nu1, nu2) + 2
+    int stage_cap;            // nodes a staged region may hold
     double tol;
     const double *j;          // caller's sources (solve) / input (apply, source)
     const double *m_in;       // caller's M or nullptr
@@ -498,6 +505,263 @@ __device__ bool up_legs(const Level<T> *H, int nr, int nu2, int from, int to, Te
     return true;
 }
 
+
+// ---------------------------------------------------------------------------
+// Smoothing staged in shared memory.  A block takes a tile of a level, loads
+// the tile plus a halo of H = 4 max(nu1, nu2) + 2 nodes (u, f, M, omega/diag;
+// zero outside the domain), and runs every colour step of the sweeps there.
+// Each colour step can spoil at most one more ring from the region's stale
+// edge inwards, so after 4 nu steps the tile and two rings around it hold
+// exactly what the grid-wide sweeps would give; the residual on the tile and
+// one ring then feeds the restriction of the coarse nodes the tile owns.  A
+// level's down leg (nu1 sweeps, residual, restriction) and up leg
+// (prolongation, nu2 sweeps) are then one grid barrier each.
+// ---------------------------------------------------------------------------
+constexpr int kTileX = 32, kTileY = 16;
+
+struct TileGeom {
+    int tx, ty;               // tile size
+    int ntx, nty;             // tiles per row / column
+};
+
+// Tile size of a level: 32 x 16, halved (larger side first) while the level
+// has fewer than 64 tiles and the tile more than 64 nodes.
+__device__ __forceinline__ TileGeom tile_geom(int n) {
+    TileGeom g{kTileX, kTileY, 0, 0};
+    for (;;) {
+        g.ntx = (n + g.tx - 1) / g.tx;
+        g.nty = (n + g.ty - 1) / g.ty;
+        if (g.ntx * g.nty >= 64 || g.tx * g.ty <= 64) break;
+        if (g.tx >= g.ty) g.tx /= 2;
+        else g.ty /= 2;
+    }
+    return g;
+}
+
+// A level staged whole by one block: one tile of side n + 1 (even), halo 1.
+// Every in-domain node is in the region and the ring outside it holds the
+// walls' zeros, so no colour step can read a stale value.
+__device__ __forceinline__ TileGeom whole_geom(int n) { return TileGeom{n + 1, n + 1, 1, 1}; }
+
+__device__ __forceinline__ bool whole_fits(int n, int cap) { return (n + 3) * (n + 3) <= cap; }
+
+template <typename T>
+struct Region {
+    int x0, y0;     // global index of the region's first node (tile origin - H)
+    int rw, rh;     // region size
+    int tw, th;     // tile size, clipped at the domain's end
+    T *su, *sf;     // nrhs * rw * rh
+    T *sm, *sd;     // rw * rh
+};
+
+template <typename T>
+__device__ __forceinline__ Region<T> make_region(unsigned char *smem, int x0t, int y0t,
+                                                 const TileGeom &g, int n, int halo, int nrhs) {
+    Region<T> R;
+    R.x0 = x0t - halo;
+    R.y0 = y0t - halo;
+    R.rw = g.tx + 2 * halo;
+    R.rh = g.ty + 2 * halo;
+    R.tw = min(g.tx, n - x0t);
+    R.th = min(g.ty, n - y0t);
+    const int np = R.rw * R.rh;
+    T *p = reinterpret_cast<T *>(smem);
+    R.su = p;
+    R.sf = p + (size_t)nrhs * np;
+    R.sm = p + (size_t)2 * nrhs * np;
+    R.sd = p + (size_t)(2 * nrhs + 1) * np;
+    return R;
+}
+
+// Region load of u (from `usrc`, or zero), f, M and omega/diag; with a coarse
+// level C, u += P (coarse u) on the way in.
+template <typename T>
+__device__ void stage_load(const Level<T> &L, const T *usrc, const Level<T> *C,
+                           const Region<T> &R, int nrhs) {
+    const int n = L.n, np = R.rw * R.rh;
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+        const int b = q / R.rw, a = q - b * R.rw;
+        const int gi = R.x0 + a, gj = R.y0 + b;
+        const bool in = gi >= 0 && gj >= 0 && gi < n && gj < n;
+        const int g = gj * n + gi;
+        R.sm[q] = (in && L.m) ? L.m[g] : T(0);
+        R.sd[q] = in ? L.idiag[g] : T(0);
+        for (int c = 0; c < nrhs; ++c) {
+            T uv = (in && usrc) ? usrc[(size_t)c * n * n + g] : T(0);
+            if (in && C) {
+                // prolongation of the coarse correction at (gi, gj)
+                const int nc = C->n;
+                int ix0, ix1, iy0, iy1;
+                T wx0, wx1, wy0, wy1;
+                if (gi & 1) {
+                    ix0 = ix1 = (gi - 1) / 2;
+                    wx0 = T(1);
+                    wx1 = T(0);
+                } else {
+                    ix0 = (gi - 2) / 2;
+                    ix1 = gi / 2;
+                    wx0 = L.pwx[2 * gi];
+                    wx1 = L.pwx[2 * gi + 1];
+                }
+                if (gj & 1) {
+                    iy0 = iy1 = (gj - 1) / 2;
+                    wy0 = T(1);
+                    wy1 = T(0);
+                } else {
+                    iy0 = (gj - 2) / 2;
+                    iy1 = gj / 2;
+                    wy0 = L.pwy[2 * gj];
+                    wy1 = L.pwy[2 * gj + 1];
+                }
+                const T *e = C->u + (size_t)c * nc * nc;
+                uv += wy0 * (wx0 * at(e, nc, ix0, iy0) + wx1 * at(e, nc, ix1, iy0)) +
+                      wy1 * (wx0 * at(e, nc, ix0, iy1) + wx1 * at(e, nc, ix1, iy1));
+            }
+            R.su[(size_t)c * np + q] = uv;
+            R.sf[(size_t)c * np + q] = in ? L.f[(size_t)c * n * n + g] : T(0);
+        }
+    }
+}
+
+// (A u) at region node (a, b) from the staged arrays (1 <= a <= rw-2, 1 <= b <= rh-2).
+template <bool CORR, typename T>
+__device__ __forceinline__ T staged_apply(const Level<T> &L, const Region<T> &R, const T *u,
+                                          int a, int b, T &m0) {
+    const int q = b * R.rw + a;
+    const int gi = R.x0 + a, gj = R.y0 + b;
+    T v[3][3], mrow[3], mcol[3];
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) v[bb][aa] = u[q + (bb - 1) * R.rw + (aa - 1)];
+    m0 = R.sm[q];
+    mrow[0] = R.sm[q - 1];
+    mrow[1] = m0;
+    mrow[2] = R.sm[q + 1];
+    mcol[0] = R.sm[q - R.rw];
+    mcol[1] = m0;
+    mcol[2] = R.sm[q + R.rw];
+    return apply_point<CORR>(L.ax[gi], L.ay[gj], v, mrow, mcol, m0);
+}
+
+// The colour steps of `sweeps` sweeps on the region (every in-domain node
+// whose 3 x 3 neighbourhood is staged).
+template <bool CORR, typename T>
+__device__ void staged_sweeps(const Level<T> &L, const Region<T> &R, int nrhs, int sweeps) {
+    const int n = L.n, np = R.rw * R.rh;
+    for (int s = 0; s < sweeps; ++s)
+        for (int col = 0; col < 4; ++col) {
+            const int ci = col & 1, cj = col >> 1;
+            const int a0 = 1 + (((R.x0 + 1) & 1) != ci), b0 = 1 + (((R.y0 + 1) & 1) != cj);
+            const int na = a0 <= R.rw - 2 ? (R.rw - 2 - a0) / 2 + 1 : 0;
+            const int nb = b0 <= R.rh - 2 ? (R.rh - 2 - b0) / 2 + 1 : 0;
+            for (int k = threadIdx.x; k < na * nb; k += blockDim.x) {
+                const int kb = k / na;
+                const int a = a0 + 2 * (k - kb * na), b = b0 + 2 * kb;
+                const int gi = R.x0 + a, gj = R.y0 + b;
+                if (gi < 0 || gj < 0 || gi >= n || gj >= n) continue;
+                const int q = b * R.rw + a;
+                const T id = R.sd[q];
+                for (int c = 0; c < nrhs; ++c) {
+                    T *u = R.su + (size_t)c * np;
+                    T m0;
+                    const T au = staged_apply<CORR>(L, R, u, a, b, m0);
+                    u[q] += (R.sf[(size_t)c * np + q] - au) * id;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// Down leg of level l, one barrier: nu1 sweeps, residual, restriction into
+// level l + 1 (f, and u = 0).  The smoothed u goes to the level's r array,
+// not to u, which other blocks are still reading as halo in this phase; the
+// up leg reads it from there.  `u_zero`: u is known to be zero (every level
+// below the finest, and the finest of the refined form), so it is not read.
+template <bool CORR, typename T>
+__device__ void staged_down(const NuArgs &A, const Level<T> *H, int l, const TileGeom &g, int h,
+                            bool u_zero, unsigned char *smem) {
+    const Level<T> &L = H[l], &C = H[l + 1];
+    const int n = L.n, nc = C.n, nr = A.nrhs;
+    for (int t = blockIdx.x; t < g.ntx * g.nty; t += gridDim.x) {
+        const int ty = t / g.ntx, tx = t - ty * g.ntx;
+        const Region<T> R = make_region<T>(smem, tx * g.tx, ty * g.ty, g, n, h, nr);
+        const int np = R.rw * R.rh;
+        stage_load<T>(L, u_zero ? nullptr : L.u, nullptr, R, nr);
+        __syncthreads();
+        staged_sweeps<CORR>(L, R, nr, A.nu1);
+        // residual on the tile and one ring, in place of f
+        const int rw1 = R.tw + 2, rh1 = R.th + 2;
+        for (int k = threadIdx.x; k < rw1 * rh1; k += blockDim.x) {
+            const int kb = k / rw1;
+            const int a = h - 1 + (k - kb * rw1), b = h - 1 + kb;
+            const int gi = R.x0 + a, gj = R.y0 + b;
+            if (gi < 0 || gj < 0 || gi >= n || gj >= n) continue;
+            const int q = b * R.rw + a;
+            for (int c = 0; c < nr; ++c) {
+                T m0;
+                const T au = staged_apply<CORR>(L, R, R.su + (size_t)c * np, a, b, m0);
+                R.sf[(size_t)c * np + q] -= au;
+            }
+        }
+        __syncthreads();
+        // smoothed u of the tile, kept in r for the up leg
+        for (int k = threadIdx.x; k < R.tw * R.th; k += blockDim.x) {
+            const int kb = k / R.tw;
+            const int a = h + (k - kb * R.tw), b = h + kb;
+            const int g0 = (R.y0 + b) * n + (R.x0 + a), q = b * R.rw + a;
+            for (int c = 0; c < nr; ++c) L.r[(size_t)c * n * n + g0] = R.su[(size_t)c * np + q];
+        }
+        // coarse nodes of the tile: fine odd (gi, gj) inside it
+        const int x0t = R.x0 + h, y0t = R.y0 + h;
+        const int I0 = x0t / 2, J0 = y0t / 2;  // first coarse node with fine index >= origin
+        const int I1 = min((x0t + R.tw) / 2, nc), J1 = min((y0t + R.th) / 2, nc);
+        const int ni = I1 - I0;
+        for (int k = threadIdx.x; k < ni * (J1 - J0); k += blockDim.x) {
+            const int kJ = k / ni;
+            const int I = I0 + (k - kJ * ni), J = J0 + kJ;
+            const int a = 2 * I + 1 - R.x0, b = 2 * J + 1 - R.y0;
+            const T *wx = L.rwx + 3 * I, *wy = L.rwy + 3 * J;
+            for (int c = 0; c < nr; ++c) {
+                const T *r = R.sf + (size_t)c * np + b * R.rw + a;
+                T s = T(0);
+#pragma unroll
+                for (int bb = 0; bb < 3; ++bb) {
+                    const T *row = r + (bb - 1) * R.rw;
+                    s += wy[bb] * (wx[0] * row[-1] + wx[1] * row[0] + wx[2] * row[1]);
+                }
+                C.f[(size_t)c * nc * nc + J * nc + I] = s;
+                C.u[(size_t)c * nc * nc + J * nc + I] = T(0);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Up leg of level l, one barrier: the down leg's smoothed u (in r) plus
+// P (coarse u), nu2 sweeps, tile back to u.
+template <bool CORR, typename T>
+__device__ void staged_up(const NuArgs &A, const Level<T> *H, int l, const TileGeom &g, int h,
+                          unsigned char *smem) {
+    const Level<T> &L = H[l];
+    const int n = L.n, nr = A.nrhs;
+    for (int t = blockIdx.x; t < g.ntx * g.nty; t += gridDim.x) {
+        const int ty = t / g.ntx, tx = t - ty * g.ntx;
+        const Region<T> R = make_region<T>(smem, tx * g.tx, ty * g.ty, g, n, h, nr);
+        const int np = R.rw * R.rh;
+        stage_load<T>(L, L.r, &H[l + 1], R, nr);
+        __syncthreads();
+        staged_sweeps<CORR>(L, R, nr, A.nu2);
+        for (int k = threadIdx.x; k < R.tw * R.th; k += blockDim.x) {
+            const int kb = k / R.tw;
+            const int a = h + (k - kb * R.tw), b = h + kb;
+            const int g0 = (R.y0 + b) * n + (R.x0 + a), q = b * R.rw + a;
+            for (int c = 0; c < nr; ++c) L.u[(size_t)c * n * n + g0] = R.su[(size_t)c * np + q];
+        }
+        __syncthreads();
+    }
+}
+
 // One V-cycle on hierarchy H: the grid-wide levels 0..loc-1, then block 0
 // alone from loc to the exact coarsest solve and back.
 template <bool CORR, typename T>
@@ -509,16 +773,52 @@ __device__ bool vcycle(const NuArgs &A, const Level<T> *H, int loc, Team grid, T
         if (blockIdx.x == 0) coarse_solve(H[0], inv, nr, blk);
         return gsync(3);
     }
-    if (!down_legs<CORR>(H, nr, A.nu1, 0, loc, grid, gsync)) return false;
+    extern __shared__ __align__(16) unsigned char nu_dsmem[];
+    if (!A.staged) {
+        if (!down_legs<CORR>(H, nr, A.nu1, 0, loc, grid, gsync)) return false;
+        if (blockIdx.x == 0) {
+            const BlockSync bs;
+            down_legs<CORR>(H, nr, A.nu1, loc, Lc, blk, bs);
+            coarse_solve(H[Lc], inv, nr, blk);
+            __syncthreads();
+            up_legs<CORR>(H, nr, A.nu2, Lc - 1, loc, blk, bs);
+        }
+        if (!gsync(3)) return false;
+        return loc == 0 || up_legs<CORR>(H, nr, A.nu2, loc - 1, 0, grid, gsync);
+    }
+    // staged: grid-wide levels in tiles, the block-0 levels whole where they
+    // fit (else with block-wide colour sweeps through global memory)
+    for (int l = 0; l < loc; ++l) {
+        staged_down<CORR, T>(A, H, l, tile_geom(H[l].n), A.halo, l > 0 || sizeof(T) == 4,
+                             nu_dsmem);
+        if (!gsync(60 + l)) return false;
+    }
     if (blockIdx.x == 0) {
         const BlockSync bs;
-        down_legs<CORR>(H, nr, A.nu1, loc, Lc, blk, bs);
+        for (int l = loc; l < Lc; ++l) {
+            if (whole_fits(H[l].n, A.stage_cap))
+                staged_down<CORR, T>(A, H, l, whole_geom(H[l].n), 1, l > 0 || sizeof(T) == 4,
+                                     nu_dsmem);
+            else
+                down_legs<CORR>(H, nr, A.nu1, l, l + 1, blk, bs);
+            __syncthreads();
+        }
         coarse_solve(H[Lc], inv, nr, blk);
         __syncthreads();
-        up_legs<CORR>(H, nr, A.nu2, Lc - 1, loc, blk, bs);
+        for (int l = Lc - 1; l >= loc; --l) {
+            if (whole_fits(H[l].n, A.stage_cap))
+                staged_up<CORR, T>(A, H, l, whole_geom(H[l].n), 1, nu_dsmem);
+            else
+                up_legs<CORR>(H, nr, A.nu2, l, l, blk, bs);
+            __syncthreads();
+        }
     }
     if (!gsync(3)) return false;
-    return loc == 0 || up_legs<CORR>(H, nr, A.nu2, loc - 1, 0, grid, gsync);
+    for (int l = loc - 1; l >= 0; --l) {
+        staged_up<CORR, T>(A, H, l, tile_geom(H[l].n), A.halo, nu_dsmem);
+        if (!gsync(80 + l)) return false;
+    }
+    return true;
 }
 
 // FP64 form (T = double): every cycle in float64 on h64.
@@ -678,6 +978,7 @@ __global__ void nu_apply_kernel(const __grid_constant__ NuArgs A, const double *
 // ---------------------------------------------------------------------------
 struct qs_nu_solver {
     int n = 0, levels = 0, correction = 0, precision = QS_FP64;
+    int want_staged = 1;
     cudaStream_t stream = nullptr;
     int grid_blocks = 0;
     NuArgs args{};
@@ -925,7 +1226,11 @@ extern "C" int qs_nu_create(int n, const double *x_nodes, const double *y_nodes,
     st = cuda_status(cudaGetDevice(&dev));
     if (st == QS_OK) st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (st == QS_OK)
-        st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0));
+        st = cuda_status(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kStageSmemMax));
+    if (st == QS_OK)
+        st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads,
+                                                                       kStageSmemMax));
     if (st == QS_OK && per_sm < 1) st = QS_ERR_CUDA;
     if (st != QS_OK) {
         qs_nu_destroy(s);
@@ -957,6 +1262,14 @@ extern "C" int qs_nu_solve(qs_nu_solver *s, const double *d_m, int nrhs, const d
     }
     if (!d_m)
         for (int l = 0; l < A.levels; ++l) A.h64[l].m = nullptr, A.h32[l].m = nullptr;
+    // staged smoothing when the largest tile's region fits in shared memory
+    A.halo = 4 * (A.nu1 > A.nu2 ? A.nu1 : A.nu2) + 2;
+    const size_t elem = s->precision == QS_FP64 ? sizeof(double) : sizeof(float);
+    const size_t stage_bytes = (size_t)(2 * nrhs + 2) * (kTileX + 2 * A.halo) *
+                               (kTileY + 2 * A.halo) * elem;
+    A.staged = s->want_staged && stage_bytes <= kStageSmemMax;
+    A.stage_cap = (kTileX + 2 * A.halo) * (kTileY + 2 * A.halo);
+    const size_t dyn = A.staged ? stage_bytes : 0;
     int st = cuda_status(cudaMemsetAsync(A.sc, 0, sizeof(NuScalars), s->stream));
     if (st != QS_OK) return st;
     void *params[] = {&A};
@@ -968,7 +1281,7 @@ extern "C" int qs_nu_solve(qs_nu_solver *s, const double *d_m, int nrhs, const d
         fn = s->correction ? (const void *)nu_solve_kernel<true, float>
                            : (const void *)nu_solve_kernel<false, float>;
     st = cuda_status(cudaLaunchCooperativeKernel(fn, dim3(s->grid_blocks), dim3(kThreads), params,
-                                                 0, s->stream));
+                                                 dyn, s->stream));
     if (st != QS_OK) return st;
     st = cuda_status(cudaMemcpyAsync(s->pinned, A.sc, sizeof(NuScalars), cudaMemcpyDeviceToHost,
                                      s->stream));
@@ -983,10 +1296,12 @@ extern "C" int qs_nu_solve(qs_nu_solver *s, const double *d_m, int nrhs, const d
 }
 
 extern "C" int qs_nu_set_cycle(qs_nu_solver *s, int pre_sweeps, int post_sweeps, double omega,
-                               int coarse_block_n) {
+                               int coarse_block_n, int staged) {
     if (!s || pre_sweeps < 0 || post_sweeps < 0 || pre_sweeps > 8 || post_sweeps > 8 ||
-        pre_sweeps + post_sweeps < 1 || !(omega > 0.0 && omega < 2.0) || coarse_block_n < 0)
+        pre_sweeps + post_sweeps < 1 || !(omega > 0.0 && omega < 2.0) || coarse_block_n < 0 ||
+        (staged != 0 && staged != 1))
         return QS_ERR_ARG;
+    s->want_staged = staged;
     s->args.nu1 = pre_sweeps;
     s->args.nu2 = post_sweeps;
     s->args.omega = omega;

@@ -190,6 +190,38 @@ def test_cycle_settings(qs, precision):
         u, cycles, _ = s.solve(_t(src["bx"]), m=_t(src["m"]), tol=1e-12, max_cycles=200)
         assert _rel(u.cpu().numpy(), ref) < PARITY, (pre, post, omega)
     lib = qs.load_library()
-    for bad in ((0, 0, 1.0, 0), (-1, 2, 1.0, 0), (9, 2, 1.0, 0), (2, 2, 0.0, 0),
-                (2, 2, 2.0, 0), (2, 2, float("nan"), 0), (2, 2, 1.3, -1)):
+    for bad in ((0, 0, 1.0, 0, 1), (-1, 2, 1.0, 0, 1), (9, 2, 1.0, 0, 1), (2, 2, 0.0, 0, 1),
+                (2, 2, 2.0, 0, 1), (2, 2, float("nan"), 0, 1), (2, 2, 1.3, -1, 1),
+                (2, 2, 1.3, 0, 2)):
         assert lib.qs_nu_set_cycle(s.h, *bad) == qs.QS_ERR_ARG, bad
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+@pytest.mark.parametrize("sweeps", [(2, 2), (1, 2), (3, 1)])
+def test_staged_smoothing_is_exact(qs, precision, sweeps):
+    """Shared-memory staged smoothing (halo 4 max(nu) + 2, recomputed) gives
+    the iterates of grid-wide colour sweeps, including on levels whose tiles
+    are clipped by the domain's end and the one-block levels staged whole
+    (level 63 with one-block level 63 does not fit and mixes both ways of
+    smoothing).  The arithmetic is the same; the
+    compiler contracts multiply-adds differently in the two code paths, so
+    they agree to rounding: 1e-11 of the largest value in float64 (about
+    1e-15 absolute here), 1e-5 in the refined form's float32 cycles."""
+    xn, yn = _axes("random", 255)
+    src = bubble_sources(xn, yn, radius=1.5)
+    s = qs.NonuniformSolver(xn, yn, precision=precision)
+    j = _t(np.stack([src["bx"], src["by"]]))
+    m = _t(src["m"])
+    got = {}
+    for staged in (True, False):
+        for blk in (63, 31, 7):
+            s.set_cycle(sweeps[0], sweeps[1], 1.3, blk, staged)
+            u, cycles, relres = s.solve(j, u=_t(np.full((2, 255, 255), 0.1)), m=m, tol=1e-11,
+                                        max_cycles=4, raise_on_error=False)
+            got[(staged, blk)] = (u.cpu().numpy(), cycles, relres)
+    tol = 1e-11 if precision == "fp64" else 1e-5
+    for blk in (63, 31, 7):
+        a, b = got[(True, blk)], got[(False, blk)]
+        np.testing.assert_allclose(a[0], b[0], rtol=0, atol=tol * np.abs(b[0]).max())
+        assert a[1] == b[1]
+        np.testing.assert_allclose(a[2], b[2], rtol=1e-3 if precision == "fp32r" else 1e-8)
