@@ -758,6 +758,133 @@ def nonuni_cpu_baseline(wl, seconds: float):
                       f"(SuperLU), FP64, single thread"}
 
 
+# ---------------------------------------------------------------- laser envelope
+LASER = "laser256"
+LASER_SOURCES = ("qs_laser.cu", "qs_grid_sync.cuh")
+# FP64 flops per cell and V-cycle of the complex solve: four red-black sweeps
+# at 30 flops a cell (complex 5-point Laplacian, kappa u, the update), one
+# residual (22) and the transfers (10), times 4/3 for the coarse levels, plus
+# the residual of the stopping test (22).
+LASER_FLOPS_PER_CELL_CYCLE = 4.0 / 3.0 * (4 * 30 + 22 + 10) + 22
+
+
+def _laser_desc(wl):
+    return (f"{wl.name}: {wl.n}x{wl.n} cells over a {wl.width:g} box, {wl.n_xi} slices of "
+            f"{wl.dxi:g}, k0={wl.k0:g}, dt={wl.dt:g}, Gaussian pulse a0={wl.a0:g} w0={wl.w0:g} "
+            f"sigma_xi={wl.sigma_xi:g} in a synthetic blowout susceptibility; one time step of "
+            f"the envelope per step, slices solved to tol={wl.tol:g}")
+
+
+def run_laser(args):
+    """The laser-envelope advance (Eq. laser_Enve) on laser256: a step is one
+    time step of the envelope over all slices (one complex multigrid solve
+    per slice, warm-started from the previous time step)."""
+    import torch
+
+    import paper_2012_00881_gb300 as qs
+    from workloads.laser import bubble_susceptibility, gaussian_pulse, laser_workload
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("nccl")
+    wl = laser_workload(LASER)
+    a_host = torch.tensor(gaussian_pulse(wl))
+    chi_host = torch.tensor(bubble_susceptibility(wl))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lz = qs.LaserEnvelope(wl.n, wl.width, wl.n_xi, wl.k0, wl.dt, wl.dxi, stream=stream)
+        chi = chi_host.cuda()
+        a = a_host.cuda()
+        for _ in range(args.warmup):
+            lz.advance(chi, a, steps=1, tol=wl.tol)
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        evs = []
+        cycles = 0
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, c, _ = lz.advance(chi, a, steps=1, tol=wl.tol)
+            e1.record(stream)
+            evs.append((e0, e1))
+            cycles += c
+        stream.synchronize()
+        clocks = sampler.stop()
+    ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in evs)) / args.steps
+    slices = wl.n_xi * args.steps
+    value = job_rate(slices, world, ms * args.steps / 1e3)
+    flops = LASER_FLOPS_PER_CELL_CYCLE * wl.n * wl.n * cycles
+    achieved = flops / (ms * args.steps / 1e3) / 1e9
+    fp64_peak = 1250.0
+    traffic = measured_traffic("laser_kernel", LASER, "fp64",
+                               source_hash=engine_source_hash(LASER_SOURCES))
+    # end to end: envelope and susceptibility from pinned host memory, the
+    # new envelope back, every step
+    a_pin = a_host.pin_memory()
+    chi_pin = chi_host.pin_memory()
+    out_pin = torch.empty_like(a_host).pin_memory()
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            a.copy_(a_pin, non_blocking=True)
+            chi.copy_(chi_pin, non_blocking=True)
+            lz.advance(chi, a, steps=1, tol=wl.tol)
+            out_pin.copy_(a, non_blocking=True)
+        e1.record(stream)
+        stream.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    out = {
+        "metric": "laser_xi_slices_per_s", "value": value, "unit": "laser slices/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": _laser_desc(wl), "v_cycles_per_slice": cycles / slices,
+                   "l2": "working set (about 190 MB: envelope and susceptibility of every "
+                         "slice) exceeds L2"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                     "unit": "GFLOP/s (FP64, nominal peak)", "frac": achieved / fp64_peak,
+                     "traffic": traffic},
+        "e2e": {"value": job_rate(slices, world, e2e_ms * args.steps / 1e3),
+                "unit": "laser slices/s", "h2d_bytes_per_step": a_host.numel() * 16 +
+                chi_host.numel() * 8, "d2h_bytes_per_step": a_host.numel() * 16},
+        "gpu_launches": args.steps,  # one persistent launch per advance
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = laser_cpu_baseline(wl, args.cpu_seconds)
+    lz.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def laser_cpu_baseline(wl, seconds: float):
+    """The oracle's step on the first slices of the same workload (one thread)."""
+    import math as _m
+    from oracle import qs_laser as OL
+    from oracle.qs_oracle import Grid
+    from workloads.laser import bubble_susceptibility, gaussian_pulse
+    g = Grid.square(wl.n, wl.width / 2)
+    a = gaussian_pulse(wl)
+    chi = bubble_susceptibility(wl)
+    t0 = time.perf_counter()
+    k = 4
+    while True:
+        OL.envelope_advance(g, a[:k], chi[:k], wl.k0, wl.dt, wl.dxi, 1)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 3 or k >= wl.n_xi:
+            break
+        k = min(wl.n_xi, 2 * k)
+        t0 = time.perf_counter()
+    return {"value": k / dt, "unit": "laser slices/s", "cores": 1, "kind": "oracle",
+            "sample": f"one time step of the first {k} slices of {wl.name}, scipy sparse LU "
+                      f"per slice, FP64, single thread"}
+
+
 def _oracle_sample(wl, seconds: float):
     """Time the FP64 oracle on the first base slices of one 3D step of the
     workload, growing the slice count until about `seconds` of CPU work."""
@@ -796,6 +923,8 @@ def run_reference(args):
         return
     if args.workload == NONUNI:
         return run_reference_nonuniform(args, world)
+    if args.workload == LASER:
+        return run_reference_laser(args, world)
     wl = _load_workload(args)
     if wl is None:  # the scan: time the oracle on its 256^2 instances
         import workloads as W
@@ -844,6 +973,27 @@ def run_reference_nonuniform(args, world):
     print(json.dumps(out), flush=True)
 
 
+def run_reference_laser(args, world):
+    from workloads.laser import laser_workload
+    wl = laser_workload(LASER)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        b = laser_cpu_baseline(wl, max(2.0, args.cpu_seconds / 2))
+        if i >= args.warmup:
+            vals.append(b["value"])
+    v = statistics.mean(vals)
+    out = {"impl": "reference", "metric": "laser_xi_slices_per_s", "value": v,
+           "unit": "laser slices/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": wl.n_xi * 1e3 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": _laser_desc(wl), "form": "oracle"},
+           "cpu_baseline": {"value": v, "unit": "laser slices/s", "cores": 1, "kind": "oracle",
+                            "sample": b["sample"]},
+           "e2e": {"value": v, "unit": "laser slices/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
@@ -854,5 +1004,7 @@ if __name__ == "__main__":
         run_grad(a)
     elif a.workload == NONUNI:
         run_nonuniform(a)
+    elif a.workload == LASER:
+        run_laser(a)
     else:
         run_native(a)

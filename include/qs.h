@@ -449,6 +449,48 @@ int qs_nu_source(qs_nu_solver *s, const double *d_j, double *d_out);
 /* Free the solver and its device memory (NULL is a no-op). */
 void qs_nu_destroy(qs_nu_solver *s);
 
+/* ---- Laser-envelope advance ---------------------------------------------
+ * Sec. "Description of different plasma wake drivers", Eq. laser_Enve: the
+ * complex envelope A of a laser with vector potential A exp(-i k0 xi) obeys
+ *   (2 i k0 d_t - 2 d_t d_xi + lap_perp) A = chi A,   chi = n_* / (1 + psi).
+ * One time step is time-centred for lap_perp and chi, with the mixed
+ * derivative as the time difference of a backward (towards the head)
+ * difference in xi; slices advance from the head (j = 0) to the tail, each a
+ * complex screened-Poisson equation
+ *   (lap - chi_j + c) A^{n+1}_j = (c + chi_j - lap) A^n_j - q (A^{n+1}_{j-1} - A^n_{j-1}),
+ *   c = 4 (i k0 - 1/dxi) / dt,  q = 4 / (dt dxi)
+ * solved by complex multigrid (red-black Gauss-Seidel V(2,2), warm-started
+ * from A^n_j as the paper does).  chi is held at t_n; A = 0 ahead of the
+ * window and on the walls.  The grid is the slice advance's: n x n cells on a
+ * square box of side `width`, cell-centred, 5-point Laplacian with odd
+ * ghosts; multigrid coarsens while the side is even and above 4, so n should
+ * be c * 2^L with c <= 4. */
+typedef struct qs_laser qs_laser;
+
+/* n cells per side (2 .. 8192), width > 0 (k_p^-1), n_xi >= 1 slices, k0 =
+ * omega_0 / omega_p > 0, dt > 0 (1/omega_p), dxi > 0 the slice spacing, or
+ * +inf for no xi coupling (q = 0).  cuda_stream: the cudaStream_t of every
+ * call (NULL = legacy default).  The object owns about (4 + 5 * 4/3) n^2
+ * complex128 of device memory until qs_laser_destroy.  Argument checks come
+ * before any CUDA call.  Errors: QS_ERR_ARG, QS_ERR_OOM, QS_ERR_CUDA. */
+int qs_laser_create(int n, double width, int n_xi, double k0, double dt, double dxi,
+                    void *cuda_stream, qs_laser **out);
+
+/* Advance the envelope `steps` (>= 0) time steps with chi held fixed.
+ * d_chi: DEVICE float64 [n_xi][n][n]; d_a: DEVICE complex128 [n_xi][n][n]
+ * (interleaved re, im), A^n in, A^{n+steps} out, caller-owned, written in
+ * place.  Each slice's solve stops at ||f - A u||_2 <= tol ||f||_2 or after
+ * max_cycles V-cycles.  cycles (HOST, may be NULL): V-cycles over all slices
+ * and steps; max_relres (HOST, may be NULL): the largest final relative
+ * residual of a slice.  Synchronises the stream.  Errors: QS_ERR_ARG,
+ * QS_ERR_NOT_CONVERGED (some slice hit max_cycles; the advance still
+ * completed), QS_ERR_TIMEOUT, QS_ERR_CUDA. */
+int qs_laser_advance(qs_laser *s, const double *d_chi, double *d_a, int steps, double tol,
+                     int max_cycles, int64_t *cycles, double *max_relres);
+
+/* Free the object and its device memory (NULL is a no-op). */
+void qs_laser_destroy(qs_laser *s);
+
 /* Name of a status code (static string). */
 const char *qs_strerror(int status);
 

@@ -106,6 +106,9 @@ PROTOTYPES = {
     "qs_nu_apply": (_I, [_P, _P, _P, _P]),
     "qs_nu_source": (_I, [_P, _P, _P]),
     "qs_nu_destroy": (None, [_P]),
+    "qs_laser_create": (_I, [_I, _D, _I, _D, _D, _D, _P, ctypes.POINTER(_P)]),
+    "qs_laser_advance": (_I, [_P, _P, _P, _I, _D, _I, _P, _P]),
+    "qs_laser_destroy": (None, [_P]),
     "qs_strerror": (ctypes.c_char_p, [_I]),
     "qs_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -549,6 +552,55 @@ class NonuniformSolver:
     def close(self):
         if self.h:
             self._lib.qs_nu_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LaserEnvelope:
+    """qs_laser_* : the envelope advance of Eq. laser_Enve on an n x n
+    cell-centred grid of side `width` with n_xi slices (float64 / complex128
+    CUDA tensors).  dxi = math.inf drops the xi coupling."""
+
+    def __init__(self, n: int, width: float, n_xi: int, k0: float, dt: float, dxi: float,
+                 stream=None):
+        import torch
+        self._lib = load_library()
+        self.h = None
+        self.n, self.n_xi = int(n), int(n_xi)
+        self._stream = torch.cuda.current_stream() if stream is None else stream
+        h = _P()
+        rc = self._lib.qs_laser_create(self.n, float(width), self.n_xi, float(k0), float(dt),
+                                       float(dxi), _P(self._stream.cuda_stream),
+                                       ctypes.byref(h))
+        if rc != QS_OK:
+            raise QsError(rc, "qs_laser_create: " + self._lib.qs_strerror(rc).decode())
+        self.h = h.value
+
+    def advance(self, chi, a, steps: int = 1, tol: float = 1e-10, max_cycles: int = 50,
+                raise_on_error: bool = True):
+        """Advance `a` (complex128 [n_xi, n, n], in place) by `steps` steps with
+        `chi` (float64, same shape) fixed.  Returns (a, cycles, max_relres)."""
+        import torch
+        if a.dtype != torch.complex128 or not a.is_contiguous():
+            raise QsError(QS_ERR_ARG, "a must be a contiguous complex128 tensor")
+        cycles = ctypes.c_int64(0)
+        relres = ctypes.c_double(0.0)
+        rc = self._lib.qs_laser_advance(self.h, _ptr(chi.contiguous()), _ptr(a), int(steps),
+                                        float(tol), int(max_cycles), ctypes.byref(cycles),
+                                        ctypes.byref(relres))
+        self.status = rc
+        if raise_on_error and rc != QS_OK:
+            raise QsError(rc, "qs_laser_advance: " + self._lib.qs_strerror(rc).decode())
+        return a, cycles.value, relres.value
+
+    def close(self):
+        if self.h:
+            self._lib.qs_laser_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -19,7 +19,7 @@ OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(LIBDIR, "libqs.so")
 
 SOURCES = ["qs_api.cu", "qs_engine.cu", "qs_adjoint.cu", "qs_aux.cu", "qs_grad_aux.cu",
-           "qs_nonuniform.cu"]
+           "qs_nonuniform.cu", "qs_laser.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

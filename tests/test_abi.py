@@ -103,3 +103,21 @@ def test_nonuniform_solver_arguments_rejected_without_gpu(lib):
     for args in ((None, None, 1, None, None, 1e-10, 10, None, None),):
         assert l.qs_nu_solve(*args) == qs.QS_ERR_ARG
     l.qs_nu_destroy(None)
+
+
+def test_laser_arguments_rejected_without_gpu(lib):
+    """qs_laser_create validates its arguments before any device call."""
+    import math
+    import paper_2012_00881_gb300 as qs
+    l = qs.load_library()
+    h = ctypes.c_void_p()
+    good = dict(n=16, width=4.0, n_xi=4, k0=3.0, dt=0.5, dxi=0.1)
+    for bad in (dict(n=1), dict(n=9000), dict(width=0.0), dict(width=math.inf), dict(n_xi=0),
+                dict(k0=0.0), dict(k0=math.nan), dict(dt=-1.0), dict(dt=math.inf),
+                dict(dxi=0.0), dict(dxi=-0.1), dict(dxi=math.nan)):
+        a = dict(good, **bad)
+        assert l.qs_laser_create(a["n"], a["width"], a["n_xi"], a["k0"], a["dt"], a["dxi"],
+                                 None, ctypes.byref(h)) == qs.QS_ERR_ARG, bad
+    assert l.qs_laser_create(16, 4.0, 4, 3.0, 0.5, 0.1, None, None) == qs.QS_ERR_ARG
+    assert l.qs_laser_advance(None, None, None, 1, 1e-10, 10, None, None) == qs.QS_ERR_ARG
+    l.qs_laser_destroy(None)
