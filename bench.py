@@ -789,6 +789,9 @@ def run_laser(args):
     if world > 1 and not torch.distributed.is_initialized():
         torch.distributed.init_process_group("nccl")
     wl = laser_workload(LASER)
+    if args.slices > 0:
+        import dataclasses
+        wl = dataclasses.replace(wl, n_xi=min(args.slices, wl.n_xi))
     a_host = torch.tensor(gaussian_pulse(wl))
     chi_host = torch.tensor(bubble_susceptibility(wl))
     stream = torch.cuda.Stream()
