@@ -514,11 +514,20 @@ class NonuniformSolver:
         jj = j.reshape(-1, self.n, self.n).contiguous()
         if u is None:
             u = torch.zeros_like(jj)
-        uu = u.reshape(-1, self.n, self.n)
+        # the library writes u in place: it must be the caller's own storage
+        if not u.is_contiguous() or u.numel() != jj.numel():
+            raise QsError(QS_ERR_ARG, "u must be a contiguous tensor shaped like j")
+        uu = u.view(-1, self.n, self.n)
+        mm = None if m is None else m.contiguous()
+        for t in (jj, uu) + (() if mm is None else (mm,)):
+            if t.dtype != torch.float64 or not t.is_cuda:
+                raise QsError(QS_ERR_ARG, "j, u and m must be float64 CUDA tensors")
+        if mm is not None and mm.numel() != self.n * self.n:
+            raise QsError(QS_ERR_ARG, "m must hold n * n values")
         nrhs = int(jj.shape[0])
         cycles = ctypes.c_int(0)
         relres = (ctypes.c_double * 4)()
-        rc = self._lib.qs_nu_solve(self.h, _ptr(m), nrhs, _ptr(jj), _ptr(uu), float(tol),
+        rc = self._lib.qs_nu_solve(self.h, _ptr(mm), nrhs, _ptr(jj), _ptr(uu), float(tol),
                                    int(max_cycles), ctypes.byref(cycles),
                                    ctypes.cast(relres, _P))
         self.status = rc
@@ -537,15 +546,18 @@ class NonuniformSolver:
 
     def apply(self, u, m=None):
         import torch
-        out = torch.empty_like(u)
-        self._check(self._lib.qs_nu_apply(self.h, _ptr(m), _ptr(u), _ptr(out)), "qs_nu_apply")
+        uc = u.contiguous()
+        mm = None if m is None else m.contiguous()
+        out = torch.empty_like(uc)
+        self._check(self._lib.qs_nu_apply(self.h, _ptr(mm), _ptr(uc), _ptr(out)), "qs_nu_apply")
         self._stream.synchronize()
         return out
 
     def source(self, j):
         import torch
-        out = torch.empty_like(j)
-        self._check(self._lib.qs_nu_source(self.h, _ptr(j), _ptr(out)), "qs_nu_source")
+        jc = j.contiguous()
+        out = torch.empty_like(jc)
+        self._check(self._lib.qs_nu_source(self.h, _ptr(jc), _ptr(out)), "qs_nu_source")
         self._stream.synchronize()
         return out
 
@@ -586,11 +598,16 @@ class LaserEnvelope:
         """Advance `a` (complex128 [n_xi, n, n], in place) by `steps` steps with
         `chi` (float64, same shape) fixed.  Returns (a, cycles, max_relres)."""
         import torch
-        if a.dtype != torch.complex128 or not a.is_contiguous():
-            raise QsError(QS_ERR_ARG, "a must be a contiguous complex128 tensor")
+        shape = (self.n_xi, self.n, self.n)
+        if a.dtype != torch.complex128 or not a.is_contiguous() or tuple(a.shape) != shape:
+            raise QsError(QS_ERR_ARG, "a must be a contiguous complex128 tensor [n_xi, n, n]")
+        # keep the contiguous copy alive until the call has returned
+        chi_c = chi.contiguous()
+        if chi_c.dtype != torch.float64 or tuple(chi_c.shape) != shape:
+            raise QsError(QS_ERR_ARG, "chi must be a float64 tensor [n_xi, n, n]")
         cycles = ctypes.c_int64(0)
         relres = ctypes.c_double(0.0)
-        rc = self._lib.qs_laser_advance(self.h, _ptr(chi.contiguous()), _ptr(a), int(steps),
+        rc = self._lib.qs_laser_advance(self.h, _ptr(chi_c), _ptr(a), int(steps),
                                         float(tol), int(max_cycles), ctypes.byref(cycles),
                                         ctypes.byref(relres))
         self.status = rc
