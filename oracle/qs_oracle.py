@@ -60,11 +60,22 @@ library, which was written separately):
 14. The driver push is the relativistic Boris scheme (a volume-preserving
     integrator) with the wake gathered trilinearly from the stored base
     slices; xi = t - z advances by dt (1 - v_z).
+15. Laser driver (optional; Eq. EoM_111, the line after it, Eq.
+    FluxCurr1_A): |A|^2 of the envelope is given at the base slices and
+    taken linearly in xi at sub-steps, like the driver current.  It adds
+    |A|^2/2 to the numerator of gamma, -grad(|A|^2/4)/(1+psi) to the kicks
+    of the push, and -n_* grad(|A|^2/4)/(1+psi)^2 to S.  grad(|A|^2) is a
+    central difference with even ghosts (A is odd at the walls, so |A|^2 is
+    mirrored) gathered by CIC like grad(psi).  The step returns
+    chi = n_*/(1+psi) at the base slices for the envelope advance of Eq.
+    laser_Enve.
 
 Parity status: every function here is pinned by tests under tests/ marked
 "not gpu" (eigenmodes, manufactured solutions, the linear-wake closed form,
 conservation laws, the xi-derivative identity behind Eq. FluxCurr1_A, and
-exact orbits of the driver push).
+exact orbits of the driver push; the laser terms by the mass shell with
+|A|^2/2, ponderomotive expulsion with energy conservation, and the linear
+laser wake (d_xi^2 + 1) psi = |A|^2/4 in tests/test_laser_wake_pins.py).
 """
 from __future__ import annotations
 
@@ -184,6 +195,11 @@ def _pad(u: np.ndarray, ghost: str) -> np.ndarray:
         p[-1, 1:-1] = -u[-1, :]
         p[1:-1, 0] = -u[:, 0]
         p[1:-1, -1] = -u[:, -1]
+    elif ghost == "even":
+        p[0, 1:-1] = u[0, :]
+        p[-1, 1:-1] = u[-1, :]
+        p[1:-1, 0] = u[:, 0]
+        p[1:-1, -1] = u[:, -1]
     elif ghost != "zero":
         raise ValueError(ghost)
     return p
@@ -308,16 +324,21 @@ class SliceFields:
     moments: Dict[str, np.ndarray]
     vmax_in: float
     guard_hits: int
+    # laser driver (Eq. EoM_111): |A|^2 on the grid and grad(|A|^2 / 4)
+    a2: Optional[np.ndarray] = None
+    pond_x: Optional[np.ndarray] = None
+    pond_y: Optional[np.ndarray] = None
 
     def stack(self) -> np.ndarray:
         return np.stack([self.psi, self.Ez, self.Bz, self.Bx, self.By])
 
 
-def gamma_qs(px, py, a):
+def gamma_qs(px, py, a, a2=0.0):
     """Lorentz factor of a plasma electron from the constant of motion
-    gamma - p_z = 1 + psi: gamma = (1 + p_perp^2 + (1+psi)^2) / (2 (1+psi))
-    (line after Eq. EoM_111, laser term zero); a = 1 + psi."""
-    return (1.0 + px * px + py * py + a * a) / (2.0 * a)
+    gamma - p_z = 1 + psi: gamma = (1 + p_perp^2 + (1+psi)^2 + |A|^2/2) /
+    (2 (1+psi)) (line after Eq. EoM_111); a = 1 + psi, a2 = |A|^2 of the laser
+    envelope at the particle (0 without a laser)."""
+    return (1.0 + px * px + py * py + a * a + 0.5 * a2) / (2.0 * a)
 
 
 def _guard(a: np.ndarray, floor: float):
@@ -326,15 +347,21 @@ def _guard(a: np.ndarray, floor: float):
 
 
 def slice_fields(g: Grid, pl: Plasma, n_ion: np.ndarray, jzb: np.ndarray,
-                 psi_floor: float) -> SliceFields:
-    """Collect_Source + Solve_Wakefield of Algorithm 1 for one slice."""
+                 psi_floor: float, a2: Optional[np.ndarray] = None) -> SliceFields:
+    """Collect_Source + Solve_Wakefield of Algorithm 1 for one slice.
+
+    `a2` is |A|^2 of a laser envelope on the grid (None: no laser).  It enters
+    gamma (line after Eq. EoM_111), hence <gamma> and j_z, and the source S
+    through -n_* grad(|A|^2/4) / (1+psi)^2 (Eq. FluxCurr1_A).  |A|^2 takes
+    even ghosts at the walls (A is odd there)."""
     h = g.h
     # surface density n_* (Eq. continuity) and psi (Eq. EqM_N8_AA)
     n_star = deposit(pl.x, pl.y, pl.w, g)
     psi = solve_poisson(n_star - n_ion, h)
     # per-particle 1 + psi, gamma (line after Eq. EoM_111), V (Eq. EoM_112_A)
     a_p, hits = _guard(1.0 + gather(psi, pl.x, pl.y, g), psi_floor)
-    gam = gamma_qs(pl.px, pl.py, a_p)
+    a2_p = 0.0 if a2 is None else gather(a2, pl.x, pl.y, g)
+    gam = gamma_qs(pl.px, pl.py, a_p, a2_p)
     vx = pl.px / a_p
     vy = pl.py / a_p
     # moments: j_perp = n_* <V> (Eq. Jr), T = n_* <V V> (Eq. FluxPres), G = n_* <gamma>
@@ -364,13 +391,21 @@ def slice_fields(g: Grid, pl: Plasma, n_ion: np.ndarray, jzb: np.ndarray,
           + gsum * dpy / (a_g * a_g)
           - jy * ez / a_g
           - (txy * dpx + tyy * dpy) / a_g)
+    pond_x = pond_y = None
+    if a2 is not None:
+        # ponderomotive term of Eq. FluxCurr1_A: -n_* grad(|A|^2/4) / (1+psi)^2
+        pond_x = ddx(0.25 * a2, h, "even")
+        pond_y = ddy(0.25 * a2, h, "even")
+        sx = sx - n_star * pond_x / (a_g * a_g)
+        sy = sy - n_star * pond_y / (a_g * a_g)
     # B_perp: laplacian(B) - kappa B = -e_z x S = (S_y, -S_x)  (Eq. Main_Eq_A)
     bx, lu = solve_screened(sy, kappa, h)
     by, _ = solve_screened(-sx, kappa, h, lu)
     vmax_in = float(np.sqrt(vx * vx + vy * vy).max()) if len(vx) else 0.0
     mom = dict(n_star=n_star, jx=jx, jy=jy, txx=txx, txy=txy, tyy=tyy, G=gsum, jz=jz,
                kappa=kappa, Sx=sx, Sy=sy)
-    return SliceFields(psi, ez, bz, bx, by, dpx, dpy, mom, vmax_in, hits + hits_g)
+    return SliceFields(psi, ez, bz, bx, by, dpx, dpy, mom, vmax_in, hits + hits_g,
+                       a2, pond_x, pond_y)
 
 
 # --------------------------------------------------------------------------
@@ -387,10 +422,19 @@ def push_plasma(g: Grid, pl: Plasma, F: SliceFields, dxi: float, psi_floor: floa
     by = gather(F.By, x, y, g)
     bz = gather(F.Bz, x, y, g)
     half = 0.5 * dxi
-    # electric-like part of Eq. EoM_111: gamma grad(psi)/(1+psi) + e_z x B_perp
-    gam = gamma_qs(pl.px, pl.py, a)
-    pxm = pl.px + half * (gam * gx / a - by)
-    pym = pl.py + half * (gam * gy / a + bx)
+    # laser (Eq. EoM_111): |A|^2 in gamma and the force -grad(|A|^2/4)/(1+psi)
+    if F.a2 is not None:
+        a2 = gather(F.a2, x, y, g)
+        px_pond = gather(F.pond_x, x, y, g)
+        py_pond = gather(F.pond_y, x, y, g)
+    else:
+        a2 = 0.0
+        px_pond = py_pond = 0.0
+    # electric-like part of Eq. EoM_111:
+    # gamma grad(psi)/(1+psi) - grad(|A|^2/4)/(1+psi) + e_z x B_perp
+    gam = gamma_qs(pl.px, pl.py, a, a2)
+    pxm = pl.px + half * ((gam * gx - px_pond) / a - by)
+    pym = pl.py + half * ((gam * gy - py_pond) / a + bx)
     # rotation by the B_z term: dp/dxi = (e_z x p) B_z / (1+psi)
     tau = half * bz / a
     pxp_ = pxm - tau * pym
@@ -398,9 +442,9 @@ def push_plasma(g: Grid, pl: Plasma, F: SliceFields, dxi: float, psi_floor: floa
     s = 2.0 * tau / (1.0 + tau * tau)
     pxr = pxm - s * pyp_
     pyr = pym + s * pxp_
-    gam2 = gamma_qs(pxr, pyr, a)
-    px = pxr + half * (gam2 * gx / a - by)
-    py = pyr + half * (gam2 * gy / a + bx)
+    gam2 = gamma_qs(pxr, pyr, a, a2)
+    px = pxr + half * ((gam2 * gx - px_pond) / a - by)
+    py = pyr + half * ((gam2 * gy - py_pond) / a + bx)
     # drift with V = p / (1 + psi)
     nx = x + dxi * px / a
     ny = y + dxi * py / a
@@ -491,17 +535,23 @@ class StepResult:
     pushes: int                  # plasma particle pushes
     guard_hits: int
     final_plasma: Plasma
+    chi: Optional[np.ndarray] = None   # (n_xi, N, N) n_* / (1+psi) with a laser driver
 
 
 def step3d(cfg: Config, plasma0: Plasma, n_ion: np.ndarray, beams: Sequence[dict],
            jzb: Optional[np.ndarray] = None, n_slices: Optional[int] = None,
-           m_schedule: Optional[Sequence[int]] = None) -> StepResult:
+           m_schedule: Optional[Sequence[int]] = None,
+           laser_a2: Optional[np.ndarray] = None) -> StepResult:
     """One 3D step with frozen drivers: the xi loop of Algorithm 1.
 
     `jzb` may be given directly (shape (n_xi, N, N)) instead of beam particles.
     `n_slices` truncates the loop after that many base slices.
     `m_schedule` fixes the sub-steps of every base interval instead of the
     adaptive rule (used to freeze the schedule of a previous run).
+    `laser_a2` is |A|^2 of a laser envelope at the base slices (shape
+    (n_xi, N, N)), interpolated linearly in xi at sub-steps like the driver
+    current; the result then also holds the laser susceptibility
+    chi = n_* / (1+psi) of Eq. laser_Enve at the base slices.
     """
     g = cfg.grid
     nb = cfg.n_xi if n_slices is None else n_slices
@@ -516,18 +566,26 @@ def step3d(cfg: Config, plasma0: Plasma, n_ion: np.ndarray, beams: Sequence[dict
     m = 1 if m_schedule is None else int(m_schedule[0])
     slices = pushes = hits = 0
     zero = np.zeros((g.n, g.n))
+    chi = None if laser_a2 is None else np.zeros((nb, g.n, g.n))
     for j in range(nb):
         ms[j] = m
         nxt = jzb[j + 1] if j + 1 < min(cfg.n_xi, jzb.shape[0]) else zero
+        if laser_a2 is not None:
+            a2_nxt = laser_a2[j + 1] if j + 1 < laser_a2.shape[0] else zero
         for q in range(m):
             frac = q / m
             jz_here = jzb[j] if q == 0 else (1.0 - frac) * jzb[j] + frac * nxt
-            F = slice_fields(g, pl, n_ion, jz_here, cfg.psi_floor)
+            a2_here = None
+            if laser_a2 is not None:
+                a2_here = laser_a2[j] if q == 0 else (1.0 - frac) * laser_a2[j] + frac * a2_nxt
+            F = slice_fields(g, pl, n_ion, jz_here, cfg.psi_floor, a2_here)
             slices += 1
             hits += F.guard_hits
             if q == 0:
                 hist[:, j] = F.stack()
                 charge[j] = float(F.moments["n_star"].sum() * g.h * g.h)
+                if chi is not None:
+                    chi[j] = F.moments["kappa"]
             if j == nb - 1:
                 break
             pl, vmax, hp = push_plasma(g, pl, F, cfg.dxi0 / m, cfg.psi_floor)
@@ -537,7 +595,7 @@ def step3d(cfg: Config, plasma0: Plasma, n_ion: np.ndarray, beams: Sequence[dict
             break
         vmaxs[j] = vmax
         m = refine_m(vmax, v0, cfg.refine_k) if m_schedule is None else int(m_schedule[j + 1])
-    return StepResult(hist, ms, vmaxs, charge, slices, pushes, hits, pl)
+    return StepResult(hist, ms, vmaxs, charge, slices, pushes, hits, pl, chi)
 
 
 def wake_at(cfg: Config, hist: np.ndarray, x, y, xi):
