@@ -579,7 +579,7 @@ def run_batched(args):
 # ---------------------------------------------------------------- oracle timing
 # ---------------------------------------------------------------- nonuniform grid
 NONUNI = "nonuni255"
-NONUNI_SOURCES = ("qs_nonuniform.cu",)
+NONUNI_SOURCES = ("qs_nonuniform.cu", "qs_grid_sync.cuh")
 # FP64 flops per finest node, field and V-cycle: four Gauss-Seidel sweeps of
 # the 9-point corrected operator (65 flops a node), one residual (63) and the
 # grid transfers (13), times 4/3 for the coarse levels, plus the residual of

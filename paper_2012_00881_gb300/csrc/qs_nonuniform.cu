@@ -50,6 +50,7 @@
 #include <vector>
 
 #include "qs.h"
+#include "qs_grid_sync.cuh"
 
 namespace {
 
@@ -126,64 +127,10 @@ template <> __device__ __forceinline__ const Level<float> *hier<float>(const NuA
     return A.h32;
 }
 
-__device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
-__device__ __forceinline__ double vload(const double *p) { return *(const volatile double *)p; }
-
-__device__ __forceinline__ unsigned long long acquire_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void release_add_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Grid-wide barrier of all blocks of the launch; false once any block has
-// recorded an error (then every block leaves the kernel).
-struct GridBarrier {
-    NuScalars *sc;
-    unsigned long long *epoch;  // shared-memory count of this block's barriers
-    __device__ bool operator()(int where) const {
-        __shared__ int s_ok;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int ok = vload(&sc->err) == 0;
-            if (ok) {
-                const unsigned long long target = (*epoch + 1) * gridDim.x;
-                *epoch += 1;
-                release_add_u64(&sc->bar, 1ull);
-                const long long t0 = clock64();
-                while (acquire_u64(&sc->bar) < target) {
-                    if (vload(&sc->err) != 0) {
-                        ok = 0;
-                        break;
-                    }
-                    if (clock64() - t0 > kBarrierLimit) {
-                        if (atomicCAS(&sc->err, 0, QS_ERR_TIMEOUT) == 0) sc->err_where = where;
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-            s_ok = ok;
-        }
-        __syncthreads();
-        return s_ok != 0;
-    }
-};
-
-struct BlockSync {
-    __device__ bool operator()(int) const {
-        __syncthreads();
-        return true;
-    }
-};
-
-// Threads taking part in a phase: the whole grid, or block 0 alone.
-struct Team {
-    int t, nt;
-};
+using qsync::BlockSync;
+using qsync::Team;
+using qsync::vload;
+using GridBarrier = qsync::GridBarrier<NuScalars>;
 
 template <typename T>
 __device__ __forceinline__ T at(const T *u, int n, int i, int j) {
@@ -459,24 +406,6 @@ __device__ void coarse_solve(const Level<T> &L, const T *inv, int nrhs, Team tm)
         for (int k = 0; k < 9; ++k) s += inv[q * 9 + k] * f[k];
         L.u[9 * c + q] = s;
     }
-}
-
-__device__ void block_reduce_add(const double *vals, int nrhs, double *dst) {
-    __shared__ double red[kThreads / 32][kMaxRhs];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int c = 0; c < nrhs; ++c) {
-        double v = vals[c];
-        for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid][c] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int c = 0; c < nrhs; ++c) {
-            double s = 0.0;
-            for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w][c];
-            atomicAdd(&dst[c], s);
-        }
-    __syncthreads();
 }
 
 // Levels from..to-1: pre-smooth, residual, restrict (team `tm`, `sync`).
@@ -835,7 +764,7 @@ __global__ void __launch_bounds__(kThreads, 1) nu_solve_kernel(const __grid_cons
         epoch = 0;
     }
     __syncthreads();
-    GridBarrier gsync{A.sc, &epoch};
+    const GridBarrier gsync{A.sc, &epoch, kBarrierLimit};
     const Team grid{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x)};
     const Team blk{(int)threadIdx.x, (int)blockDim.x};
     NuScalars *sc = A.sc;
@@ -887,8 +816,8 @@ __global__ void __launch_bounds__(kThreads, 1) nu_solve_kernel(const __grid_cons
                 rn[c] += r * r;
             }
         }
-        block_reduce_add(fn, nr, sc->fnorm);
-        block_reduce_add(rn, nr, sc->norm[0]);
+        qsync::block_sum_add<kThreads>(fn, nr, sc->fnorm);
+        qsync::block_sum_add<kThreads>(rn, nr, sc->norm[0]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0)
         coarse_inverse<CORR>(H[Lc], reinterpret_cast<T *>(A.coarse_inv));
@@ -946,7 +875,7 @@ __global__ void __launch_bounds__(kThreads, 1) nu_solve_kernel(const __grid_cons
                 rn[c] += r * r;
             }
         }
-        block_reduce_add(rn, nr, sc->norm[(cyc + 1) % 3]);
+        qsync::block_sum_add<kThreads>(rn, nr, sc->norm[(cyc + 1) % 3]);
         if (!gsync(4)) return;
     }
 }
