@@ -624,14 +624,11 @@ def wake_at(cfg: Config, hist: np.ndarray, x, y, xi):
     return out
 
 
-def push_beam(cfg: Config, hist: np.ndarray, beam: dict, dt: float) -> dict:
-    """Push_Driver of Algorithm 1: one relativistic Boris step of length dt in
-    the frozen wake, E^W = e_z E_z + E_perp, B^W = e_z B_z + B_perp, with
-    E_perp = -grad(psi) - e_z x B_perp (Eqs. EoM_beam_1/2; reading 6)."""
+def boris_step(beam: dict, ex, ey, ez, bx, by, bz, dt: float) -> dict:
+    """One relativistic Boris step of length dt (half kick, rotation, half
+    kick, then the drift with the new velocity; xi = t - z advances by
+    dt (1 - v_z)) of Eqs. EoM_beam_1/2 in the given fields at the particles."""
     x, y, xi = beam["x"], beam["y"], beam["xi"]
-    ez, bz, bx, by, gx, gy = wake_at(cfg, hist, x, y, xi)
-    ex = -gx + by
-    ey = -gy - bx
     qm = beam["q_over_m"]
     hq = 0.5 * dt * qm
     ux = beam["px"] + hq * ex
@@ -656,6 +653,14 @@ def push_beam(cfg: Config, hist: np.ndarray, beam: dict, dt: float) -> dict:
     out.update(x=x + dt * ux / gam, y=y + dt * uy / gam, xi=xi + dt * (1.0 - uz / gam),
                px=ux, py=uy, pz=uz)
     return out
+
+
+def push_beam(cfg: Config, hist: np.ndarray, beam: dict, dt: float) -> dict:
+    """Push_Driver of Algorithm 1: one relativistic Boris step of length dt in
+    the frozen wake, E^W = e_z E_z + E_perp, B^W = e_z B_z + B_perp, with
+    E_perp = -grad(psi) - e_z x B_perp (Eqs. EoM_beam_1/2; reading 6)."""
+    ez, bz, bx, by, gx, gy = wake_at(cfg, hist, beam["x"], beam["y"], beam["xi"])
+    return boris_step(beam, -gx + by, -gy - bx, ez, bx, by, bz, dt)
 
 
 def beam_gamma(beam: dict) -> np.ndarray:
