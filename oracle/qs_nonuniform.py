@@ -41,6 +41,13 @@ N3. Layout: vertex-centred.  Each axis has n interior nodes plus the two walls
     difference operators below therefore drop the wall columns.
 N4. The J part of d_x(lap) moves to the right-hand side (J'); the M Psi part
     stays in the operator, so A is a 9-point, non-symmetric matrix.
+N5. Particles (the section's grids carry the whole PIC, not only the solver):
+    a particle's weight goes to the four nodes around it with linear weights
+    in physical coordinates (CIC on the node grid); weight that falls on a
+    wall node is folded into the adjacent interior node, so deposits conserve
+    charge, and the density is the deposit over the node's dual area, the
+    first and last nodes owning the whole interval to the wall.  The gather
+    uses the same weights (it is the transpose of the deposit).
 
 One library routine is used as a step: scipy's sparse LU (SuperLU) solves the
 assembled system exactly to rounding.  Everything is float64.  Arrays are
@@ -48,7 +55,8 @@ indexed [iy, ix], flattened with ix fastest.  Pinned by
 tests/test_nonuniform_pins.py (uniform-grid reduction to the 5-point scheme of
 Eq. 2D_Laplac_Uni, exactness on quadratics, second-order truncation with the
 correction and first-order without it, second-order convergence of the
-solution).
+solution; for particles, charge conservation, the gather as the deposit's
+transpose, exact bilinear gathers, and unit density from a uniform lattice).
 """
 from __future__ import annotations
 
@@ -59,6 +67,10 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 __all__ = [
+    "node_areas",
+    "cic_node_weights",
+    "deposit",
+    "gather",
     "spacings",
     "second_difference",
     "first_difference",
@@ -159,3 +171,68 @@ def solve(xn, yn, j, m=None, correction: bool = True) -> np.ndarray:
     a = operator(xn, yn, m, correction).tocsc()
     rhs = corrected_source(xn, yn, j, correction).reshape(-1)
     return spla.spsolve(a, rhs).reshape(ny, nx)
+
+
+# --------------------------------------------------------------------------
+# particles on the node grid (reading N5)
+# --------------------------------------------------------------------------
+def _dual_lengths(xn: np.ndarray) -> np.ndarray:
+    """Length each interior node owns: half of each adjacent interval, and the
+    whole interval to the wall for the first and last node."""
+    xn = np.asarray(xn, dtype=np.float64)
+    hm, hp = spacings(xn)
+    v = 0.5 * (hm + hp)
+    v[0] += 0.5 * hm[0]
+    v[-1] += 0.5 * hp[-1]
+    return v
+
+
+def node_areas(xn: np.ndarray, yn: np.ndarray) -> np.ndarray:
+    """Dual areas [ny, nx] of the interior nodes; they sum to the box area."""
+    return np.outer(_dual_lengths(yn), _dual_lengths(xn))
+
+
+def cic_node_weights(xn: np.ndarray, x: np.ndarray):
+    """(left node, weight of the right node) of each coordinate: the interval
+    [xn[k], xn[k+1]] holding it (walls included, clamped to the box) and the
+    linear weight; interior node indices, -1 / n for the walls."""
+    xn = np.asarray(xn, dtype=np.float64)
+    n = xn.size - 2
+    x = np.clip(np.asarray(x, dtype=np.float64), xn[0], xn[-1])
+    k = np.clip(np.searchsorted(xn, x, side="right") - 1, 0, n)
+    f = (x - xn[k]) / (xn[k + 1] - xn[k])
+    return k - 1, f
+
+
+def _fold(i: np.ndarray, n: int) -> np.ndarray:
+    return np.clip(i, 0, n - 1)
+
+
+def _stencil(xn, yn, x, y):
+    ix, fx = cic_node_weights(xn, x)
+    iy, fy = cic_node_weights(yn, y)
+    nx, ny = len(xn) - 2, len(yn) - 2
+    out = []
+    for dy, wy in ((0, 1.0 - fy), (1, fy)):
+        for dx, wx in ((0, 1.0 - fx), (1, fx)):
+            out.append((_fold(iy + dy, ny), _fold(ix + dx, nx), wy * wx))
+    return out
+
+
+def deposit(xn, yn, x, y, q) -> np.ndarray:
+    """Density [ny, nx] of particle weights q at (x, y) (reading N5)."""
+    nx, ny = len(xn) - 2, len(yn) - 2
+    out = np.zeros(ny * nx)
+    q = np.asarray(q, dtype=np.float64)
+    for jy, jx, w in _stencil(xn, yn, x, y):
+        out += np.bincount(jy * nx + jx, weights=q * w, minlength=ny * nx)
+    return out.reshape(ny, nx) / node_areas(xn, yn)
+
+
+def gather(u, xn, yn, x, y) -> np.ndarray:
+    """Node field u [ny, nx] at the particles, with the deposit's weights."""
+    u = np.asarray(u, dtype=np.float64)
+    out = np.zeros(len(np.atleast_1d(x)))
+    for jy, jx, w in _stencil(xn, yn, x, y):
+        out += w * u[jy, jx]
+    return out

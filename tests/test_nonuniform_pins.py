@@ -134,3 +134,52 @@ def test_rejects_bad_axes():
         nu.spacings(np.array([0.0, 1.0, 0.5, 2.0]))
     with pytest.raises(ValueError):
         nu.spacings(np.array([0.0, 1.0]))
+
+
+# ---------------------------------------------------------------- particles (reading N5)
+def _particles(xn, yn, count, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(xn[0], xn[-1], count)
+    y = rng.uniform(yn[0], yn[-1], count)
+    return x, y, rng.uniform(0.5, 1.5, count)
+
+
+def test_node_deposit_conserves_charge_and_areas_tile_the_box():
+    xn, yn = three_region_axis(31, 5.0), alternating_axis(15, 3.0, 2.5)
+    np.testing.assert_allclose(nu.node_areas(xn, yn).sum(), 10.0 * 6.0, rtol=1e-14)
+    x, y, q = _particles(xn, yn, 5000, 1)
+    n = nu.deposit(xn, yn, x, y, q)
+    np.testing.assert_allclose((n * nu.node_areas(xn, yn)).sum(), q.sum(), rtol=1e-13)
+
+
+def test_node_gather_is_the_deposit_transpose():
+    xn, yn = three_region_axis(31, 5.0), alternating_axis(15, 3.0, 2.5)
+    x, y, q = _particles(xn, yn, 3000, 2)
+    u = np.random.default_rng(3).standard_normal((15, 31))
+    lhs = (nu.gather(u, xn, yn, x, y) * q).sum()
+    rhs = (u * nu.deposit(xn, yn, x, y, q) * nu.node_areas(xn, yn)).sum()
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-13)
+
+
+def test_node_gather_reproduces_bilinear_fields_inside():
+    xn, yn = three_region_axis(31, 5.0), alternating_axis(15, 3.0, 2.5)
+    X, Y = np.meshgrid(xn[1:-1], yn[1:-1])
+    u = 0.7 * X - 1.3 * Y + 0.2 * X * Y + 0.5
+    rng = np.random.default_rng(4)
+    x = rng.uniform(xn[1], xn[-2], 500)          # between interior nodes only
+    y = rng.uniform(yn[1], yn[-2], 500)
+    np.testing.assert_allclose(nu.gather(u, xn, yn, x, y), 0.7 * x - 1.3 * y + 0.2 * x * y + 0.5,
+                               rtol=0, atol=1e-12)
+
+
+def test_node_deposit_of_a_uniform_density_is_one():
+    """A fine uniform lattice of equal weights (density 1) deposits n = 1 at
+    every node, walls included, up to the lattice's own discreteness."""
+    xn, yn = three_region_axis(31, 5.0), alternating_axis(15, 3.0, 2.5)
+    m = 1200
+    xs = xn[0] + (np.arange(m) + 0.5) * (xn[-1] - xn[0]) / m
+    ys = yn[0] + (np.arange(m) + 0.5) * (yn[-1] - yn[0]) / m
+    X, Y = np.meshgrid(xs, ys)
+    q = np.full(X.size, (xn[-1] - xn[0]) * (yn[-1] - yn[0]) / X.size)
+    n = nu.deposit(xn, yn, X.ravel(), Y.ravel(), q)
+    assert np.abs(n - 1.0).max() < 5e-3
