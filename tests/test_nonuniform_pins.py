@@ -183,3 +183,52 @@ def test_node_deposit_of_a_uniform_density_is_one():
     q = np.full(X.size, (xn[-1] - xn[0]) * (yn[-1] - yn[0]) / X.size)
     n = nu.deposit(xn, yn, X.ravel(), Y.ravel(), q)
     assert np.abs(n - 1.0).max() < 5e-3
+
+
+def _node_linear_wake_error(n):
+    """psi of the node-grid slice advance under a weak bi-Gaussian driver
+    against the linear theory of the uniform oracle's closed-form pin:
+    psi = n_b int sin(xi - xi') f(xi') dxi' (1 - lap)^-1 g, with the node
+    grid's own (1 - lap)^-1 (9-point operator, M = -1)."""
+    from oracle import qs_nonuniform_pic as P
+    hw, n_xi, nb, sr, sz, xic, length = 6.0, 192, 1e-3, 1.0, 1.0, 3.0, 9.0
+    ax = three_region_axis(n, hw)
+    G = P.NodeGrid(ax, ax)
+    X, Y = np.meshgrid(ax[1:-1], ax[1:-1])
+    gr = np.exp(-(X ** 2 + Y ** 2) / sr ** 2)
+    dxi = length / n_xi
+    xi = np.arange(n_xi) * dxi
+    jzb = nb * np.exp(-(xi - xic) ** 2 / sz ** 2)[:, None, None] * gr[None]
+    pl, n_ion = P.init_plasma_nodes(G, 4)
+    hist, _ = P.step3d_nodes(G, n_xi, dxi, pl, n_ion, jzb)
+    ghat = nu.solve(ax, ax, -gr, -np.ones_like(gr))
+    xf = np.linspace(0.0, length, 90001)
+    ff = np.exp(-(xf - xic) ** 2 / sz ** 2)
+    conv = []
+    for x0 in xi:
+        sel = xf <= x0
+        conv.append(np.trapezoid(np.sin(x0 - xf[sel]) * ff[sel], dx=xf[1] - xf[0])
+                    if sel.sum() > 1 else 0.0)
+    psi_l = nb * np.array(conv)[:, None, None] * ghat[None]
+    m = n // 6
+    return (np.linalg.norm((hist[0] - psi_l)[:, m:-m, m:-m])
+            / np.linalg.norm(psi_l[:, m:-m, m:-m]))
+
+
+@pytest.mark.slow
+def test_node_grid_slice_advance_linear_wake():
+    """The whole slice loop on the three-region node grid (deposits, the
+    9-point solves of the five fields, the push) reaches the linear beam wake
+    at second order in the spacing."""
+    e31, e63 = _node_linear_wake_error(31), _node_linear_wake_error(63)
+    assert e63 < 0.06, e63
+    assert e31 / e63 > 2.5, (e31, e63)
+
+
+def test_node_quiet_start_is_unit_density():
+    from oracle import qs_nonuniform_pic as P
+    ax = three_region_axis(31, 5.0)
+    G = P.NodeGrid(ax, alternating_axis(15, 3.0, 2.0))
+    pl, n_ion = P.init_plasma_nodes(G, 4)
+    np.testing.assert_allclose(pl.w.sum(), 10.0 * 6.0, rtol=1e-13)
+    assert np.abs(n_ion - 1.0).max() < 0.02
