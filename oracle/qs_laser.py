@@ -35,7 +35,9 @@ One library routine is used as a step: scipy's sparse LU (SuperLU) solves each
 slice's complex system exactly to rounding.  Everything is complex128 /
 float64.  Arrays are [slice, iy, ix].  Pinned by tests/test_laser_pins.py
 (unitarity without the xi coupling, the paraxial Gaussian beam's closed form,
-the group-velocity slip (chi + k_perp^2) / (2 k0^2) of a pulse in plasma).
+the group-velocity slip (chi + k_perp^2) / (2 k0^2) of a pulse in plasma, and
+the coupled step handing chi ~ 1 of a weakly perturbed plasma to the
+envelope).
 """
 from __future__ import annotations
 
@@ -45,9 +47,10 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .qs_oracle import Grid, _second_difference_1d
+from .qs_oracle import Config, Grid, _second_difference_1d, step3d
 
-__all__ = ["laplacian_matrix", "step_coefficients", "envelope_advance", "envelope_step"]
+__all__ = ["laplacian_matrix", "step_coefficients", "envelope_advance", "envelope_step",
+           "laser_step3d"]
 
 
 def laplacian_matrix(n: int, h: float) -> sp.csr_matrix:
@@ -90,3 +93,17 @@ def envelope_advance(g: Grid, a, chi, k0: float, dt: float, dxi: float, steps: i
 def envelope_step(g: Grid, a, chi, k0: float, dt: float, dxi: float):
     """One time step (see envelope_advance)."""
     return envelope_advance(g, a, chi, k0, dt, dxi, 1)
+
+
+def laser_step3d(cfg: Config, plasma0, n_ion, envelope, k0: float, dt: float, beams=(),
+                 jzb=None, m_schedule=None):
+    """One 3D step with a laser driver (Algorithm 1 with the laser): the xi
+    loop with |A|^2 of the envelope (the slice advance's laser terms), which
+    also yields chi = n_*/(1+psi) at the base slices, then one time step of
+    Eq. laser_Enve with that chi over the same slices.  Returns (the step's
+    result, the envelope at t + dt)."""
+    a2 = np.abs(np.asarray(envelope)) ** 2
+    if jzb is None and not beams:
+        jzb = np.zeros(a2.shape)
+    r = step3d(cfg, plasma0, n_ion, beams, jzb=jzb, laser_a2=a2, m_schedule=m_schedule)
+    return r, envelope_advance(cfg.grid, envelope, r.chi, k0, dt, cfg.dxi0, 1)

@@ -78,3 +78,25 @@ def test_xi_coupling_runs_from_head_to_tail():
     a = QL.envelope_advance(g, a0, np.full((60, 8, 8), 0.5), 4.0, 0.5, 0.1, 5)
     assert not a[xi < 3.0].any()
     assert np.abs(a[xi > 3.0]).max() > 0.1
+
+
+def test_laser_step_hands_the_plasma_susceptibility_to_the_envelope():
+    """A weak pulse in uniform plasma: the wake's chi = n_*/(1+psi) is 1 up to
+    O(a0^2), and the envelope then advances as it does with chi = 1, not as in
+    vacuum."""
+    from oracle import qs_oracle as Q
+    n, hw, n_xi = 16, 4.0, 48
+    cfg = Q.Config(n, -hw, hw, -hw, hw, n_xi, 0.0, 4.8, refine_k=1)
+    g = cfg.grid
+    X, Y = _centres(g)
+    xi = (np.arange(n_xi) + 0.5) * cfg.dxi0
+    env = (0.05 * np.exp(-((xi - 2.0) / 0.8) ** 2)[:, None, None]
+           * np.exp(-(X ** 2 + Y ** 2) / 2.0)[None]).astype(np.complex128)
+    pl, n_ion = Q.init_plasma(g, 4)
+    r, new = QL.laser_step3d(cfg, pl, n_ion, env, k0=3.0, dt=2.0, m_schedule=[1] * n_xi)
+    assert np.abs(r.chi - 1.0).max() < 5e-3
+    with_one = QL.envelope_advance(g, env, np.ones_like(r.chi), 3.0, 2.0, cfg.dxi0, 1)
+    vacuum = QL.envelope_advance(g, env, np.zeros_like(r.chi), 3.0, 2.0, cfg.dxi0, 1)
+    d1 = np.linalg.norm(new - with_one)
+    d0 = np.linalg.norm(new - vacuum)
+    assert d1 < 0.02 * d0, (d1, d0)
