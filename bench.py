@@ -666,7 +666,7 @@ def run_nonuniform(args):
             t1.record(stream)
             stream.synchronize()
             clocks = sampler.stop()
-        ms = max_over_ranks(t0.elapsed_time(t1)) / args.steps
+        ms = max_over_ranks(t0.elapsed_time(t1), f"cuda:{local}") / args.steps
         dur = sum(a.elapsed_time(b) for a, b, _, _ in launches) / 1e3
         flops = sum(NONUNI_FLOPS_PER_NODE_CYCLE * wl.n * wl.n * nr * cyc
                     for _, _, nr, cyc in launches)
@@ -710,7 +710,7 @@ def run_nonuniform(args):
             e2e_step()
         e1.record(stream)
         stream.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), f"cuda:{local}") / args.steps
     out = {
         "metric": "nonuniform_slice_field_solves_per_s", "value": r["value"],
         "unit": "slice field sets/s", "n_gpus": world, "steps": args.steps,
@@ -817,7 +817,7 @@ def run_laser(args):
             cycles += c
         stream.synchronize()
         clocks = sampler.stop()
-    ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in evs)) / args.steps
+    ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in evs), f"cuda:{local}") / args.steps
     slices = wl.n_xi * args.steps
     value = job_rate(slices, world, ms * args.steps / 1e3)
     flops = LASER_FLOPS_PER_CELL_CYCLE * wl.n * wl.n * cycles
@@ -840,7 +840,7 @@ def run_laser(args):
             out_pin.copy_(a, non_blocking=True)
         e1.record(stream)
         stream.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), f"cuda:{local}") / args.steps
     out = {
         "metric": "laser_xi_slices_per_s", "value": value, "unit": "laser slices/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
