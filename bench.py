@@ -45,7 +45,92 @@ def _args():
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--slices", type=int, default=0,
                    help="profiling only: truncate the window to this many base slices")
+    p.add_argument("--parity-slices", type=int, default=-1,
+                   help="base slices of the live parity check against the oracle "
+                        "(-1: the workload's default, 0: off)")
     return p.parse_args()
+
+
+# live parity: base slices of the oracle prefix that the bench compares the
+# GPU forms with (a few minutes of one host core at most, run concurrently
+# with the GPU legs): through the driver and the first bubble at 256^2
+PARITY_SLICES = {"linear64": 128, "blowout256": 256, "blowout512": 24}
+PARITY_TOL = 1e-12  # solver tolerance of the parity steps (both sides solve exactly)
+
+
+def _oracle_prefix_job(name: str, n_prefix: int, path: str):
+    """Spawned process: the oracle's history of the first n_prefix base slices
+    of workload `name`, saved to `path` (.npy) with its run time."""
+    import numpy as np
+
+    import oracle as O
+    import workloads as W
+    wl = W.workload(name)
+    beams = [W.sample_beam(b) for b in wl.beams]
+    cfg = O.config_from_workload(wl)
+    pl, n_ion = O.plasma_from_workload(wl)
+    t0 = time.perf_counter()
+    r = O.step3d(cfg, pl, n_ion, beams, n_slices=n_prefix)
+    np.save(path, r.history)
+    with open(path + ".s", "w") as f:
+        f.write(f"{time.perf_counter() - t0:.3f}")
+
+
+def _start_parity(args, rank, world):
+    """Starts the oracle prefix in a spawned process before any CUDA work."""
+    n = args.parity_slices
+    if n < 0:
+        n = PARITY_SLICES.get(args.workload, 0)
+    if n <= 0 or rank != 0 or world != 1 or args.slices > 0:
+        return None
+    import multiprocessing as mp
+    d = tempfile.mkdtemp(prefix="qs_parity_")
+    path = os.path.join(d, "oracle.npy")
+    proc = mp.get_context("spawn").Process(target=_oracle_prefix_job,
+                                          args=(args.workload, n, path), daemon=True)
+    proc.start()
+    return {"proc": proc, "path": path, "n": n, "dir": d}
+
+
+def _finish_parity(job, qs, wl, forms):
+    """Per-field relative L2 error of each form against the oracle prefix:
+    ||F_gpu - F_oracle|| / max(||F_oracle||, ||psi_oracle||) over the first
+    n base slices, from one untimed step per form solved to PARITY_TOL."""
+    import numpy as np
+    import workloads as W
+    if job is None:
+        return None
+    n = job["n"]
+    got = {}
+    beams_np = [W.sample_beam(b) for b in wl.beams]
+    for form in forms:
+        ctx = qs.Context(qs.config_from_workload(wl, precision=form, mg_tol=PARITY_TOL))
+        if wl.profile is None:
+            ctx.init_plasma(wl.ppc)
+        else:
+            ctx.init_plasma(wl.ppc, wl.profile[0], wl.profile[1])
+        st = ctx.step3d([qs.Beam(b) for b in beams_np])
+        got[form] = (ctx.fields(qs.FIELD_ALL, 0, n, device=False).numpy(), st["psi_guard_hits"])
+        ctx.close()
+    job["proc"].join(timeout=900)
+    if job["proc"].is_alive() or not os.path.exists(job["path"]):
+        job["proc"].terminate()
+        return {"slices": n, "error": "oracle prefix did not finish"}
+    ref = np.load(job["path"])
+    oracle_s = float(open(job["path"] + ".s").read())
+    import shutil
+    shutil.rmtree(job["dir"], ignore_errors=True)
+    names = ("psi", "Ez", "Bz", "Bx", "By")
+    out = {"slices": n, "xi_end": n * wl.xi_len / wl.n_xi, "mg_tol": PARITY_TOL,
+           "oracle_s": oracle_s, "bar": {"fp64": 1e-9, "fp32r": 2e-5},
+           "norm": "||F - F_oracle|| / max(||F_oracle||, ||psi_oracle||) over the prefix"}
+    scale = np.linalg.norm(ref[0])
+    for form, (g, hits) in got.items():
+        out[form] = {nm: float(np.linalg.norm(g[i] - ref[i]) /
+                               max(np.linalg.norm(ref[i]), scale, 1e-300))
+                     for i, nm in enumerate(names)}
+        out[form]["psi_guard_hits"] = int(hits)
+    return out
 
 
 SCAN = "scan48"
@@ -96,7 +181,8 @@ def _workload_desc(wl):
 
 
 # ---------------------------------------------------------------- ncu traffic
-ENGINE_SOURCES = ("qs_engine.cu", "qs_solve.cuh", "qs_mg.cuh", "qs_tile.cuh", "qs_internal.cuh")
+ENGINE_SOURCES = ("qs_engine.cuh", "qs_engine_fp64.cu", "qs_engine_fp32r.cu", "qs_solve.cuh",
+                  "qs_mg.cuh", "qs_tile.cuh", "qs_internal.cuh")
 
 
 def engine_source_hash(sources=ENGINE_SOURCES) -> str:
@@ -137,18 +223,36 @@ def measured_traffic(kernel: str, workload: str, form: str, profiles_dir: str = 
 
 
 # ---------------------------------------------------------------- roofline model
-def algorithmic_bytes(stats, wl, b: int, n_xi: int) -> float:
-    """Bytes one slice-engine launch must move at minimum (the byte model):
-    particles 14b per particle per pushed slice (5b on the last slice), grid
-    phases 50b per point per slice + 10b per point per base slice, multigrid
-    24b per component-point per V-cycle plus 8b per point per screened cycle."""
+def algorithmic_bytes(stats, wl, form: str, n_xi: int) -> float:
+    """Bytes one slice-engine launch must move at minimum (the byte model).
+
+    b = 8 (float64 form) or 4 (refined form: float32 momenta, weights, moment
+    grids and inner multigrid cycles); positions, n_*, the fields and the
+    history are float64 in both forms.
+      particles, per pushed slice: positions read twice and written once
+        (48 B), momenta read twice and written once (6b), weights read by the
+        moment and density deposits (b + 8); the last slice reads positions,
+        momenta and weights once (16 + 3b);
+      grid phases, per slice: 50 words per point, of which 21 are moment
+        grids (clears, deposits, reads in the assembly: b) and 29 float64
+        (sources, fields, gradients, kappa, guesses); per base slice the
+        history store 10 float64 words per point;
+      multigrid, per V-cycle and component: 24b per point, plus 8b per point
+        for kappa in a screened cycle; the refined form adds its float64
+        outer residual and correction, 40 B per point and component (read u,
+        r, write u, r, float32 r), and 32 B per point and component for the
+        float64 residual that starts each solve."""
+    b = 8 if form == "fp64" else 4
     nn = wl.n * wl.n
     np_ = wl.n_plasma
     slices = stats["slices"]
-    part = (14 * (slices - 1) + 5) * b * np_
-    grid = (50 * slices + 10 * n_xi) * b * nn
+    part = ((48 + 6 * b + b + 8) * (slices - 1) + (16 + 3 * b)) * np_
+    grid = ((21 * b + 29 * 8) * slices + 10 * 8 * n_xi) * nn
     v = stats["vcycles"]
-    mg = (v[0] * 24 + v[1] * 48 + v[2] * 56) * b * nn
+    comp_cycles = v[0] + 2 * v[1] + 2 * v[2]
+    mg = (comp_cycles * 24 * b + v[2] * 8 * b) * nn
+    if form != "fp64":
+        mg += (comp_cycles * 40 + 5 * slices * 32) * nn
     return float(part + grid + mg)
 
 
@@ -213,6 +317,7 @@ def run_native(args):
     import workloads as W
 
     rank, world, local = _dist_env()
+    parity_job = _start_parity(args, rank, world)  # before the first CUDA call
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -239,13 +344,9 @@ def run_native(args):
             ctx.init_plasma(wl.ppc)
         else:
             ctx.init_plasma(wl.ppc, wl.profile[0], wl.profile[1])
-        master = [qs.Beam(b, device=dev) for b in beams_np]
+        # the bunches advance from step to step (consecutive 3D steps of the
+        # run: deposit, slice loop in their frozen current, driver push)
         beams = [qs.Beam(b, device=dev) for b in beams_np]
-
-        def reset_beams():
-            for src, dst in zip(master, beams):
-                for k in qs.Beam.KEYS:
-                    dst.t[k].copy_(src.t[k])
 
         def one_step():
             st = ctx.step3d(beams)
@@ -253,7 +354,6 @@ def run_native(args):
             return st
 
         for _ in range(args.warmup):
-            reset_beams()
             one_step()
         torch.cuda.synchronize()
         if world > 1:
@@ -264,7 +364,6 @@ def run_native(args):
         vc = [0, 0, 0]
         max_m = 0
         for _ in range(args.steps):
-            reset_beams()
             flush.zero_()  # evict L2 between timed steps (outside the events)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -279,12 +378,13 @@ def run_native(args):
             pushes += st["pushes"]
             vc = [a + b for a, b in zip(vc, st["vcycles"])]
             max_m = max(max_m, st["max_m"])
-            bytes_alg += algorithmic_bytes(st, wl, 8 if form == "fp64" else 4, wl.n_xi)
+            bytes_alg += algorithmic_bytes(st, wl, form, wl.n_xi)
         clocks = sampler.stop()
         total_ms = max_over_ranks(sum(times), dev)
-        # end to end through the public API with host buffers
-        host = [{k: torch.as_tensor(b[k]).pin_memory() for k in qs.Beam.KEYS} for b in beams_np]
-        back = [{k: torch.empty_like(h[k]).pin_memory() for k in qs.Beam.KEYS} for h in host]
+        # end to end through the public API with host buffers: each step copies
+        # the bunches in from pinned host memory and their pushed state back,
+        # which the next step starts from
+        host = [{k: b.t[k].cpu().pin_memory() for k in qs.Beam.KEYS} for b in beams]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2e_slices = 0
@@ -294,9 +394,9 @@ def run_native(args):
                     db.t[k].copy_(hb[k], non_blocking=True)
             st = one_step()
             e2e_slices += st["slices"]
-            for bb, db in zip(back, beams):
+            for hb, db in zip(host, beams):
                 for k in qs.Beam.KEYS:
-                    bb[k].copy_(db.t[k], non_blocking=True)
+                    hb[k].copy_(db.t[k], non_blocking=True)
             torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         eng_s = sum(engine_ms) / 1e3
@@ -349,6 +449,8 @@ def run_native(args):
     }
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if parity_job is not None:
+        out["parity"] = _finish_parity(parity_job, qs, wl, forms)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -513,7 +615,7 @@ def run_batched(args):
         for s_, wl in zip(st, insts):
             slices += s_["slices"]
             pushes += s_["pushes"]
-            bytes_alg += algorithmic_bytes(s_, wl, 4, wl.n_xi)
+            bytes_alg += algorithmic_bytes(s_, wl, "fp32r", wl.n_xi)
     clocks = sampler.stop()
     total_ms = max_over_ranks(sum(times), dev)
     # end to end: beams from pinned host memory each step, read back after

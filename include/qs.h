@@ -111,6 +111,10 @@ typedef struct {
                                 /* state (up to 2 n_xi slices, if that fits in  */
                                 /* 40 % of free device memory), so the adjoint  */
                                 /* recomputes nothing; 0 = off                  */
+    int64_t barrier_wait_cycles;/* limit of every grid-barrier wait of the slice */
+                                /* loop, in SM clock cycles; a wait that runs   */
+                                /* out records QS_ERR_TIMEOUT and the kernel    */
+                                /* returns; 0 = default 4e9 (about 2 s)         */
 } qs_config;
 
 /* Driver-beam macroparticles: structure of arrays of float64, n entries each.
@@ -361,9 +365,11 @@ int qs_cell_sort(qs_ctx *ctx, const double *x, const double *y, const int32_t *i
  * calls share it and it keeps the last call's contents; each call clears the
  * part it uses before using it.  Calls that overlap on the GPU (on different
  * streams, or from different host threads without ordering) race on it and
- * give wrong results: order them.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture begins.
+ * give wrong results: order them.  Every call looks up the array's device
+ * address (cudaGetSymbolAddress) in the current device's current context,
+ * so a device reset or a context switch between calls is harmless; the
+ * first call on a device also loads the module there, so make that first
+ * call before any stream capture begins.
  * Errors: QS_ERR_ARG, QS_ERR_CUDA (launch or address lookup failed). */
 int qs_cell_sort_noalloc(int n, double x_min, double y_min, double h, const double *x,
                          const double *y, const int32_t *id, int64_t np, int32_t *cell,

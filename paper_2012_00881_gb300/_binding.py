@@ -50,6 +50,7 @@ class QsConfig(ctypes.Structure):
         ("omega_pct", ctypes.c_int),
         ("coarse_pre_sweeps", ctypes.c_int),
         ("checkpoint_every", ctypes.c_int),
+        ("barrier_wait_cycles", ctypes.c_int64),
     ]
 
 
@@ -163,6 +164,37 @@ def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
 
+def _check_sort_tensors(x, y, pid, out, n_cells: int, device=None):
+    """Checks the tensors of a cell sort before any launch: x, y contiguous
+    CUDA float64 of one length, pid int32 of that length, the outputs int32
+    of sizes (npart, n_cells, n_cells + 1, npart), all on one device (and on
+    `device` when given).  Raises ValueError on a mismatch."""
+    import torch
+    npart = int(x.numel()) if hasattr(x, "numel") else -1
+    dev = x.device if hasattr(x, "device") else None
+    for name, t, dt, size in (("x", x, torch.float64, npart), ("y", y, torch.float64, npart),
+                              ("pid", pid, torch.int32, npart)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"cell sort: {name} must be a torch tensor")
+        if not t.is_cuda or t.dtype != dt or not t.is_contiguous() or t.numel() != size:
+            raise ValueError(f"cell sort: {name} must be a contiguous CUDA {dt} tensor of "
+                             f"{size} entries (got {t.dtype}, {t.numel()}, cuda={t.is_cuda})")
+        if t.device != dev:
+            raise ValueError(f"cell sort: {name} is on {t.device}, x on {dev}")
+    if device is not None and dev != torch.device(device):
+        raise ValueError(f"cell sort: tensors on {dev}, the context's device is {device}")
+    if out is not None:
+        if len(out) != 4:
+            raise ValueError("cell sort: out must be (cell, count, offset, perm)")
+        for name, t, size in zip(("cell", "count", "offset", "perm"), out,
+                                 (npart, n_cells, n_cells + 1, npart)):
+            if (not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int32
+                    or not t.is_contiguous() or t.numel() != size or t.device != dev):
+                raise ValueError(f"cell sort: out {name} must be a contiguous int32 tensor of "
+                                 f"{size} entries on {dev}")
+    return npart
+
+
 class Beam:
     """Driver macroparticles as float64 CUDA tensors (caller-owned memory)."""
 
@@ -212,6 +244,7 @@ class Context:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
+        self.device = torch.device("cuda", torch.cuda.current_device())
         h = _P()
         st = self.lib.qs_create(ctypes.byref(cfg), _P(stream.cuda_stream), ctypes.byref(h))
         if st != QS_OK:
@@ -368,12 +401,12 @@ class Context:
     def cell_sort(self, x, y, pid):
         """Run the library's cell sort on CUDA tensors; returns (cell, count, offset, perm)."""
         import torch
-        n = int(x.numel())
         m = self.n * self.n
-        cell = torch.empty(n, dtype=torch.int32, device="cuda")
-        count = torch.empty(m, dtype=torch.int32, device="cuda")
-        offset = torch.empty(m + 1, dtype=torch.int32, device="cuda")
-        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        n = _check_sort_tensors(x, y, pid, None, m, device=self.device)
+        cell = torch.empty(n, dtype=torch.int32, device=x.device)
+        count = torch.empty(m, dtype=torch.int32, device=x.device)
+        offset = torch.empty(m + 1, dtype=torch.int32, device=x.device)
+        perm = torch.empty(n, dtype=torch.int32, device=x.device)
         self._check(self.lib.qs_cell_sort(self.h, _ptr(x), _ptr(y), _ptr(pid), n, _ptr(cell),
                                           _ptr(count), _ptr(offset), _ptr(perm)), "qs_cell_sort")
         return cell, count, offset, perm
@@ -388,21 +421,25 @@ def cell_sort_noalloc(n: int, x_min: float, y_min: float, h: float, x, y, pid, o
     tensors (cell, count, offset, perm); the library allocates nothing.
     Waits for the stream before returning."""
     import torch
+    if not (1 <= int(n) and int(n) * int(n) <= NOALLOC_MAX_CELLS):
+        raise ValueError(f"cell_sort_noalloc: n * n must be in [1, {NOALLOC_MAX_CELLS}]")
+    npart = _check_sort_tensors(x, y, pid, out, int(n) * int(n))
     lib = load_library()
-    npart = int(x.numel())
-    if out is None:
-        out = (torch.empty(npart, dtype=torch.int32, device=x.device),
-               torch.empty(n * n, dtype=torch.int32, device=x.device),
-               torch.empty(n * n + 1, dtype=torch.int32, device=x.device),
-               torch.empty(npart, dtype=torch.int32, device=x.device))
-    cell, count, offset, perm = out
-    st = torch.cuda.current_stream() if stream is None else stream
-    rc = lib.qs_cell_sort_noalloc(n, float(x_min), float(y_min), float(h), _ptr(x), _ptr(y),
-                                  _ptr(pid), npart, _ptr(cell), _ptr(count), _ptr(offset),
-                                  _ptr(perm), _P(st.cuda_stream))
-    if rc != QS_OK:
-        raise QsError(rc, "qs_cell_sort_noalloc: " + lib.qs_strerror(rc).decode())
-    st.synchronize()
+    # the C call uses the current device's stream and scratch array
+    with torch.cuda.device(x.device):
+        if out is None:
+            out = (torch.empty(npart, dtype=torch.int32, device=x.device),
+                   torch.empty(n * n, dtype=torch.int32, device=x.device),
+                   torch.empty(n * n + 1, dtype=torch.int32, device=x.device),
+                   torch.empty(npart, dtype=torch.int32, device=x.device))
+        cell, count, offset, perm = out
+        st = torch.cuda.current_stream(x.device) if stream is None else stream
+        rc = lib.qs_cell_sort_noalloc(n, float(x_min), float(y_min), float(h), _ptr(x), _ptr(y),
+                                      _ptr(pid), npart, _ptr(cell), _ptr(count), _ptr(offset),
+                                      _ptr(perm), _P(st.cuda_stream))
+        if rc != QS_OK:
+            raise QsError(rc, "qs_cell_sort_noalloc: " + lib.qs_strerror(rc).decode())
+        st.synchronize()
     return cell, count, offset, perm
 
 

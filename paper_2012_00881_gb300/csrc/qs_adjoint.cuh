@@ -26,6 +26,8 @@
 // treated as inactive where it did not clamp (a clamped value has no
 // derivative).  All arithmetic is float64; the transposed solves use the
 // context's multigrid (refined form: float32 inner cycles, float64 residual).
+#pragma once
+
 #include <cuda_runtime.h>
 
 #include "qs_solve.cuh"
@@ -153,7 +155,7 @@ __device__ void adj_prepare(const EngineArgs &A, const AdjArgs &D, const Slice &
         if (A.precision == QS_FP32_REFINED) {
             const float k32 = (float)kap;
             A.k32[i] = k32;
-            A.d32[i] = 1.f / ((float)(4 + nw) + (float)A.lev_h2[0] * k32);
+            A.d32[i] = 1.f / ((float)(4 + nw) + A.lev_h2f[0] * k32);
         } else {
             A.invd0[i] = 1.0 / ((double)(4 + nw) + A.lev_h2[0] * kap);
         }
@@ -530,33 +532,3 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1)
 }
 
 }  // namespace
-
-int qs_adjoint_max_blocks(int device, int precision, size_t smem_bytes, int *blocks) {
-    const void *fn = precision == QS_FP32_REFINED ? (const void *)adjoint_engine<true>
-                                                  : (const void *)adjoint_engine<false>;
-    int per_sm = 0, sms = 0;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
-        cudaSuccess)
-        return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QS_ENGINE_THREADS,
-                                                      smem_bytes) != cudaSuccess)
-        return -1;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
-        return -1;
-    *blocks = per_sm * sms;
-    return 0;
-}
-
-cudaError_t qs_launch_adjoint(cudaStream_t st, const EngineArgs &a, const AdjArgs &d,
-                              int grid_blocks, size_t smem_bytes) {
-    EngineArgs ca = a;
-    AdjArgs cd = d;
-    void *args[] = {&ca, &cd};
-    const void *fn = a.precision == QS_FP32_REFINED ? (const void *)adjoint_engine<true>
-                                                    : (const void *)adjoint_engine<false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid_blocks), dim3(QS_ENGINE_THREADS), args,
-                                       smem_bytes, st);
-}

@@ -186,6 +186,10 @@ int validate(const qs_config *cfg, char *why, size_t nwhy) {
         snprintf(why, nwhy, "checkpoint_every must be >= 0");
         return QS_ERR_ARG;
     }
+    if (cfg->barrier_wait_cycles < 0) {
+        snprintf(why, nwhy, "barrier_wait_cycles must be >= 0");
+        return QS_ERR_ARG;
+    }
     return QS_OK;
 }
 
@@ -489,7 +493,7 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
     a.nu1c = g.coarse_pre_sweeps > 0 ? g.coarse_pre_sweeps : g.pre_sweeps;
     a.omega = (g.omega_pct > 0 ? g.omega_pct : QS_DEFAULT_OMEGA_PCT) / 100.0;
     a.np = c->np;
-    a.spin_cycles = 4000000000LL;
+    a.spin_cycles = g.barrier_wait_cycles > 0 ? (long long)g.barrier_wait_cycles : 4000000000LL;
     a.x = c->x;
     a.y = c->y;
     a.px = c->px;
@@ -538,6 +542,9 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
         a.lev_n[l] = c->lev_n[l];
         const double hl = c->h * (double)(1 << l);
         a.lev_h2[l] = hl * hl;
+        a.lev_inv_h2[l] = 1.0 / (hl * hl);
+        a.lev_h2f[l] = (float)(hl * hl);
+        a.lev_inv_h2f[l] = (float)(1.0 / (hl * hl));
         a.lev[l] = c->lev[l];
         a.lev32[l] = c->lev32[l];
     }

@@ -327,38 +327,23 @@ cudaError_t qs_launch_cell_sort(cudaStream_t st, const double *x, const double *
 // insertion cursor) is the file-scope device array below, which every GPU
 // that loads this library holds until the process exits.
 // ---------------------------------------------------------------------------
-#include <atomic>
-#include <mutex>
-
 // Largest grid the allocation-free sort accepts: QS_NOALLOC_MAX_CELLS cells
 // (512 x 512), i.e. 1 MiB of int32 cursors.
 static __device__ __align__(256) int32_t g_noalloc_cursor[QS_NOALLOC_MAX_CELLS];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::atomic<int32_t *> g_cursor_addr[kMaxDevices];
-std::mutex g_cursor_mu;
-
-// Device address of g_noalloc_cursor on the current device, looked up once
-// per device (the host-side name of the array is only a stand-in, never a
-// device address).
-cudaError_t cursor_address(int dev, int32_t **out) {
-    int32_t *p = g_cursor_addr[dev].load(std::memory_order_acquire);
-    if (p) {
-        *out = p;
-        return cudaSuccess;
-    }
-    std::lock_guard<std::mutex> lock(g_cursor_mu);
-    p = g_cursor_addr[dev].load(std::memory_order_relaxed);
-    if (!p) {
-        void *addr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_cursor);
-        if (e != cudaSuccess) return e;
-        p = static_cast<int32_t *>(addr);
-        g_cursor_addr[dev].store(p, std::memory_order_release);
-    }
-    *out = p;
+// Device address of g_noalloc_cursor in the current device's current
+// context.  The host-side name of the array is only a stand-in, never a
+// device address, and the address belongs to one context: it is looked up
+// on every call (a host-side query, cheap next to the launches), so a
+// cudaDeviceReset or another context made current between calls cannot
+// leave a stale address behind.
+cudaError_t cursor_address(int32_t **out) {
+    void *addr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_cursor);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<int32_t *>(addr);
     return cudaSuccess;
 }
 
@@ -371,13 +356,8 @@ extern "C" int qs_cell_sort_noalloc(int n, double x_min, double y_min, double h,
     if (n < 1 || (int64_t)n * n > QS_NOALLOC_MAX_CELLS) return QS_ERR_ARG;
     if (!(h > 0.0) || np < 0 || np > (int64_t)0x7fffffff || !count || !offset) return QS_ERR_ARG;
     if (np > 0 && (!x || !y || !id || !cell || !perm)) return QS_ERR_ARG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return QS_ERR_CUDA;
-    }
     int32_t *cursor = nullptr;
-    if (cursor_address(dev, &cursor) != cudaSuccess) {
+    if (cursor_address(&cursor) != cudaSuccess) {
         cudaGetLastError();
         return QS_ERR_CUDA;
     }

@@ -11,6 +11,8 @@
 // grid of side <= 4 whose dense inverse is cached.  Refined form: float64
 // residual, float32 inner cycles whose grid-wide levels are staged tile by
 // tile in shared memory, float64 correction.
+#pragma once
+
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -235,7 +237,7 @@ __device__ void phase_assemble1(const EngineArgs &A, const PS<P> &Q, const doubl
         if (A.precision == QS_FP32_REFINED) {
             const float k32 = (float)kap;
             A.k32[i] = k32;
-            A.d32[i] = 1.f / ((float)(4 + nw) + (float)A.lev_h2[0] * k32);
+            A.d32[i] = 1.f / ((float)(4 + nw) + A.lev_h2f[0] * k32);
         } else {
             A.invd0[i] = 1.0 / ((double)(4 + nw) + A.lev_h2[0] * kap);
         }
@@ -547,80 +549,3 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1)
 }
 
 }  // namespace
-
-int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks) {
-    const void *fn = precision == QS_FP32_REFINED ? (const void *)slice_engine<true>
-                                                  : (const void *)slice_engine<false>;
-    int per_sm = 0, sms = 0;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
-        cudaSuccess)
-        return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QS_ENGINE_THREADS,
-                                                      smem_bytes) != cudaSuccess)
-        return -1;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
-        return -1;
-    *blocks = per_sm * sms;
-    return 0;
-}
-
-size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
-                            int tile_x, int tile_y, int nu, int nu2, size_t *block_offset,
-                            size_t *tile_offset) {
-    int lg = 0;
-    while (lg < nlev - 1 && lev_n[lg] > block_level_n) ++lg;
-    const size_t inv = (qsmg::coarse_inv_bytes(lev_n, nlev) + 255) & ~(size_t)255;
-    size_t b = precision == QS_FP32_REFINED ? qsmg::block_smem_bytes<float>(lev_n, nlev, lg, 2)
-                                            : qsmg::block_smem_bytes<double>(lev_n, nlev, lg, 2);
-    b = (b + 255) & ~(size_t)255;
-    if (block_offset) *block_offset = inv;
-    if (tile_offset) *tile_offset = b;  // relative to the block part
-    size_t total = inv + b;
-    if (precision == QS_FP32_REFINED && tile_x > 0)
-        total += qstile::tile_smem_bytes(tile_x, tile_y, nu, nu2);
-    return total + 256;
-}
-
-cudaError_t qs_launch_engine_batched(cudaStream_t st, const EngineArgs *list, int n_inst,
-                                     int precision, int team, int teams, BatchState *bs,
-                                     size_t smem_bytes) {
-    void *args[] = {(void *)&list, &n_inst, &team, &bs};
-    const void *fn = precision == QS_FP32_REFINED ? (const void *)slice_engine_batched<true>
-                                                  : (const void *)slice_engine_batched<false>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
-        cudaSuccess)
-        return cudaGetLastError();
-    return cudaLaunchCooperativeKernel(fn, dim3(team * teams), dim3(QS_ENGINE_THREADS), args,
-                                       smem_bytes, st);
-}
-
-int qs_engine_batched_max_blocks(int device, int precision, size_t smem_bytes, int *blocks) {
-    const void *fn = precision == QS_FP32_REFINED ? (const void *)slice_engine_batched<true>
-                                                  : (const void *)slice_engine_batched<false>;
-    int per_sm = 0, sms = 0;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
-        cudaSuccess)
-        return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QS_ENGINE_THREADS,
-                                                      smem_bytes) != cudaSuccess)
-        return -1;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
-        return -1;
-    *blocks = per_sm * sms;
-    return 0;
-}
-
-cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_blocks,
-                             size_t smem_bytes) {
-    EngineArgs copy = a;
-    void *args[] = {&copy};
-    const void *fn = a.precision == QS_FP32_REFINED ? (const void *)slice_engine<true>
-                                                    : (const void *)slice_engine<false>;
-    // the limit is a property of the kernel, shared by every context: set it
-    // for this launch (another context may have set a smaller one)
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid_blocks), dim3(QS_ENGINE_THREADS), args,
-                                       smem_bytes, st);
-}

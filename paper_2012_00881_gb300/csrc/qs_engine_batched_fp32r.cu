@@ -1,0 +1,5 @@
+// The refined form of slice_engine_batched in a translation unit of its own (the
+// kernels are large; separate units compile in parallel).
+#include "qs_engine.cuh"
+
+const void *qs_kernel_engine_batched_fp32r() { return (const void *)slice_engine_batched<true>; }

@@ -92,6 +92,11 @@ struct EngineArgs {
     int nlev;
     int lev_n[QS_MAX_LEV];
     double lev_h2[QS_MAX_LEV];
+    // the same spacing as constants of each storage type, computed on the
+    // host: GB300's float64 pipe runs at 1/64 of float32, so a divide or a
+    // conversion that every thread repeats costs microseconds per phase
+    double lev_inv_h2[QS_MAX_LEV];
+    float lev_h2f[QS_MAX_LEV], lev_inv_h2f[QS_MAX_LEV];
     LevelArrays lev[QS_MAX_LEV];
     int block_level_n;  // levels with side <= this are relaxed by one block
     // refined form: float32 inner hierarchy (level 0: correction e, residual r)
@@ -279,6 +284,16 @@ cudaError_t qs_launch_cell_sort(cudaStream_t st, const double *x, const double *
                                 const int32_t *id, int64_t np, int n, double x_min,
                                 double y_min, double h, int32_t *cell, int32_t *count,
                                 int32_t *offset, int32_t *cursor, int32_t *perm);
+// launch handles of the persistent kernels, one translation unit per form
+const void *qs_kernel_engine_fp64();
+const void *qs_kernel_engine_fp32r();
+const void *qs_kernel_engine_batched_fp64();
+const void *qs_kernel_engine_batched_fp32r();
+const void *qs_kernel_adjoint_fp64();
+const void *qs_kernel_adjoint_fp32r();
+const void *qs_kernel_engine(int precision);
+const void *qs_kernel_engine_batched(int precision);
+const void *qs_kernel_adjoint(int precision);
 cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_blocks,
                              size_t smem_bytes);
 cudaError_t qs_launch_engine_batched(cudaStream_t st, const EngineArgs *list, int n_inst,

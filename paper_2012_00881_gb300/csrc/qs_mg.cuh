@@ -27,6 +27,9 @@ struct Lvl {
     T *d;  // inverse diagonal 1/(4 + walls + h^2 kappa) (screened) or nullptr
     int n;
     double h2;
+    double inv_h2;  // 1 / h2
+    T h2t;          // h2 and 1 / h2 in the storage type (no per-thread
+    T inv_h2t;      // float64 divide or conversion in the sweeps)
     T omega;  // relaxation factor of the red-black sweeps (1 = Gauss-Seidel)
 };
 
@@ -135,7 +138,7 @@ __device__ __forceinline__ void gs_point(T *const u0, T *const u1, const T *cons
 template <typename T, int NC>
 __device__ void relax_half(const Lvl<T> L, int color, Thr R) {
     const int n = L.n;
-    const T h2 = T(L.h2);
+    const T h2 = L.h2t;
     T *const u0 = L.u[0];
     T *const u1 = L.u[NC - 1];
     const T *const f0 = L.f[0];
@@ -164,9 +167,9 @@ __device__ void relax_half(const Lvl<T> L, int color, Thr R) {
 template <typename T, int NC>
 __device__ void restrict_res(const Lvl<T> F, const Lvl<T> C, Thr R) {
     const int n = F.n, m = C.n;
-    const T inv_h2 = T(1.0 / F.h2);
+    const T inv_h2 = F.inv_h2t;
     const T *const k = F.k;
-    const T ch2 = T(C.h2);
+    const T ch2 = C.h2t;
     for (Walk w(R.t0, R.nt, m); w.q < m * m; w.next()) {
         const int I = w.col, J = w.row;
         const int i0 = (2 * J) * n + 2 * I;
@@ -235,7 +238,7 @@ template <typename T, int NC>
 __device__ void coarse_solve(const Lvl<T> L, double *work, CoarseInv ci) {
     const int n = L.n, m = n * n, W = 2 * m;
     if (!*ci.ready) {
-        const double inv_h2 = 1.0 / L.h2;
+        const double inv_h2 = L.inv_h2;
         double *fac = work + m * W;
         for (int e = threadIdx.x; e < m * W; e += blockDim.x) {
             const int i = e / W, j = e - i * W;
@@ -251,8 +254,12 @@ __device__ void coarse_solve(const Lvl<T> L, double *work, CoarseInv ci) {
             if (iy < n - 1) work[i * W + i + n] = -inv_h2;
         }
         __syncthreads();
+        __shared__ double s_inv_piv;
         for (int k = 0; k < m; ++k) {
-            const double inv_piv = 1.0 / work[k * W + k];
+            // one float64 divide per pivot, not one per thread
+            if (threadIdx.x == 0) s_inv_piv = 1.0 / work[k * W + k];
+            __syncthreads();
+            const double inv_piv = s_inv_piv;
             for (int i = threadIdx.x; i < m; i += blockDim.x)
                 fac[i] = (i == k) ? 0.0 : work[i * W + k] * inv_piv;
             __syncthreads();
@@ -349,6 +356,9 @@ __device__ void block_vcycle(const Hier<T> &H, int lg, int nu1, int nu2, void *s
             const int m = H.lv[l].n * H.lv[l].n;
             S[l].n = H.lv[l].n;
             S[l].h2 = H.lv[l].h2;
+            S[l].inv_h2 = H.lv[l].inv_h2;
+            S[l].h2t = H.lv[l].h2t;
+            S[l].inv_h2t = H.lv[l].inv_h2t;
             S[l].omega = H.lv[l].omega;
             for (int c = 0; c < 2; ++c) {
                 S[l].u[c] = p;

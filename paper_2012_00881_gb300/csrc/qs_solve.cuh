@@ -153,6 +153,9 @@ __device__ void hier64(const EngineArgs &A, const SolveSpec &V, Hier<double> &H)
         Lvl<double> &v = H.lv[l];
         v.n = A.lev_n[l];
         v.h2 = A.lev_h2[l];
+        v.inv_h2 = A.lev_inv_h2[l];
+        v.h2t = A.lev_h2[l];
+        v.inv_h2t = A.lev_inv_h2[l];
         v.omega = A.omega;
         for (int c = 0; c < 2; ++c) {
             v.u[c] = l == 0 ? V.u[c] : A.lev[l].u[c];
@@ -169,6 +172,9 @@ __device__ void hier32(const EngineArgs &A, const SolveSpec &V, Hier<float> &H) 
         Lvl<float> &v = H.lv[l];
         v.n = A.lev_n[l];
         v.h2 = A.lev_h2[l];
+        v.inv_h2 = A.lev_inv_h2[l];
+        v.h2t = A.lev_h2f[l];
+        v.inv_h2t = A.lev_inv_h2f[l];
         v.omega = (float)A.omega;
         for (int c = 0; c < 2; ++c) {
             v.u[c] = l == 0 ? A.e32[c] : A.lev32[l].u[c];
@@ -186,7 +192,7 @@ template <int NC>
 __device__ void relax_half_finalize(const Lvl<float> L, int color, Thr R, double *fin0,
                                     double *fin1) {
     const int n = L.n;
-    const float h2 = (float)L.h2;
+    const float h2 = L.h2t;
     float *const u0 = L.u[0];
     float *const u1 = L.u[NC - 1];
     const float *const f0 = L.f[0];
@@ -344,7 +350,7 @@ template <int NC>
 __device__ void residual_norm(const EngineArgs &A, const SolveSpec &V, double *out, Thr T,
                               bool to32, float *const *r32) {
     const int n = A.N;
-    const double inv_h2 = 1.0 / A.lev_h2[0];
+    const double inv_h2 = A.lev_inv_h2[0];
     const double *const kap = V.screened ? A.kap : nullptr;
     const double *const u0 = V.u[0];
     const double *const u1 = V.u[NC - 1];
@@ -399,22 +405,32 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
         if (threadIdx.x == 0) inv_ready[1] = 0;
         __syncthreads();
     }
-    double fn[2] = {0.0, 0.0};
-    bool any_zero = false, all_zero = true;
-    for (int c = 0; c < V.nc; ++c) {
-        fn[c] = vload(&sc->fnorm[V.kind][c]);
-        if (fn[c] == 0.0) any_zero = true;
-        else all_zero = false;
+    // The scalar bookkeeping of the solve (source norms, the convergence
+    // test) is done by thread 0 alone and broadcast through shared memory:
+    // float64 divides and square roots repeated by every thread would cost
+    // microseconds on GB300's float64 pipe.
+    __shared__ double s_fn[2];
+    __shared__ int s_zero_mask, s_conv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int mask = 0;
+        for (int c = 0; c < V.nc; ++c) {
+            s_fn[c] = vload(&sc->fnorm[V.kind][c]);
+            if (s_fn[c] == 0.0) mask |= 1 << c;
+        }
+        s_zero_mask = mask;
     }
+    __syncthreads();
+    const int zero_mask = s_zero_mask;
     const Thr T = grid_thr(bid, nblk);
-    if (any_zero) {
+    if (zero_mask) {
         const int nn = A.N * A.N;
         for (int c = 0; c < V.nc; ++c)
-            if (fn[c] == 0.0)
+            if (zero_mask & (1 << c))
                 for (int k = T.t0; k < nn; k += T.nt) V.u[c][k] = 0.0;
         SYNC(20);
     }
-    if (all_zero) return true;
+    if (zero_mask == (1 << V.nc) - 1) return true;
     __shared__ Hier<double> H64;
     __shared__ Hier<float> H32;
     __syncthreads();
@@ -422,9 +438,8 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
     else hier64(A, V, H64);
     __syncthreads();
     bool conv = false;
-    double rel = 0.0;
+    double rel = 0.0;  // thread 0 only
     int it = 0;
-    const double fl = 1e-13 / A.lev_h2[0];
     bool norms_ready = false;  // the last cycle already produced this slot's norms
     // The fused residual update writes the next float32 right-hand side into
     // the other buffer of a pair: the current one is still read as halo by
@@ -439,17 +454,25 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
                     for (int e = 0; e < 4; ++e) sc->rnorm[(slot + 2) & 3][e] = 0.0;
                 SYNC(21);
             }
-            conv = true;
-            rel = 0.0;
-            for (int c = 0; c < V.nc; ++c) {
-                if (fn[c] == 0.0) continue;
-                const double rn = vload(&sc->rnorm[slot & 3][c]);
-                const double un = vload(&sc->rnorm[slot & 3][2 + c]);
-                double thr = fmax(A.mg_tol * A.mg_tol * fn[c], A.mg_atol * A.mg_atol);
-                thr = fmax(thr, fl * fl * un);
-                if (rn > thr) conv = false;
-                rel = fmax(rel, sqrt(rn / fn[c]));
+            if (threadIdx.x == 0) {
+                const double fl = 1e-13 * A.lev_inv_h2[0];
+                int cv = 1;
+                rel = 0.0;
+                for (int c = 0; c < V.nc; ++c) {
+                    const double fn = s_fn[c];
+                    if (fn == 0.0) continue;
+                    const double rn = vload(&sc->rnorm[slot & 3][c]);
+                    const double un = vload(&sc->rnorm[slot & 3][2 + c]);
+                    double thr = fmax(A.mg_tol * A.mg_tol * fn, A.mg_atol * A.mg_atol);
+                    thr = fmax(thr, fl * fl * un);
+                    if (rn > thr) cv = 0;
+                    rel = fmax(rel, sqrt(rn / fn));
+                }
+                s_conv = cv;
             }
+            __syncthreads();
+            conv = s_conv != 0;
+            __syncthreads();  // s_conv is rewritten by the next test
             ++slot;
             if (conv || it >= A.mg_max_vcycles) break;
         }
@@ -460,7 +483,7 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
                                    {A.r64[0], A.r64[V.nc - 1]},
                                    {A.r32[1 - rbuf][0], A.r32[1 - rbuf][V.nc - 1]},
                                    V.screened ? A.kap : nullptr,
-                                   1.0 / A.lev_h2[0]};
+                                   A.lev_inv_h2[0]};
             double *nout = sc->rnorm[slot & 3], *nclr = sc->rnorm[(slot + 2) & 3];
             if (V.nc == 1)
                 ok = A.tile_x > 0

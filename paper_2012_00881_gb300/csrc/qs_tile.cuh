@@ -218,7 +218,7 @@ __device__ void down_level(const Lvl<float> F, const Lvl<float> C, int nu1, int 
     const int n = F.n, m = C.n;
     const int H = 2 * nu1 + 1;
     const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
-    const float h2 = (float)F.h2, inv_h2 = (float)(1.0 / F.h2), ch2 = (float)C.h2;
+    const float h2 = F.h2t, inv_h2 = F.inv_h2t, ch2 = C.h2t;
     const bool scr = F.k != nullptr;
     const float *const gf0 = F.f[0];
     const float *const gf1 = F.f[NC - 1];
@@ -407,7 +407,7 @@ __device__ void up_cascade_fused(const qsmg::Hier<float> &Hh, int lg, const floa
             const Region g = cascade_region(Hh, l, tx0, ty0, TX, TY, nu2);
             const CascadeSmem t = cascade_layout(sm, g.R, TX, TY, nu2);
             stage_cascade<NC>(F, g, t, src0, src1, sox, soy, sp, Hh.lv[l + 1].n);
-            staged_sweeps<NC>(g, F.n, (float)F.h2, t.su0, t.su1, t.sf0, t.sf1,
+            staged_sweeps<NC>(g, F.n, F.h2t, t.su0, t.su1, t.sf0, t.sf1,
                               F.d ? t.sd : nullptr, 2 * nu2, F.omega);
             // keep the window that the next finer region prolongs from
             const Region gf = cascade_region(Hh, l - 1, tx0, ty0, TX, TY, nu2);
@@ -447,7 +447,7 @@ __device__ void up_cascade_fused(const qsmg::Hier<float> &Hh, int lg, const floa
         }
         stage_cascade<NC>(F, g, t, src0, src1, sox, soy, sp, Hh.lv[1].n);
         mark(65);
-        staged_sweeps<NC>(g, n, (float)F.h2, t.su0, t.su1, t.sf0, t.sf1, F.d ? t.sd : nullptr,
+        staged_sweeps<NC>(g, n, F.h2t, t.su0, t.su1, t.sf0, t.sf1, F.d ? t.sd : nullptr,
                           2 * nu2, F.omega);
         mark(66);
         const int RX = g.RX;

@@ -24,7 +24,7 @@ class _Problem:
     Lorentz factor, the witness, dt and the profile's radius."""
 
     def __init__(self, ctx: "B.Context", z, gamma: float, witness: "B.Beam", dt: float,
-                 ppc: int, r_max: float, checkpoint_every: int = 0):
+                 ppc: int, r_max: float, checkpoint_every: int = 0, schedule=None):
         self.ctx = ctx
         self.z = z
         self.gamma = float(gamma)
@@ -33,6 +33,8 @@ class _Problem:
         self.ppc = int(ppc)
         self.r_max = float(r_max)
         self.checkpoint_every = int(checkpoint_every)
+        # sub-step counts per base interval held fixed (None: the adaptive rule)
+        self.schedule = None if schedule is None else [int(v) for v in schedule]
 
 
 class WitnessGain(torch.autograd.Function):
@@ -43,7 +45,7 @@ class WitnessGain(torch.autograd.Function):
         c = prob.ctx
         c.init_plasma(prob.ppc, tb, prob.r_max)
         drv = B.bigaussian_beam(th, prob.z, prob.gamma)
-        c.step3d([drv, prob.witness])
+        c.step3d([drv, prob.witness], schedule=prob.schedule)
         gain = c.beam_gain(prob.witness, prob.dt)
         fctx.prob = prob
         fctx.th = th
@@ -67,7 +69,9 @@ class WitnessGain(torch.autograd.Function):
 
 
 def witness_gain(ctx: "B.Context", theta, table, z, gamma: float, witness: "B.Beam", dt: float,
-                 ppc: int, r_max: float, checkpoint_every: int = 0):
-    """L(theta, table) as a differentiable torch scalar (float64, CPU)."""
-    prob = _Problem(ctx, z, gamma, witness, dt, ppc, r_max, checkpoint_every)
+                 ppc: int, r_max: float, checkpoint_every: int = 0, schedule=None):
+    """L(theta, table) as a differentiable torch scalar (float64, CPU).  With
+    `schedule` (n_xi sub-step counts) the forward step replays it instead of
+    choosing sub-steps adaptively; the loss is then smooth in its inputs."""
+    prob = _Problem(ctx, z, gamma, witness, dt, ppc, r_max, checkpoint_every, schedule)
     return WitnessGain.apply(theta, table, prob)

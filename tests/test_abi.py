@@ -121,3 +121,19 @@ def test_laser_arguments_rejected_without_gpu(lib):
     assert l.qs_laser_create(16, 4.0, 4, 3.0, 0.5, 0.1, None, None) == qs.QS_ERR_ARG
     assert l.qs_laser_advance(None, None, None, 1, 1e-10, 10, None, None) == qs.QS_ERR_ARG
     l.qs_laser_destroy(None)
+
+
+def test_sort_bindings_reject_host_tensors_and_oversized_grids():
+    """The sort bindings check their tensors before any library call, so a
+    wrong tensor never reaches a kernel (CPU: no CUDA is needed to fail)."""
+    import torch
+
+    import paper_2012_00881_gb300 as qs
+    x = torch.zeros(10, dtype=torch.float64)
+    pid = torch.arange(10, dtype=torch.int32)
+    with pytest.raises(ValueError):  # host tensors
+        qs.cell_sort_noalloc(4, -1.0, -1.0, 0.5, x, x, pid)
+    with pytest.raises(ValueError):  # more cells than the fixed scratch holds
+        qs.cell_sort_noalloc(513, -1.0, -1.0, 0.5, x, x, pid)
+    with pytest.raises(ValueError):
+        qs.cell_sort_noalloc(4, -1.0, -1.0, 0.5, [0.0] * 10, x, pid)

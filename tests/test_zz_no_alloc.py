@@ -61,6 +61,30 @@ def test_noalloc_cell_sort_matches_context_sort_twice(qs):
         for a, b, name in zip(got, ref, ("cell", "count", "offset", "perm")):
             assert np.array_equal(a, b), (seed, name)
         assert got[2][-1] == npart
+        # and directly against the oracle's counting sort (ties by id)
+        import oracle as O
+        want = O.cell_sort(xh, yh, ph, O.Grid.square(n, L))
+        for a, b, name in zip(got, want, ("cell", "count", "offset", "perm")):
+            assert np.array_equal(a.astype(np.int64), np.asarray(b, dtype=np.int64)), (seed, name)
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_launch(qs):
+    import torch
+    x = torch.zeros(100, dtype=torch.float64, device="cuda")
+    pid = torch.arange(100, dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):  # float32 positions
+        qs.cell_sort_noalloc(8, -1.0, -1.0, 0.25, x.float(), x, pid)
+    with pytest.raises(ValueError):  # ids of another length
+        qs.cell_sort_noalloc(8, -1.0, -1.0, 0.25, x, x, pid[:50])
+    short = (torch.empty(100, dtype=torch.int32, device="cuda"),
+             torch.empty(10, dtype=torch.int32, device="cuda"),
+             torch.empty(65, dtype=torch.int32, device="cuda"),
+             torch.empty(100, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):  # count shorter than n * n
+        qs.cell_sort_noalloc(8, -1.0, -1.0, 0.25, x, x, pid, out=short)
+    with pytest.raises(ValueError):  # non-contiguous
+        qs.cell_sort_noalloc(8, -1.0, -1.0, 0.25, torch.zeros(200, dtype=torch.float64,
+                                                              device="cuda")[::2], x, pid)
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(qs):
