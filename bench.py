@@ -1099,10 +1099,442 @@ def run_reference_laser(args, world):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------- nonuniform slice loop
+NUPIC = "nupic255"
+
+
+def _nupic_inputs():
+    """The node-grid slice loop of Sec. "Multigrid Solver with Nonuniform
+    Grids" against the uniform grid it replaces: 255^2 nodes on the
+    three-region axis over [-12.5, 12.5] (spacing 0.045 on the axis to 0.136
+    outside), and 512^2 uniform cells of 0.05 over [-12.8, 12.8]; the driver
+    of the 256^2 blowout (n_b = 5, sigma_r = 0.3, sigma_z = 0.7, xi_c = 2.1),
+    4 particles per cell, 256 base slices over a 3.0 window (through the
+    driver and the front of the bubble)."""
+    from workloads.nonuniform import driver_current_nodes, three_region_axis
+    import workloads as W
+    ax = three_region_axis(255, 12.5)
+    n_xi, length = 256, 3.0
+    jzb = driver_current_nodes(ax, ax, n_xi, length, 5.0, 0.3, 0.7, 2.1)
+    drv = W.workload("blowout256").beams[0]
+    uni = W.Workload(name="uniform512", n=512, half_width=12.8, n_xi=n_xi, xi_len=length,
+                     ppc=4, beams=(drv,))
+    return ax, n_xi, length, jzb, uni
+
+
+def run_nupic(args):
+    import torch
+
+    import paper_2012_00881_gb300 as qs
+    import workloads as W
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    ax, n_xi, length, jzb_np, uni = _nupic_inputs()
+    form = "fp32r" if args.form == "both" else args.form
+    jzb = torch.tensor(jzb_np, device=dev)
+    pic = qs.NonuniformPIC(ax, ax, n_xi, length, precision=form)
+    pic.init_plasma(4)
+    for _ in range(args.warmup):
+        pic.step3d(jzb, tol=1e-10)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    t0 = time.perf_counter()
+    slices, ms_dev, vc = 0, 0.0, [0, 0, 0]
+    for _ in range(args.steps):
+        _, st = pic.step3d(jzb, tol=1e-10)
+        slices += st["slices"]
+        ms_dev += st["gpu_ms"]
+        vc = [a + b for a, b in zip(vc, st["vcycles"])]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    total_s = max_over_ranks(ms_dev / 1e3, dev)
+    value = job_rate(slices, world, total_s)
+    # end to end: the driver current in from pinned host memory, the wake out
+    jz_host = torch.tensor(jzb_np).pin_memory()
+    hist_host = torch.empty((5,) + tuple(jzb_np.shape), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        jzb.copy_(jz_host, non_blocking=True)
+        hist, _ = pic.step3d(jzb, tol=1e-10)
+        hist_host.copy_(hist, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t1
+    pic.close()
+    # the uniform 512^2 engine on the same box, driver and window
+    ctx = qs.Context(qs.config_from_workload(uni, precision=form))
+    ctx.init_plasma(uni.ppc)
+    beams = [qs.Beam(W.sample_beam(b), device=dev) for b in uni.beams]
+    ctx.step3d(beams)
+    u_ms, u_sl = 0.0, 0
+    for _ in range(args.steps):
+        st = ctx.step3d(beams)
+        u_ms += st["gpu_ms"]
+        u_sl += st["slices"]
+    ctx.close()
+    if rank != 0:
+        return
+    out = {"metric": "nonuniform_xi_slices_per_s", "value": value, "unit": "slices/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 particles, " + form + " solves",
+           "data": "synthetic",
+           "config": {"workload": f"{NUPIC}: 255^2 nodes, three-region axis on [-12.5,12.5], "
+                                  f"{n_xi} slices over {length}, 4 ppc (262,144), bi-Gaussian "
+                                  f"driver n_b=5 sigma_r=0.3 sigma_z=0.7 as j_z on the nodes",
+                      "form": form, "l2": "history larger than L2"},
+           "vcycles_per_step": [v / args.steps for v in vc],
+           "wall_ms_per_step": wall * 1e3 / args.steps,
+           "uniform_512": {"value": u_sl / (u_ms / 1e3), "unit": "slices/s",
+                           "config": "512^2 cells of 0.05 on [-12.8,12.8], same driver "
+                                     "(500k particles), window and slices, " + form},
+           "e2e": {"value": slices * world / e2e_s, "unit": "slices/s",
+                   "h2d_bytes_per_step": jzb_np.nbytes, "d2h_bytes_per_step": 5 * jzb_np.nbytes},
+           "roofline": None,
+           "gpu_launches": None, "clocks": clocks}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = nupic_cpu_baseline(args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+
+
+def nupic_cpu_baseline(seconds: float):
+    """The oracle's node-grid slice loop on the first base slices."""
+    import oracle as O  # noqa: F401  (package import)
+    from oracle import qs_nonuniform_pic as P
+    ax, n_xi, length, jzb, _ = _nupic_inputs()
+    G = P.NodeGrid(ax, ax)
+    pl, n_ion = P.init_plasma_nodes(G, 4)
+    n = 1
+    while True:
+        t0 = time.perf_counter()
+        P.step3d_nodes(G, n, length / n_xi, pl, n_ion, jzb[:n])
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * seconds or n >= 16:
+            break
+        n = min(16, max(n + 1, int(n * max(2.0, 0.5 * seconds / max(dt, 1e-3)))))
+    return {"value": n / dt, "unit": "slices/s", "cores": 1, "kind": "oracle",
+            "sample": f"the first {n} base slices of {NUPIC} (scipy sparse LU per solve), "
+                      f"FP64, single thread"}
+
+
+# ---------------------------------------------------------------- DLA driver push
+DLA = "dla256"
+DLA_NSUB = 50  # sub-steps per laser time step (the paper's DLA comparison uses 50)
+
+
+def run_dla(args):
+    """The driver push in the laser's own fields (qs_push_beam_dla): a witness
+    of 200,000 electrons (gamma = 20, sigma_r = 0.5, 1.0 behind the pulse
+    centre) pushed by one laser time step of 5 in 50 sub-steps, in the wake
+    and the envelope of one laser-driven step of laserwake256 (the envelope
+    at t and after its step)."""
+    import torch
+
+    import paper_2012_00881_gb300 as qs
+    import workloads as W
+    from workloads.laser import gaussian_pulse
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    lw, wl = _laserwake_inputs()
+    ctx = qs.Context(qs.config_from_workload(wl, precision="fp32r"))
+    ctx.init_plasma(wl.ppc)
+    lz = qs.LaserEnvelope(lw.n, lw.width, lw.n_xi, lw.k0, lw.dt, lw.dxi)
+    env0 = torch.tensor(gaussian_pulse(lw), device=dev)
+    env1 = env0.clone()
+    ctx.laser_step3d(lz, env1, tol=lw.tol)  # the wake, and the envelope at t + dt
+    spec = W.BeamSpec(amplitude=0.05, sigma_x=0.5, sigma_y=0.5, sigma_z=0.5,
+                      xi_c=lw.xi_c + 1.0, n_particles=200_000, seed=11, gamma=20.0)
+    wit = W.sample_beam(spec)
+    beam = qs.Beam(wit, device=dev)
+    master = {k: v.clone() for k, v in beam.t.items()}
+
+    def reset():
+        for k in qs.Beam.KEYS:
+            beam.t[k].copy_(master[k])
+
+    for _ in range(args.warmup):
+        reset()
+        ctx.push_beam_dla([beam], lw.dt, env0, env1, lw.k0, DLA_NSUB)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.push_beam_dla([beam], lw.dt, env0, env1, lw.k0, DLA_NSUB)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    ms = max_over_ranks(sum(times), dev) / args.steps
+    subs = spec.n_particles * DLA_NSUB
+    # float64 work per particle sub-step: two envelope gathers (8 points of
+    # A and its three differences, 2 complex values each), the wake gather
+    # (8 points, 6 values), the carrier, the fields and the Boris step
+    flops_per_sub = 2 * 8 * 4 * 2 * 4 + 8 * 6 * 3 + 60
+    achieved = subs * flops_per_sub / (ms / 1e3) / 1e9
+    # end to end: the witness in from pinned host memory and back
+    host = {k: master[k].cpu().pin_memory() for k in qs.Beam.KEYS}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for k in qs.Beam.KEYS:
+            beam.t[k].copy_(host[k], non_blocking=True)
+        ctx.push_beam_dla([beam], lw.dt, env0, env1, lw.k0, DLA_NSUB)
+        for k in qs.Beam.KEYS:
+            host[k].copy_(beam.t[k], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    lz.close()
+    ctx.close()
+    if rank != 0:
+        return
+    out = {"metric": "dla_particle_substeps_per_s", "value": job_rate(subs, world, ms / 1e3),
+           "unit": "particle sub-steps/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{DLA}: 200,000 witness electrons (gamma 20), one laser "
+                                  f"time step of {lw.dt} in {DLA_NSUB} sub-steps, in the wake "
+                                  f"and envelopes of one laserwake256 step"},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": 1250.0,
+                        "unit": "GFLOP/s (FP64)", "frac": achieved / 1250.0, "traffic": None,
+                        "peak_source": "nominal: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2"},
+           "e2e": {"value": subs * args.steps / e2e_s, "unit": "particle sub-steps/s",
+                   "h2d_bytes_per_step": 7 * 8 * spec.n_particles,
+                   "d2h_bytes_per_step": 7 * 8 * spec.n_particles},
+           "gpu_launches": args.steps, "clocks": clocks}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = dla_cpu_baseline(args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+
+
+def dla_cpu_baseline(seconds: float):
+    """The oracle's sub-cycled push (qs_dla.push_beam_dla) of a sample of the
+    witness in a synthetic wake and the same envelope, on one host core."""
+    import numpy as np
+
+    import oracle as O
+    from oracle import qs_dla as D
+    import workloads as W
+    from workloads.laser import gaussian_pulse
+    lw, wl = _laserwake_inputs()
+    cfg = O.config_from_workload(wl)
+    env = gaussian_pulse(lw)
+    hist = np.zeros((5, wl.n_xi, wl.n, wl.n))
+    n = 200
+    while True:
+        spec = W.BeamSpec(amplitude=0.05, sigma_x=0.5, sigma_y=0.5, sigma_z=0.5,
+                          xi_c=lw.xi_c + 1.0, n_particles=n, seed=11, gamma=20.0)
+        b = W.sample_beam(spec)
+        t0 = time.perf_counter()
+        D.push_beam_dla(cfg, hist, env, env, lw.k0, b, lw.dt, DLA_NSUB)
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * seconds or n >= 200_000:
+            break
+        n = min(200_000, int(n * max(2.0, 0.5 * seconds / max(dt, 1e-3))))
+    return {"value": n * DLA_NSUB / dt, "unit": "particle sub-steps/s", "cores": 1,
+            "kind": "oracle", "sample": f"{n} particles, {DLA_NSUB} sub-steps, numpy FP64, "
+                                        f"single thread"}
+
+
+# ---------------------------------------------------------------- laser-driven step
+LASERWAKE = "laserwake256"
+
+
+def _laserwake_inputs():
+    """The laser-driven 3D step: the 256^2 laser geometry (box 24, 256 slices
+    of 0.08, k0 = 20, dt = 5) with a uniform plasma of 4 particles per cell,
+    driven by the Gaussian envelope a0 = 2, w0 = 3, sigma_xi = 2 centred 4
+    behind the head (the laser blowout of the paper's Table 1 scaled to this
+    grid) and no beam."""
+    import workloads as W
+    from workloads.laser import laser_workload
+    lw = laser_workload(LASER)
+    wl = W.Workload(name=LASERWAKE, n=lw.n, half_width=lw.width / 2, n_xi=lw.n_xi,
+                    xi_len=lw.n_xi * lw.dxi, ppc=4, beams=())
+    return lw, wl
+
+
+def run_laserwake(args):
+    """One laser-driven 3D step per bench step (qs_laser_step3d): the slice
+    loop with the laser terms (|A|^2 in gamma, the ponderomotive force, the
+    source term, chi out), then one time step of the envelope with that chi;
+    the envelope carries over from step to step."""
+    import torch
+
+    import paper_2012_00881_gb300 as qs
+    from workloads.laser import gaussian_pulse
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    lw, wl = _laserwake_inputs()
+    env0 = torch.tensor(gaussian_pulse(lw))
+    forms = ["fp64", "fp32r"] if args.form == "both" else [args.form]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    results = {}
+    for form in forms:
+        ctx = qs.Context(qs.config_from_workload(wl, precision=form))
+        ctx.init_plasma(wl.ppc)
+        lz = qs.LaserEnvelope(lw.n, lw.width, lw.n_xi, lw.k0, lw.dt, lw.dxi)
+        a = env0.to(dev)
+        for _ in range(args.warmup):
+            ctx.laser_step3d(lz, a, tol=lw.tol)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        times, wake_ms, slices, bytes_alg, env_cycles = [], 0.0, 0, 0.0, 0
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = ctx.laser_step3d(lz, a, tol=lw.tol)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            wake_ms += st["gpu_ms"]
+            slices += st["slices"]
+            env_cycles += st["env_cycles"]
+            bytes_alg += algorithmic_bytes(st, wl, form, wl.n_xi)
+        clocks = sampler.stop()
+        total_ms = max_over_ranks(sum(times), dev)
+        # end to end: the envelope from pinned host memory and back every step
+        host = a.cpu().pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_slices = 0
+        for _ in range(args.steps):
+            a.copy_(host, non_blocking=True)
+            st = ctx.laser_step3d(lz, a, tol=lw.tol)
+            host.copy_(a, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_slices += st["slices"]
+        e2e_s = time.perf_counter() - t0
+        achieved = bytes_alg / (wake_ms / 1e3) / 1e9
+        results[form] = dict(
+            value=job_rate(slices, world, total_ms / 1e3), ms_per_step=total_ms / args.steps,
+            wake_ms_per_step=wake_ms / args.steps,
+            envelope_ms_per_step=(total_ms - wake_ms) / args.steps,
+            env_cycles_per_step=env_cycles / args.steps,
+            roofline={"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                      "frac": achieved / hbm_peak, "traffic": None, "kernel": "slice_engine",
+                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+            e2e={"value": e2e_slices * world / e2e_s, "unit": "slices/s",
+                 "h2d_bytes_per_step": env0.numel() * 16,
+                 "d2h_bytes_per_step": env0.numel() * 16},
+            clocks=clocks)
+        lz.close()
+        ctx.close()
+    if rank != 0:
+        return
+    main = "fp32r" if "fp32r" in results else forms[0]
+    r = results[main]
+    out = {"metric": "laser_driven_xi_slices_per_s", "value": r["value"], "unit": "slices/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if main == "fp64" else "f32+f64",
+           "data": "synthetic",
+           "config": {"workload": f"{LASERWAKE}: 256^2 on [-12,12]^2, 256 slices of 0.08, "
+                                  f"4 ppc (262,144), laser a0=2 w0=3 sigma_xi=2 xi_c=4, "
+                                  f"k0=20, dt=5; a step = the wake with the laser terms, "
+                                  f"then one envelope time step",
+                      "form": main, "l2": "history and envelope larger than L2"},
+           "roofline": r["roofline"], "e2e": r["e2e"], "gpu_launches": args.steps * 3,
+           "clocks": r["clocks"],
+           "forms": {k: {kk: v[kk] for kk in ("value", "ms_per_step", "wake_ms_per_step",
+                                               "envelope_ms_per_step", "env_cycles_per_step")}
+                     for k, v in results.items()}}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = laserwake_cpu_baseline(args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+
+
+def laserwake_cpu_baseline(seconds: float):
+    """The oracle's laser-driven wake (step3d with laser_a2) on the first base
+    slices, grown until about `seconds` of one host core."""
+    import numpy as np
+
+    import oracle as O
+    from workloads.laser import gaussian_pulse
+    lw, wl = _laserwake_inputs()
+    a2 = np.abs(gaussian_pulse(lw)) ** 2
+    cfg = O.config_from_workload(wl)
+    pl, n_ion = O.plasma_from_workload(wl)
+    n = 2
+    while True:
+        t0 = time.perf_counter()
+        r = O.step3d(cfg, pl, n_ion, [], jzb=np.zeros((n + 1, wl.n, wl.n)), n_slices=n,
+                     laser_a2=a2)
+        dt = time.perf_counter() - t0
+        if dt > 0.25 * seconds or n >= wl.n_xi:
+            break
+        n = min(wl.n_xi, max(n + 1, int(n * max(2.0, 0.5 * seconds / max(dt, 1e-3)))))
+    return {"value": r.slices / dt, "unit": "slices/s", "cores": 1, "kind": "oracle",
+            "sample": f"the laser-driven wake of the first {n} base slices of {LASERWAKE}, "
+                      f"numpy/scipy FP64, single thread (the envelope step excluded)"}
+
+
+def _reference_line(metric: str, workload: str, b: dict, ms_per_step: float, world: int,
+                    args) -> str:
+    return json.dumps({"impl": "reference", "metric": metric, "value": b["value"],
+                       "unit": b["unit"], "n_gpus": world, "steps": args.steps,
+                       "warmup": args.warmup, "ms_per_step": ms_per_step,
+                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                       "dtype": "f64", "data": "synthetic",
+                       "config": {"workload": workload, "form": "oracle"}, "cpu_baseline": b,
+                       "e2e": {"value": b["value"], "unit": b["unit"], "h2d_bytes_per_step": 0,
+                               "d2h_bytes_per_step": 0}})
+
+
 if __name__ == "__main__":
     a = _args()
-    if a.impl == "reference":
+    if a.impl == "reference" and a.workload == DLA:
+        rank, world, _ = _dist_env()
+        if rank == 0:
+            b = dla_cpu_baseline(a.cpu_seconds)
+            print(_reference_line("dla_particle_substeps_per_s", DLA, b,
+                                  200_000 * DLA_NSUB * 1e3 / b["value"], world, a), flush=True)
+    elif a.impl == "reference" and a.workload in (LASERWAKE, NUPIC):
+        rank, world, _ = _dist_env()
+        if rank == 0:
+            if a.workload == LASERWAKE:
+                b = laserwake_cpu_baseline(a.cpu_seconds)
+                print(_reference_line("laser_driven_xi_slices_per_s", LASERWAKE, b,
+                                      256e3 / b["value"], world, a), flush=True)
+            else:
+                b = nupic_cpu_baseline(a.cpu_seconds)
+                print(_reference_line("nonuniform_xi_slices_per_s", NUPIC, b,
+                                      256e3 / b["value"], world, a), flush=True)
+    elif a.impl == "reference":
         run_reference(a)
+    elif a.workload == LASERWAKE:
+        run_laserwake(a)
+    elif a.workload == NUPIC:
+        run_nupic(a)
+    elif a.workload == DLA:
+        run_dla(a)
     elif a.workload == SCAN:
         run_batched(a)
     elif a.workload == GRAD:

@@ -82,10 +82,11 @@ typedef struct {
     int mg_max_vcycles;         /* per solve; exceeding it -> NOT_CONVERGED     */
     double psi_floor;           /* 1+psi is clamped to >= psi_floor             */
     int64_t max_psi_guard_hits; /* -1: unlimited                                */
-    int sort_every;             /* accepted, >= 0; the slice loop keeps the     */
-                                /* lattice order, which is already cell order   */
-                                /* at the head of the window (qs_cell_sort      */
-                                /* gives the sort on demand)                    */
+    int sort_every;             /* > 0: every this many base slices the slice   */
+                                /* loop reorders the plasma by (cell, id), the  */
+                                /* order of qs_cell_sort (not in steps that     */
+                                /* store checkpoints for the adjoint); 0 = the  */
+                                /* lattice order throughout                     */
     int pre_sweeps, post_sweeps;/* red-black Gauss-Seidel sweeps per level      */
     int coarse_block_n;         /* multigrid levels of side <= this are relaxed  */
                                 /* by one thread block in shared memory;         */
@@ -115,6 +116,13 @@ typedef struct {
                                 /* loop, in SM clock cycles; a wait that runs   */
                                 /* out records QS_ERR_TIMEOUT and the kernel    */
                                 /* returns; 0 = default 4e9 (about 2 s)         */
+    int cluster_size;           /* QS_FP64: the multigrid solves of small grids */
+                                /* run in one thread-block cluster of this many */
+                                /* blocks (8 or 16; N must divide by 2 * size), */
+                                /* the rest of the slice loop on every block;   */
+                                /* 0 = automatic (N <= 64: 16 when N divides by */
+                                /* 32, else 8 when N divides by 16),            */
+                                /* 1 = off                                      */
 } qs_config;
 
 /* Driver-beam macroparticles: structure of arrays of float64, n entries each.
@@ -196,6 +204,23 @@ int qs_step3d(qs_ctx *ctx, const qs_beam *beams, int n_beams, qs_step_stats *sta
 int qs_step3d_schedule(qs_ctx *ctx, const qs_beam *beams, int n_beams,
                        const int32_t *m_schedule, qs_step_stats *stats);
 
+/* As qs_step3d, with a laser driver in the slice advance (Sec. "Description
+ * of different plasma wake drivers"): `a2` (DEVICE float64 [n_xi][ny][nx],
+ * caller-owned, read only) is |A|^2 of the laser envelope at the base
+ * slices; at sub-steps it is taken linearly in xi between base slices, like
+ * the beam current.  It adds |A|^2 / 2 to the numerator of gamma (the line
+ * after Eq. EoM_111), hence to n_*<gamma> and j_z; the ponderomotive force
+ * -grad(|A|^2 / 4) / (1+psi) to the push (Eq. EoM_111); and
+ * -n_* grad(|A|^2 / 4) / (1+psi)^2 to the source S of Eq. FluxCurr1_A.  The
+ * gradient is the central difference with even ghosts (A is odd at the
+ * walls, so |A|^2 is mirrored).  `chi` (DEVICE float64 [n_xi][ny][nx], may
+ * be NULL) receives the susceptibility chi = n_* / (1+psi) of Eq.
+ * laser_Enve at every base slice.  beams / n_beams as qs_step3d (n_beams may
+ * be 0: a laser-only driver).  qs_step3d_adjoint is not available after this
+ * step (QS_ERR_STATE).  Errors: as qs_step3d; QS_ERR_ARG if a2 is NULL. */
+int qs_step3d_laser(qs_ctx *ctx, const qs_beam *beams, int n_beams, const double *a2,
+                    double *chi, qs_step_stats *stats);
+
 /* Batched form: one 3D step (as qs_step3d) of each of n independent
  * contexts, which may differ in size, window, drivers, tiles and sweeps, in a
  * single persistent launch.  The launch is split into teams of `team_blocks`
@@ -221,6 +246,28 @@ int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const i
  * wake is zero.  xi advances by dt (1 - v_z).  Arrays are updated IN PLACE
  * (DEVICE pointers).  Errors: QS_ERR_STATE (no step yet), QS_ERR_ARG. */
 int qs_push_beam(qs_ctx *ctx, qs_beam *beams, int n_beams, double dt);
+
+/* Push_Driver with the laser's own high-frequency fields (Sec. "Description
+ * of different plasma wake drivers", Eq. E_B_Fields; the sub-cycling of Sec.
+ * "Modeling direct laser acceleration of electrons with WAND-PIC"): beam
+ * particles are not ponderomotive, so besides the stored wake (as
+ * qs_push_beam) they feel the fields rebuilt from the envelope A (vector
+ * potential Re[A e^{-i k0 xi}], polarised along x):
+ *   E_x = Re[-((d_t A + d_xi A) - i k0 A) e^{-i k0 xi}],  B_y = Re[(-d_xi A + i k0 A) e^{-i k0 xi}],
+ *   E_z = Re[-d_x A e^{-i k0 xi}],                        B_z = Re[-d_y A e^{-i k0 xi}].
+ * The step dt is split into n_sub (>= 1) relativistic Boris sub-steps
+ * (Eqs. EoM_beam_1/2); at sub-step s the envelope is linear in time between
+ * env_n (time t) and env_np1 (t + dt) at s / n_sub, d_t A = (env_np1 -
+ * env_n) / dt.  A and its derivatives are gathered like the wake (CIC in x,
+ * y, linear in xi, zero outside the box and the window); d_x A, d_y A are
+ * central differences with odd ghosts, d_xi A the central difference between
+ * base slices with A = 0 beyond the window; the carrier phase is taken at the
+ * particle's own xi.  env_n, env_np1: DEVICE complex128 [n_xi][ny][nx]
+ * (interleaved re, im), caller-owned, read only (they may be the same
+ * array).  k0 = omega_0 / omega_p > 0.  Beam arrays are updated IN PLACE.
+ * Errors: QS_ERR_STATE (no step yet), QS_ERR_ARG. */
+int qs_push_beam_dla(qs_ctx *ctx, qs_beam *beams, int n_beams, double dt, const double *env_n,
+                     const double *env_np1, double k0, int n_sub);
 
 /* ---- differentiable form: the adjoint of one 3D step ----
  *
@@ -455,6 +502,61 @@ int qs_nu_source(qs_nu_solver *s, const double *d_j, double *d_out);
 /* Free the solver and its device memory (NULL is a no-op). */
 void qs_nu_destroy(qs_nu_solver *s);
 
+/* ---- The slice advance on a nonuniform transverse grid ------------------
+ * Sec. "Multigrid Solver with Nonuniform Grids" uses the node grid for the
+ * whole quasi-static loop.  This is the slice loop of qs_step3d (Algorithm 1)
+ * with every grid operation on the tensor-product node grid of qs_nu_create:
+ * CIC deposits and gathers linear in physical coordinates between the nodes
+ * around a particle (weight on a wall node folded into the adjacent interior
+ * node, density = deposit / the node's dual area: half of each adjacent
+ * interval, the whole interval to the wall for the first and last node);
+ * gradients by the three-point first difference printed after Eq.
+ * 2D_Laplac_3rd, zero beyond the walls; the five field equations by the
+ * nonuniform solver with the third-order correction, warm-started from the
+ * previous slice (M = 0 for psi, E_z, B_z; M = -kappa for B_perp); the
+ * Boris-like push with specular walls at the outer nodes; sub-steps by
+ * Step_Size_Refinement with V0 = (smallest node spacing) / dxi0.  Particles
+ * and grids are float64; the solves run in `precision` (QS_FP64 or
+ * QS_FP32_REFINED, see qs_nu_create).  The driver enters as a given j_z on
+ * the nodes of the base slices.  Arrays are [iy][ix] over the n x n interior
+ * nodes. */
+typedef struct qs_nu_pic qs_nu_pic;
+
+/* n = 2^k - 1 interior nodes per side; x_nodes, y_nodes: HOST, n + 2
+ * strictly increasing coordinates, walls first and last (copied).  n_xi base
+ * slices over a window of length xi_len; refine_k and psi_floor as in
+ * qs_config.  The object owns its device memory until qs_nu_pic_destroy.
+ * Errors: QS_ERR_ARG, QS_ERR_OOM, QS_ERR_CUDA. */
+int qs_nu_pic_create(int n, const double *x_nodes, const double *y_nodes, int n_xi,
+                     double xi_len, int refine_k, double psi_floor, int precision,
+                     void *cuda_stream, qs_nu_pic **out);
+
+/* Quiet-start plasma: sqrt(ppc) x sqrt(ppc) particles in every rectangle
+ * between neighbouring nodes (walls included) at offsets (k + 1/2)/sqrt(ppc)
+ * of it, weight = its area / ppc, p_perp = 0; the ion background is their
+ * deposit.  (n + 1)^2 ppc particles.  Synchronises.  Errors: QS_ERR_ARG
+ * (ppc not a perfect square), QS_ERR_OOM, QS_ERR_CUDA. */
+int qs_nu_pic_init_plasma(qs_nu_pic *s, int ppc);
+
+/* One 3D step from the lattice at the head of the window.  d_jzb: DEVICE
+ * float64 [n_xi][n][n] driver j_z on the nodes of the base slices (linear in
+ * xi at sub-steps).  d_hist: DEVICE float64 [5][n_xi][n][n], OVERWRITTEN with
+ * psi, E_z, B_z, B_x, B_y at the base slices.  Each solve stops at relative
+ * residual tol or max_cycles V-cycles.  stats (may be NULL): slices,
+ * pushes, V-cycles per solve kind, max_m, gpu_ms.  Synchronises.  Errors:
+ * QS_ERR_STATE (no plasma), QS_ERR_ARG, QS_ERR_NOT_CONVERGED (a solve hit
+ * max_cycles; the step still completed), QS_ERR_TIMEOUT, QS_ERR_CUDA. */
+int qs_nu_pic_step3d(qs_nu_pic *s, const double *d_jzb, double *d_hist, double tol,
+                     int max_cycles, qs_step_stats *stats);
+
+/* The plasma after the last step (or the lattice), HOST arrays of
+ * qs_nu_pic_count() entries (any may be NULL).  Synchronises. */
+int qs_nu_pic_get_plasma(qs_nu_pic *s, double *x, double *y, double *px, double *py, double *w);
+int64_t qs_nu_pic_count(const qs_nu_pic *s);
+
+/* Free the object and its device memory (NULL is a no-op). */
+void qs_nu_pic_destroy(qs_nu_pic *s);
+
 /* ---- Laser-envelope advance ---------------------------------------------
  * Sec. "Description of different plasma wake drivers", Eq. laser_Enve: the
  * complex envelope A of a laser with vector potential A exp(-i k0 xi) obeys
@@ -496,6 +598,24 @@ int qs_laser_advance(qs_laser *s, const double *d_chi, double *d_a, int steps, d
 
 /* Free the object and its device memory (NULL is a no-op). */
 void qs_laser_destroy(qs_laser *s);
+
+/* One 3D step of a laser-driven wake (Algorithm 1 with the laser driver,
+ * Sec. "WAND-PIC's Global Algorithm", last paragraph): |A|^2 of `envelope`
+ * (DEVICE complex128 [n_xi][ny][nx], interleaved re, im, caller-owned)
+ * drives the slice loop of qs_step3d_laser, together with the beams (n_beams
+ * may be 0), which yields chi = n_* / (1+psi) at the base slices; then the
+ * envelope advances one time step of Eq. laser_Enve with that chi
+ * (qs_laser_advance with steps = 1, tol, max_cycles), IN PLACE.  The laser
+ * object must have the context's cells, box width, slice count and slice
+ * spacing (QS_ERR_ARG otherwise).  The context allocates, on first use, two
+ * float64 arrays of n_xi * N^2 (|A|^2 and chi), kept until qs_destroy.
+ * stats: the slice loop's counters; env_cycles, env_relres (HOST, may be
+ * NULL): the envelope advance's V-cycles and largest final relative
+ * residual.  Synchronises.  Errors: those of qs_step3d_laser and
+ * qs_laser_advance, QS_ERR_OOM. */
+int qs_laser_step3d(qs_ctx *ctx, qs_laser *laser, const qs_beam *beams, int n_beams,
+                    double *envelope, double tol, int max_cycles, qs_step_stats *stats,
+                    int64_t *env_cycles, double *env_relres);
 
 /* Name of a status code (static string). */
 const char *qs_strerror(int status);

@@ -10,14 +10,14 @@ from ._binding import (FIELD_ALL, FIELD_BX, FIELD_BY, FIELD_BZ, FIELD_EZ, FIELD_
                        QS_ERR_TIMEOUT, QS_FP32_REFINED, QS_FP64, QS_OK, Beam, Context, QsConfig,
                        QsError, config_from_workload, default_config, load_library,
                        step3d_batched, cell_sort_noalloc, bigaussian_beam,
-                       bigaussian_adjoint, NonuniformSolver,
+                       bigaussian_adjoint, NonuniformSolver, NonuniformPIC,
                        LaserEnvelope)
 from .grad import WitnessGain, witness_gain
 
 __all__ = [
     "Beam", "Context", "QsConfig", "QsError", "config_from_workload", "default_config",
     "step3d_batched", "cell_sort_noalloc", "bigaussian_beam", "bigaussian_adjoint",
-    "WitnessGain", "witness_gain", "NonuniformSolver", "LaserEnvelope",
+    "WitnessGain", "witness_gain", "NonuniformSolver", "NonuniformPIC", "LaserEnvelope",
     "load_library", "PROTOTYPES", "FIELD_ALL", "FIELD_PSI", "FIELD_EZ", "FIELD_BZ", "FIELD_BX",
     "FIELD_BY", "FIELD_JZB", "FIELD_NAMES", "QS_FP64", "QS_FP32_REFINED",
 ]

@@ -51,6 +51,7 @@ class QsConfig(ctypes.Structure):
         ("coarse_pre_sweeps", ctypes.c_int),
         ("checkpoint_every", ctypes.c_int),
         ("barrier_wait_cycles", ctypes.c_int64),
+        ("cluster_size", ctypes.c_int),
     ]
 
 
@@ -87,6 +88,9 @@ PROTOTYPES = {
     "qs_step3d": (_I, [_P, _P, _I, ctypes.POINTER(QsStepStats)]),
     "qs_step3d_schedule": (_I, [_P, _P, _I, _P, ctypes.POINTER(QsStepStats)]),
     "qs_push_beam": (_I, [_P, _P, _I, _D]),
+    "qs_push_beam_dla": (_I, [_P, _P, _I, _D, _P, _P, _D, _I]),
+    "qs_step3d_laser": (_I, [_P, _P, _I, _P, _P, ctypes.POINTER(QsStepStats)]),
+    "qs_laser_step3d": (_I, [_P, _P, _P, _I, _P, _D, _I, ctypes.POINTER(QsStepStats), _P, _P]),
     "qs_step3d_batched": (_I, [_P, _I, _P, _P, _I, _P]),
     "qs_fields": (_I, [_P, _I, _I, _I, _P, _I]),
     "qs_slice_diagnostics": (_I, [_P, _P, _P, _P]),
@@ -107,6 +111,12 @@ PROTOTYPES = {
     "qs_nu_apply": (_I, [_P, _P, _P, _P]),
     "qs_nu_source": (_I, [_P, _P, _P]),
     "qs_nu_destroy": (None, [_P]),
+    "qs_nu_pic_create": (_I, [_I, _P, _P, _I, _D, _I, _D, _I, _P, ctypes.POINTER(_P)]),
+    "qs_nu_pic_init_plasma": (_I, [_P, _I]),
+    "qs_nu_pic_step3d": (_I, [_P, _P, _P, _D, _I, ctypes.POINTER(QsStepStats)]),
+    "qs_nu_pic_get_plasma": (_I, [_P, _P, _P, _P, _P, _P]),
+    "qs_nu_pic_count": (_I64, [_P]),
+    "qs_nu_pic_destroy": (None, [_P]),
     "qs_laser_create": (_I, [_I, _D, _I, _D, _D, _D, _P, ctypes.POINTER(_P)]),
     "qs_laser_advance": (_I, [_P, _P, _P, _I, _D, _I, _P, _P]),
     "qs_laser_destroy": (None, [_P]),
@@ -301,6 +311,75 @@ class Context:
                     vcycles=list(stats.vcycles), psi_guard_hits=stats.psi_guard_hits,
                     sorts=stats.sorts, max_relres=stats.max_relres, vmax=stats.vmax,
                     max_m=stats.max_m, gpu_ms=stats.gpu_ms)
+
+    @staticmethod
+    def _stats_dict(st: int, stats) -> Dict:
+        return dict(status=st, slices=stats.slices, substeps=stats.substeps, pushes=stats.pushes,
+                    vcycles=list(stats.vcycles), psi_guard_hits=stats.psi_guard_hits,
+                    sorts=stats.sorts, max_relres=stats.max_relres, vmax=stats.vmax,
+                    max_m=stats.max_m, gpu_ms=stats.gpu_ms)
+
+    def _field_tensor(self, t, name: str, dtype=None):
+        """Checks a CUDA tensor of shape [n_xi, N, N] for a laser step."""
+        import torch
+        shape = (self.n_xi, self.n, self.n)
+        dtype = dtype or torch.float64
+        if (not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype
+                or not t.is_contiguous() or tuple(t.shape) != shape or t.device != self.device):
+            raise QsError(QS_ERR_ARG, f"{name} must be a contiguous {dtype} CUDA tensor "
+                                      f"{list(shape)} on {self.device}")
+        return t
+
+    def step3d_laser(self, beams: Sequence[Beam], a2, chi=None,
+                     raise_on_error: bool = True) -> Dict:
+        """qs_step3d_laser: the slice loop with |A|^2 of a laser envelope
+        (float64 [n_xi, N, N] CUDA tensor) at the base slices; `chi` (same
+        shape, optional) receives n_* / (1+psi) at the base slices."""
+        self._field_tensor(a2, "a2")
+        if chi is not None:
+            self._field_tensor(chi, "chi")
+        arr = _beam_array(beams)
+        stats = QsStepStats()
+        st = self.lib.qs_step3d_laser(self.h, ctypes.cast(arr, _P), len(beams), _ptr(a2),
+                                      _ptr(chi), ctypes.byref(stats))
+        if raise_on_error:
+            self._check(st, "qs_step3d_laser")
+        return self._stats_dict(st, stats)
+
+    def laser_step3d(self, laser: "LaserEnvelope", envelope, beams: Sequence[Beam] = (),
+                     tol: float = 1e-10, max_cycles: int = 50,
+                     raise_on_error: bool = True) -> Dict:
+        """qs_laser_step3d: one laser-driven 3D step (the wake with |A|^2 of
+        `envelope`, then one envelope time step with the wake's chi); the
+        complex128 [n_xi, N, N] envelope is advanced in place."""
+        import torch
+        self._field_tensor(envelope, "envelope", torch.complex128)
+        arr = _beam_array(beams)
+        stats = QsStepStats()
+        cyc = ctypes.c_int64(0)
+        rel = ctypes.c_double(0.0)
+        st = self.lib.qs_laser_step3d(self.h, _P(laser.h), ctypes.cast(arr, _P), len(beams),
+                                      _ptr(envelope), float(tol), int(max_cycles),
+                                      ctypes.byref(stats), ctypes.byref(cyc), ctypes.byref(rel))
+        if raise_on_error:
+            self._check(st, "qs_laser_step3d")
+        out = self._stats_dict(st, stats)
+        out.update(env_cycles=cyc.value, env_relres=rel.value)
+        return out
+
+    def push_beam_dla(self, beams: Sequence[Beam], dt: float, env_n, env_np1, k0: float,
+                      n_sub: int):
+        """qs_push_beam_dla: n_sub Boris sub-steps of dt/n_sub in the stored wake
+        plus the laser fields rebuilt from the envelopes at t and t + dt
+        (complex128 [n_xi, N, N] CUDA tensors)."""
+        import torch
+        self._field_tensor(env_n, "env_n", torch.complex128)
+        self._field_tensor(env_np1, "env_np1", torch.complex128)
+        arr = _beam_array(beams)
+        self._check(self.lib.qs_push_beam_dla(self.h, ctypes.cast(arr, _P), len(beams), float(dt),
+                                              _ptr(env_n), _ptr(env_np1), float(k0), int(n_sub)),
+                    "qs_push_beam_dla")
+        self.stream.synchronize()
 
     def push_beam(self, beams: Sequence[Beam], dt: float):
         arr = _beam_array(beams)
@@ -601,6 +680,73 @@ class NonuniformSolver:
     def close(self):
         if self.h:
             self._lib.qs_nu_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class NonuniformPIC:
+    """qs_nu_pic_*: the slice loop on a nonuniform node grid (n x n interior
+    nodes, node coordinates with the walls), float64 particles and grids,
+    solves in `precision` ("fp64" or "fp32r")."""
+
+    def __init__(self, x_nodes, y_nodes, n_xi: int, xi_len: float, refine_k: int = 8,
+                 psi_floor: float = 1e-3, precision: str = "fp64", stream=None):
+        import numpy as np
+        import torch
+        self._lib = load_library()
+        self.h = None
+        xn = np.ascontiguousarray(x_nodes, dtype=np.float64)
+        yn = np.ascontiguousarray(y_nodes, dtype=np.float64)
+        self.n, self.n_xi = int(xn.size) - 2, int(n_xi)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        h = _P()
+        rc = self._lib.qs_nu_pic_create(self.n, xn.ctypes.data, yn.ctypes.data, self.n_xi,
+                                        float(xi_len), int(refine_k), float(psi_floor),
+                                        QS_FP64 if precision == "fp64" else QS_FP32_REFINED,
+                                        _P(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != QS_OK:
+            raise QsError(rc, "qs_nu_pic_create: " + self._lib.qs_strerror(rc).decode())
+        self.h = h.value
+
+    def init_plasma(self, ppc: int):
+        rc = self._lib.qs_nu_pic_init_plasma(self.h, int(ppc))
+        if rc != QS_OK:
+            raise QsError(rc, "qs_nu_pic_init_plasma: " + self._lib.qs_strerror(rc).decode())
+
+    def step3d(self, jzb, tol: float = 1e-10, max_cycles: int = 60,
+               raise_on_error: bool = True):
+        """One 3D step with the driver current jzb (float64 CUDA [n_xi, n, n]);
+        returns (history [5, n_xi, n, n] CUDA tensor, stats dict)."""
+        import torch
+        shape = (self.n_xi, self.n, self.n)
+        if (not isinstance(jzb, torch.Tensor) or not jzb.is_cuda or jzb.dtype != torch.float64
+                or not jzb.is_contiguous() or tuple(jzb.shape) != shape):
+            raise QsError(QS_ERR_ARG, f"jzb must be a contiguous float64 CUDA tensor {shape}")
+        hist = torch.empty((5,) + shape, dtype=torch.float64, device=jzb.device)
+        stats = QsStepStats()
+        rc = self._lib.qs_nu_pic_step3d(self.h, _ptr(jzb), _ptr(hist), float(tol),
+                                        int(max_cycles), ctypes.byref(stats))
+        if raise_on_error and rc != QS_OK:
+            raise QsError(rc, "qs_nu_pic_step3d: " + self._lib.qs_strerror(rc).decode())
+        return hist, Context._stats_dict(rc, stats)
+
+    def plasma(self):
+        import numpy as np
+        n = int(self._lib.qs_nu_pic_count(self.h))
+        arrs = [np.zeros(n) for _ in range(5)]
+        rc = self._lib.qs_nu_pic_get_plasma(self.h, *[a.ctypes.data for a in arrs])
+        if rc != QS_OK:
+            raise QsError(rc, "qs_nu_pic_get_plasma")
+        return dict(zip(("x", "y", "px", "py", "w"), arrs))
+
+    def close(self):
+        if self.h is not None:
+            self._lib.qs_nu_pic_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -22,7 +22,7 @@ LIB = os.path.join(LIBDIR, "libqs.so")
 # parallel compile is bounded by the slowest single kernel
 SOURCES = ["qs_engine_fp32r.cu", "qs_engine_batched_fp32r.cu", "qs_engine_fp64.cu",
            "qs_engine_batched_fp64.cu", "qs_adjoint_fp32r.cu", "qs_adjoint_fp64.cu",
-           "qs_nonuniform.cu", "qs_laser.cu", "qs_grad_aux.cu", "qs_aux.cu", "qs_api.cu",
+           "qs_nonuniform.cu", "qs_laser.cu", "qs_nupic.cu", "qs_grad_aux.cu", "qs_aux.cu", "qs_api.cu",
            "qs_engine_host.cu", "qs_adjoint_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -36,11 +36,23 @@ struct qs_ctx {
     int tile_x = 0, tile_y = 0;
     size_t tile_offset = 0, block_offset = 0;
     double *hist = nullptr, *jzb = nullptr;
+    // laser driver: |A|^2 and grad(|A|^2/4) of the current slice; |A|^2 and
+    // chi of every base slice for the laser-driven step (allocated on use)
+    double *a2 = nullptr, *pondx = nullptr, *pondy = nullptr;
+    float *f32[5] = {};  // refined form: float32 grad psi and B for the push
+    double *a2_all = nullptr, *chi_all = nullptr;
+    bool last_laser = false;
     DevScalars *sc = nullptr;
     int32_t *diag_m = nullptr, *d_sched = nullptr;
     double *diag_vmax = nullptr, *diag_charge = nullptr;
     // sort scratch
     int32_t *s_cursor = nullptr;
+    // the in-loop sort (config.sort_every > 0): cell counts and offsets, the
+    // per-block chunk sums, per-particle cells and order, the spare particle set
+    int32_t *l_count = nullptr, *l_offset = nullptr, *l_cursor = nullptr, *l_bsum = nullptr;
+    int32_t *l_cell = nullptr, *l_order = nullptr, *id2 = nullptr;
+    double *x2 = nullptr, *y2 = nullptr, *wd2 = nullptr;
+    void *px2 = nullptr, *py2 = nullptr, *w2 = nullptr;
     int64_t *trace = nullptr;
     // plasma
     int64_t np = 0;
@@ -66,6 +78,8 @@ struct qs_ctx {
     bool store_valid = false;
     int engine_blocks = 0;
     size_t engine_smem = 0;
+    int cl_size = 1;          // thread-block cluster of the float64 small-grid solves
+    size_t cl_offset = 0;     // its arrays in the engine's dynamic shared memory
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     char msg[512] = {0};
 };
@@ -190,6 +204,16 @@ int validate(const qs_config *cfg, char *why, size_t nwhy) {
         snprintf(why, nwhy, "barrier_wait_cycles must be >= 0");
         return QS_ERR_ARG;
     }
+    const int cs = cfg->cluster_size;
+    if (cs != 0 && cs != 1 && cs != 8 && cs != 16) {
+        snprintf(why, nwhy, "cluster_size must be 0, 1, 8 or 16");
+        return QS_ERR_ARG;
+    }
+    if (cs > 1 && (cfg->precision != QS_FP64 || cfg->nx % (2 * cs) != 0 || cfg->nx > 128)) {
+        snprintf(why, nwhy, "cluster_size %d needs QS_FP64 and N <= 128 divisible by %d", cs,
+                 2 * cs);
+        return QS_ERR_ARG;
+    }
     return QS_OK;
 }
 
@@ -212,7 +236,8 @@ int create_impl(qs_ctx *c) {
                         &c->f_psi, &c->f_ez, &c->f_bz, &c->f_bx, &c->f_by, &c->dpx, &c->dpy,
                         &c->jz,  &c->kap, &c->invd0, &c->hist1[0], &c->hist1[1],
                         &c->hist1[2], &c->hist1[3], &c->hist1[4], &c->hist2[0], &c->hist2[1],
-                        &c->hist2[2], &c->hist2[3], &c->hist2[4]};
+                        &c->hist2[2], &c->hist2[3], &c->hist2[4], &c->a2, &c->pondx,
+                        &c->pondy};
     for (double **p : grids) AL(L, *p, nn);
     const bool ref = g.precision == QS_FP32_REFINED;
     for (int l = 1; l < c->nlev; ++l) {
@@ -233,6 +258,8 @@ int create_impl(qs_ctx *c) {
             AL(L, c->lev[l].d, m);
         }
     }
+    if (ref)
+        for (int k = 0; k < 5; ++k) AL(L, c->f32[k], nn);
     if (ref) {
         float **g32[] = {&c->e32[0],    &c->e32[1],    &c->r32[0][0], &c->r32[0][1],
                          &c->r32[1][0], &c->r32[1][1], &c->k32,       &c->d32,
@@ -253,6 +280,12 @@ int create_impl(qs_ctx *c) {
     AL(L, c->diag_vmax, (size_t)g.n_xi);
     AL(L, c->diag_charge, (size_t)g.n_xi);
     AL(L, c->s_cursor, nn);
+    if (g.sort_every > 0) {
+        AL(L, c->l_count, nn);
+        AL(L, c->l_offset, nn + 1);
+        AL(L, c->l_cursor, nn);
+        AL(L, c->l_bsum, (size_t)1024);
+    }
     if (g.trace_capacity > 0) AL(L, c->trace, 2 * (size_t)g.trace_capacity);
     // fields start at zero (the warm start of the first slice)
     for (double **p : grids) CK(cudaMemsetAsync(*p, 0, nn * sizeof(double), c->st), "memset");
@@ -265,16 +298,27 @@ int create_impl(qs_ctx *c) {
     c->engine_smem = qs_engine_smem_bytes(c->lev_n, c->nlev, c->block_level_n, g.precision,
                                           c->tile_x, c->tile_y, nu, g.post_sweeps,
                                           &c->block_offset, &c->tile_offset);
+    int cs = g.cluster_size;
+    if (cs == 0)  // 16 blocks where the grid splits into strips of >= 2 rows
+        cs = (!ref && c->N <= 64 && c->N % 32 == 0) ? 16
+                                                     : (!ref && c->N <= 64 && c->N % 16 == 0) ? 8 : 1;
+    if (cs > 1) {
+        c->cl_offset = (c->engine_smem + 255) & ~(size_t)255;
+        c->engine_smem = c->cl_offset + qs_cluster_smem_bytes(c->lev_n, c->nlev, cs);
+    }
     if (c->engine_smem > 220 * 1024)
         return fail(c, QS_ERR_ARG,
                     "coarse_block_n = %d with %d x %d tiles needs %zu bytes of shared memory",
                     c->block_level_n, c->tile_x, c->tile_y, c->engine_smem);
     int blocks = 0;
-    if (qs_engine_max_blocks(c->dev, g.precision, c->engine_smem, &blocks) != 0 || blocks < 1)
+    if (qs_engine_max_blocks(c->dev, g.precision, c->engine_smem, &blocks, cs) != 0 ||
+        blocks < cs)
         return fail(c, QS_ERR_CUDA, "slice engine cannot be made resident");
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev), "attr");
     c->engine_blocks = blocks < sms ? blocks : sms;
+    c->engine_blocks -= c->engine_blocks % cs;  // whole clusters
+    c->cl_size = cs;
     CK(cudaEventCreate(&c->ev0), "event");
     CK(cudaEventCreate(&c->ev1), "event");
     CK(cudaStreamSynchronize(c->st), "sync");
@@ -342,6 +386,8 @@ void qs_destroy(qs_ctx *c) {
     else cudaDeviceSynchronize();
     if (c->ckpt) cudaFree(c->ckpt);
     if (c->store) cudaFree(c->store);
+    if (c->a2_all) cudaFree(c->a2_all);
+    if (c->chi_all) cudaFree(c->chi_all);
     free_list(c->plasma_allocs);
     free_list(c->allocs);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -364,6 +410,15 @@ int qs_init_plasma(qs_ctx *c, int ppc, const double *profile, int n_coef, double
     c->have_plasma = c->have_step = false;
     c->ckpt_valid = false;
     c->store_valid = false;
+    if (np != c->np) {
+        // the checkpoints and the slice store are sized by the particle count
+        if (c->ckpt) cudaFree(c->ckpt);
+        if (c->store) cudaFree(c->store);
+        c->ckpt = nullptr;
+        c->ckpt_count = 0;
+        c->store = nullptr;
+        c->store_slots = 0;
+    }
     auto &L = c->plasma_allocs;
     AL(L, c->t_x, np);
     AL(L, c->t_y, np);
@@ -381,6 +436,31 @@ int qs_init_plasma(qs_ctx *c, int ppc, const double *profile, int n_coef, double
         AL(L, c->px32, np);
         AL(L, c->py32, np);
         AL(L, c->w32, np);
+    }
+    if (c->cfg.sort_every > 0) {  // the spare set of the in-loop sort
+        AL(L, c->l_cell, np);
+        AL(L, c->l_order, np);
+        AL(L, c->id2, np);
+        AL(L, c->x2, np);
+        AL(L, c->y2, np);
+        if (c->cfg.precision == QS_FP32_REFINED) {
+            float *a = nullptr, *b = nullptr, *w = nullptr;
+            AL(L, a, np);
+            AL(L, b, np);
+            AL(L, w, np);
+            AL(L, c->wd2, np);
+            c->px2 = a;
+            c->py2 = b;
+            c->w2 = w;
+        } else {
+            double *a = nullptr, *b = nullptr, *w = nullptr;
+            AL(L, a, np);
+            AL(L, b, np);
+            AL(L, w, np);
+            c->px2 = a;
+            c->py2 = b;
+            c->w2 = w;
+        }
     }
     double *d_table = nullptr;
     if (profile) {
@@ -549,6 +629,25 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
         a.lev32[l] = c->lev32[l];
     }
     a.block_level_n = c->block_level_n;
+    a.cl_size = c->cl_size;
+    a.cl_smem_offset = (int)c->cl_offset;
+    a.id = c->id;
+    if (g.sort_every > 0 && c->x2) {
+        a.sort_every = g.sort_every;
+        a.id2 = c->id2;
+        a.x2 = c->x2;
+        a.y2 = c->y2;
+        a.wd2 = c->wd2;
+        a.px2 = c->px2;
+        a.py2 = c->py2;
+        a.w2 = c->w2;
+        a.s_count = c->l_count;
+        a.s_offset = c->l_offset;
+        a.s_cursor = c->l_cursor;
+        a.s_cell = c->l_cell;
+        a.s_order = c->l_order;
+        a.s_bsum = c->l_bsum;
+    }
     a.tile_x = c->tile_x;
     a.tile_y = c->tile_y;
     a.tile_smem_offset = (int)c->tile_offset;
@@ -562,6 +661,11 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
     }
     a.k32 = c->k32;
     a.d32 = c->d32;
+    a.dpx32 = c->f32[0];
+    a.dpy32 = c->f32[1];
+    a.bx32 = c->f32[2];
+    a.by32 = c->f32[3];
+    a.bz32 = c->f32[4];
     a.hist = c->hist;
     a.jzb = c->jzb;
     a.m_sched = sched ? c->d_sched : nullptr;
@@ -611,7 +715,7 @@ static int step_finish(qs_ctx *c, qs_step_stats *stats, double gpu_ms) {
         stats->pushes = hs.pushes;
         for (int k = 0; k < 3; ++k) stats->vcycles[k] = hs.vcycles[k];
         stats->psi_guard_hits = (int64_t)hs.guard_hits;
-        stats->sorts = 0;
+        stats->sorts = hs.sorts;
         stats->max_relres = hs.max_relres;
         unsigned long long vb = hs.vmax_all_bits;
         double vm;
@@ -625,18 +729,25 @@ static int step_finish(qs_ctx *c, qs_step_stats *stats, double gpu_ms) {
 }
 
 static int step_impl(qs_ctx *c, const qs_beam *beams, int n_beams, const int32_t *sched,
-                     qs_step_stats *stats) {
+                     qs_step_stats *stats, const double *a2 = nullptr, double *chi = nullptr) {
     if (check_ctx(c)) return QS_ERR_ARG;
     EngineArgs a;
     c->ckpt_valid = false;
     int r = step_prepare(c, beams, n_beams, sched, c->st, a);
     if (r != QS_OK) return r;
+    c->last_laser = a2 != nullptr;
+    if (a2) {
+        a.a2_base = a2;
+        a.a2 = c->a2;
+        a.pondx = c->pondx;
+        a.pondy = c->pondy;
+        a.chi = chi;
+    }
     const int K = c->cfg.checkpoint_every;
     if (K > 0) {  // plasma checkpoints for a later qs_step3d_adjoint
         const size_t need = (size_t)((c->cfg.n_xi + K - 1) / K) * 4 * c->np;
         if (c->ckpt_count < need) {
             if (c->ckpt) cudaFree(c->ckpt);
-    if (c->store) cudaFree(c->store);
             c->ckpt = nullptr;
             c->ckpt_count = 0;
             CK(cudaMalloc(&c->ckpt, need * sizeof(double)), "cudaMalloc checkpoints");
@@ -706,6 +817,46 @@ int qs_step3d_schedule(qs_ctx *c, const qs_beam *beams, int n_beams, const int32
     return step_impl(c, beams, n_beams, m_schedule, stats);
 }
 
+int qs_step3d_laser(qs_ctx *c, const qs_beam *beams, int n_beams, const double *a2, double *chi,
+                    qs_step_stats *stats) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!a2) return fail(c, QS_ERR_ARG, "a2 is NULL");
+    return step_impl(c, beams, n_beams, nullptr, stats, a2, chi);
+}
+
+int qs_laser_step3d(qs_ctx *c, qs_laser *laser, const qs_beam *beams, int n_beams,
+                    double *envelope, double tol, int max_cycles, qs_step_stats *stats,
+                    int64_t *env_cycles, double *env_relres) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!laser || !envelope) return fail(c, QS_ERR_ARG, "NULL laser or envelope");
+    const qs_config &g = c->cfg;
+    int ln = 0, lxi = 0;
+    double lw = 0.0, ldxi = 0.0;
+    qs_laser_shape(laser, &ln, &lw, &lxi, &ldxi);
+    const double dxi0 = (g.xi_max - g.xi_min) / g.n_xi;
+    if (ln != c->N || lxi != g.n_xi || std::fabs(lw - (g.x_max - g.x_min)) > 1e-12 * lw ||
+        std::fabs(ldxi - dxi0) > 1e-12 * dxi0)
+        return fail(c, QS_ERR_ARG, "the envelope's cells, box, slices or slice spacing "
+                                   "differ from the context's");
+    const size_t n = (size_t)g.n_xi * c->N * c->N;
+    if (!c->a2_all) {
+        CK(cudaMalloc(&c->a2_all, n * sizeof(double)), "cudaMalloc |A|^2");
+        if (cudaMalloc(&c->chi_all, n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->a2_all);
+            c->a2_all = nullptr;
+            return fail(c, QS_ERR_OOM, "cudaMalloc chi");
+        }
+    }
+    CK(qs_launch_abs2(c->st, envelope, c->a2_all, (int64_t)n), "|A|^2");
+    int r = step_impl(c, beams, n_beams, nullptr, stats, c->a2_all, c->chi_all);
+    if (r != QS_OK) return r;  // the step synchronised its stream: chi is complete
+    r = qs_laser_advance(laser, c->chi_all, envelope, 1, tol, max_cycles, env_cycles,
+                         env_relres);
+    if (r != QS_OK) return fail(c, r, "envelope advance: %s", qs_strerror(r));
+    return QS_OK;
+}
+
 int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const int *n_beams,
                       int team_blocks, qs_step_stats *stats) {
     if (n < 1 || !ctxs) return QS_ERR_ARG;
@@ -742,6 +893,7 @@ int qs_step3d_batched(qs_ctx **ctxs, int n, const qs_beam *const *beams, const i
         }
         list[k].trace = nullptr;
         list[k].trace_cap = 0;
+        list[k].cl_size = 1;  // the batched launch has no clusters
         if (ctxs[i]->engine_smem > smem) smem = ctxs[i]->engine_smem;
     }
     int total = 0;
@@ -826,6 +978,8 @@ int qs_step3d_adjoint(qs_ctx *c, const double *d_hist, int checkpoint_every, dou
                       double *d_w, double *d_nion, qs_step_stats *stats) {
     if (check_ctx(c)) return QS_ERR_ARG;
     if (!c->have_step) return fail(c, QS_ERR_STATE, "qs_step3d has not been run");
+    if (c->last_laser)
+        return fail(c, QS_ERR_STATE, "the adjoint does not cover the laser terms of the last step");
     if (!d_jzb || !d_w || !d_nion) return fail(c, QS_ERR_ARG, "NULL output array");
     if (checkpoint_every < 0) return fail(c, QS_ERR_ARG, "checkpoint_every must be >= 0");
     const qs_config &g = c->cfg;
@@ -942,7 +1096,9 @@ int qs_step3d_adjoint(qs_ctx *c, const double *d_hist, int checkpoint_every, dou
         d.j0 = j0;
         d.j1 = j1;
         d.n_sub = n_sub;
-        CK(qs_launch_adjoint(st, a, d, blocks, c->engine_smem), "adjoint engine launch");
+        EngineArgs ra = a;
+        ra.cl_size = 1;  // the adjoint launch has no clusters: grid-wide solves
+        CK(qs_launch_adjoint(st, ra, d, blocks, c->engine_smem), "adjoint engine launch");
         CK(cudaEventRecord(c->ev1, st), "event");
         CK(cudaStreamSynchronize(st), "adjoint engine");
         float ms = 0.f;
@@ -1042,6 +1198,29 @@ int qs_push_beam(qs_ctx *c, qs_beam *beams, int n_beams, double dt) {
         CK(qs_launch_beam_push(c->st, bm, c->N, g.x_min, g.x_max, g.y_min, g.y_max, c->h, g.n_xi,
                                g.xi_min, dxi0, c->hist, dt),
            "beam push");
+    }
+    return QS_OK;
+}
+
+int qs_push_beam_dla(qs_ctx *c, qs_beam *beams, int n_beams, double dt, const double *env_n,
+                     const double *env_np1, double k0, int n_sub) {
+    if (check_ctx(c)) return QS_ERR_ARG;
+    if (!c->have_step) return fail(c, QS_ERR_STATE, "qs_step3d has not been run");
+    if (n_beams < 0 || (n_beams > 0 && !beams)) return fail(c, QS_ERR_ARG, "bad beam list");
+    if (!env_n || !env_np1) return fail(c, QS_ERR_ARG, "NULL envelope");
+    if (!(dt > 0.0) || !(k0 > 0.0) || n_sub < 1)
+        return fail(c, QS_ERR_ARG, "need dt > 0, k0 > 0 and n_sub >= 1");
+    const qs_config &g = c->cfg;
+    const double dxi0 = (g.xi_max - g.xi_min) / g.n_xi;
+    for (int b = 0; b < n_beams; ++b) {
+        const qs_beam &bm = beams[b];
+        if (bm.n < 0) return fail(c, QS_ERR_ARG, "beam %d: negative count", b);
+        if (bm.n > 0 && (!bm.x || !bm.y || !bm.xi || !bm.px || !bm.py || !bm.pz))
+            return fail(c, QS_ERR_ARG, "beam %d: NULL array", b);
+        CK(qs_launch_beam_push_dla(c->st, bm, c->N, g.x_min, g.x_max, g.y_min, g.y_max, c->h,
+                                   g.n_xi, g.xi_min, dxi0, c->hist, env_n, env_np1, k0, dt,
+                                   n_sub),
+           "beam push (laser fields)");
     }
     return QS_OK;
 }

@@ -167,6 +167,128 @@ __global__ void k_beam_push(double *x, double *y, double *xi, double *px, double
     }
 }
 
+// ---- driver push in the laser's high-frequency fields (DLA) ----
+//
+// The envelope A (vector potential A e^{-i k0 xi}, polarised along x) and its
+// derivatives gathered at a particle like the wake: CIC in x, y on the base
+// slices, linear in xi, zero outside the box and the window.  d_x A, d_y A
+// are central differences with odd ghosts (A is zero on the walls), d_xi A
+// the central difference between base slices with A = 0 ahead of and behind
+// the window.  out = (A, d_xi A, d_x A, d_y A), complex.
+__device__ void envelope_at(const double2 *env, int n, int n_xi, double x_min, double x_max,
+                            double y_min, double y_max, double h, double xi_min, double dxi0,
+                            double x, double y, double xi, double2 out[4]) {
+    for (int k = 0; k < 4; ++k) out[k] = make_double2(0.0, 0.0);
+    if (!(x >= x_min && x <= x_max && y >= y_min && y <= y_max)) return;
+    const double s = (xi - xi_min) / dxi0;
+    const double fl = floor(s);
+    if (!(fl > -2.0 && fl < (double)n_xi)) return;
+    const int j0 = (int)fl;
+    const double f = s - fl;
+    const size_t nn = (size_t)n * n;
+    const double inv2h = 0.5 / h, inv2xi = 0.5 / dxi0;
+    Cic c = cic_stencil(x, y, x_min, y_min, h, n);
+    const int idx[4] = {c.i00, c.i01, c.i10, c.i11};
+    const double wc[4] = {c.w00, c.w01, c.w10, c.w11};
+    for (int side = 0; side < 2; ++side) {
+        const int j = j0 + side;
+        if (j < 0 || j >= n_xi) continue;
+        const double wj = side ? f : 1.0 - f;
+        const double2 *a = env + (size_t)j * nn;
+        const double2 *ap = j + 1 < n_xi ? a + nn : nullptr;
+        const double2 *am = j > 0 ? a - nn : nullptr;
+        for (int k = 0; k < 4; ++k) {
+            const int i = idx[k];
+            const int iy = i / n, ix = i - iy * n;
+            const double ww = wj * wc[k];
+            const double2 ac = a[i];
+            const double2 ae = ix < n - 1 ? a[i + 1] : make_double2(-ac.x, -ac.y);
+            const double2 aw = ix > 0 ? a[i - 1] : make_double2(-ac.x, -ac.y);
+            const double2 an = iy < n - 1 ? a[i + n] : make_double2(-ac.x, -ac.y);
+            const double2 aq = iy > 0 ? a[i - n] : make_double2(-ac.x, -ac.y);
+            const double2 xp = ap ? ap[i] : make_double2(0.0, 0.0);
+            const double2 xm = am ? am[i] : make_double2(0.0, 0.0);
+            out[0].x += ww * ac.x;
+            out[0].y += ww * ac.y;
+            out[1].x += ww * (xp.x - xm.x) * inv2xi;
+            out[1].y += ww * (xp.y - xm.y) * inv2xi;
+            out[2].x += ww * (ae.x - aw.x) * inv2h;
+            out[2].y += ww * (ae.y - aw.y) * inv2h;
+            out[3].x += ww * (an.x - aq.x) * inv2h;
+            out[3].y += ww * (an.y - aq.y) * inv2h;
+        }
+    }
+}
+
+// Push_Driver in the wake plus the laser's fields of Eq. E_B_Fields (the
+// real parts of the printed complex fields; x polarisation):
+//   E_x = Re[-((d_t A + d_xi A) - i k0 A) e^{-i k0 xi}],  B_y = Re[(-d_xi A + i k0 A) e^{-i k0 xi}],
+//   E_z = Re[-d_x A e^{-i k0 xi}],                        B_z = Re[-d_y A e^{-i k0 xi}],
+// in n_sub relativistic Boris sub-steps of dt / n_sub (Eqs. EoM_beam_1/2).  At
+// sub-step s the envelope is taken linearly in time between env_n and
+// env_np1 at frac = s / n_sub, d_t A = (A^{n+1} - A^n) / dt; the carrier
+// phase is evaluated at the particle's own xi; the wake is frozen.
+__global__ void k_beam_push_dla(double *x, double *y, double *xi, double *px, double *py,
+                                double *pz, int64_t nb, double qm, int n, double x_min,
+                                double x_max, double y_min, double y_max, double h, int n_xi,
+                                double xi_min, double dxi0, const double *hist,
+                                const double2 *env_n, const double2 *env_np1, double k0,
+                                double dt, int n_sub) {
+    const double hs = dt / n_sub, hq = 0.5 * hs * qm, inv_dt = 1.0 / dt;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nb;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double X = x[p], Y = y[p], XI = xi[p];
+        double ux = px[p], uy = py[p], uz = pz[p];
+        for (int s = 0; s < n_sub; ++s) {
+            double wk[6];
+            wake_at(hist, n, n_xi, x_min, x_max, y_min, y_max, h, xi_min, dxi0, X, Y, XI, wk);
+            double2 gn[4], gp[4];
+            envelope_at(env_n, n, n_xi, x_min, x_max, y_min, y_max, h, xi_min, dxi0, X, Y, XI,
+                        gn);
+            envelope_at(env_np1, n, n_xi, x_min, x_max, y_min, y_max, h, xi_min, dxi0, X, Y,
+                        XI, gp);
+            const double fr = (double)s / (double)n_sub, fo = 1.0 - fr;
+            const double ar = fo * gn[0].x + fr * gp[0].x, ai = fo * gn[0].y + fr * gp[0].y;
+            const double tr = (gp[0].x - gn[0].x) * inv_dt, ti = (gp[0].y - gn[0].y) * inv_dt;
+            const double xr = fo * gn[1].x + fr * gp[1].x, xim = fo * gn[1].y + fr * gp[1].y;
+            const double dxr = fo * gn[2].x + fr * gp[2].x, dxim = fo * gn[2].y + fr * gp[2].y;
+            const double dyr = fo * gn[3].x + fr * gp[3].x, dyim = fo * gn[3].y + fr * gp[3].y;
+            double sn, cs;
+            sincos(k0 * XI, &sn, &cs);  // e^{-i k0 xi} = cs - i sn
+            // Re[(u + i v)(cs - i sn)] = u cs + v sn
+            const double exl = -((tr + xr) + k0 * ai) * cs - ((ti + xim) - k0 * ar) * sn;
+            const double byl = (-xr - k0 * ai) * cs + (-xim + k0 * ar) * sn;
+            const double ezl = -dxr * cs - dxim * sn;
+            const double bzl = -dyr * cs - dyim * sn;
+            const double ez = wk[0] + ezl, bz = wk[1] + bzl, bx = wk[2], by = wk[3] + byl;
+            const double ex = -wk[4] + wk[3] + exl, ey = -wk[5] - wk[2];
+            double vx = ux + hq * ex, vy = uy + hq * ey, vz = uz + hq * ez;
+            double gam = sqrt(1.0 + vx * vx + vy * vy + vz * vz);
+            const double tx = hq * bx / gam, ty = hq * by / gam, tz = hq * bz / gam;
+            const double ss = 2.0 / (1.0 + tx * tx + ty * ty + tz * tz);
+            const double upx = vx + (vy * tz - vz * ty);
+            const double upy = vy + (vz * tx - vx * tz);
+            const double upz = vz + (vx * ty - vy * tx);
+            vx = vx + ss * (upy * tz - upz * ty);
+            vy = vy + ss * (upz * tx - upx * tz);
+            vz = vz + ss * (upx * ty - upy * tx);
+            ux = vx + hq * ex;
+            uy = vy + hq * ey;
+            uz = vz + hq * ez;
+            gam = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+            X += hs * ux / gam;
+            Y += hs * uy / gam;
+            XI += hs * (1.0 - uz / gam);
+        }
+        x[p] = X;
+        y[p] = Y;
+        xi[p] = XI;
+        px[p] = ux;
+        py[p] = uy;
+        pz[p] = uz;
+    }
+}
+
 __global__ void k_convert(const double *src, float *dst, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -286,9 +408,36 @@ cudaError_t qs_launch_beam_push(cudaStream_t st, const qs_beam &b, int n, double
     return cudaGetLastError();
 }
 
+cudaError_t qs_launch_beam_push_dla(cudaStream_t st, const qs_beam &b, int n, double x_min,
+                                    double x_max, double y_min, double y_max, double h,
+                                    int n_xi, double xi_min, double dxi0, const double *hist,
+                                    const double *env_n, const double *env_np1, double k0,
+                                    double dt, int n_sub) {
+    if (b.n <= 0) return cudaSuccess;
+    k_beam_push_dla<<<blocks_for(b.n), kThreads, 0, st>>>(
+        b.x, b.y, b.xi, b.px, b.py, b.pz, b.n, b.q_over_m, n, x_min, x_max, y_min, y_max, h,
+        n_xi, xi_min, dxi0, hist, (const double2 *)env_n, (const double2 *)env_np1, k0, dt,
+        n_sub);
+    return cudaGetLastError();
+}
+
 cudaError_t qs_launch_convert(cudaStream_t st, const double *src, float *dst, int64_t n) {
     if (n <= 0) return cudaSuccess;
     k_convert<<<blocks_for(n), kThreads, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+__global__ void k_abs2(const double *a, double *out, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double re = a[2 * k], im = a[2 * k + 1];
+        out[k] = re * re + im * im;
+    }
+}
+
+cudaError_t qs_launch_abs2(cudaStream_t st, const double *a, double *out, int64_t n) {
+    if (n <= 0) return cudaSuccess;
+    k_abs2<<<blocks_for(n), kThreads, 0, st>>>(a, out, n);
     return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ template <typename P>
 struct PS {
     double *x, *y;
     P *px, *py, *w;
-    const double *wd;  // float64 weights: n_* must cancel n_ion to rounding
+    double *wd;  // float64 weights: n_* must cancel n_ion to rounding
     double *na, *nb;   // n_* of this slice and of the next one
     P *jx, *jy, *txx, *txy, *tyy, *G;
 };
@@ -73,6 +73,18 @@ __device__ __forceinline__ void dep(P *g, const CicP<P> &c, P q) {
     atomicAdd(g + c.i01, q * c.w01);
     atomicAdd(g + c.i10, q * c.w10);
     atomicAdd(g + c.i11, q * c.w11);
+}
+
+// 1 / a in float64 for a >= psi_floor > 0 by Newton's iteration for the
+// reciprocal, r <- r (2 - a r), from the float32 reciprocal: each step doubles
+// the correct bits (24, 48, then float64 rounding).  Four float64 operations
+// and two conversions instead of a float64 divide, a long instruction
+// sequence on GB300's 1/64-rate float64 pipe.
+__device__ __forceinline__ double rcp_newton(double a) {
+    double r = (double)__frcp_rn((float)a);
+    r = r * fma(-a, r, 2.0);
+    r = r * fma(-a, r, 2.0);
+    return r;
 }
 
 // n_* of the initial particles
@@ -121,9 +133,17 @@ __device__ __forceinline__ void apply_guess(double *u, double *h1, double *h2, i
 // moment accumulators and the next-slice density buffer
 template <typename P>
 __device__ void phase_psi_rhs(const EngineArgs &A, const PS<P> &Q, const double *ncur,
-                              double *nnext, bool base, int j, Thr T, const Guess &g) {
+                              double *nnext, bool base, int j, int q, int m, Thr T,
+                              const Guess &g) {
     const int nn = A.N * A.N;
     double s = 0.0, cs = 0.0;
+    if (A.a2_base) {  // |A|^2 of this slice, linear in xi between base slices
+        const double frac = (double)q / (double)m;
+        const double *a0 = A.a2_base + (size_t)j * nn;
+        const double *a1 = (j + 1 < A.n_xi) ? a0 + nn : nullptr;
+        for (int i = T.t0; i < nn; i += T.nt)
+            A.a2[i] = q == 0 ? a0[i] : (1.0 - frac) * a0[i] + frac * (a1 ? a1[i] : 0.0);
+    }
     for (int i = T.t0; i < nn; i += T.nt) {
         if (g.active) apply_guess(A.psi, A.hist1[0], A.hist2[0], i, g);
         const double nv = (double)ncur[i];
@@ -159,20 +179,23 @@ __device__ void phase_moments(const EngineArgs &A, const PS<P> &Q, Thr T) {
         const double a = guard(1.0 + cic_gather(A.psi, cd), A.psi_floor, hits);
         const P px = Q.px[p], py = Q.py[p];
         const double p2 = (double)px * px + (double)py * py;
-        const double ia = 1.0 / a;  // one division per particle (FP64 divides are slow)
+        // one reciprocal per particle (float64 divides are slow)
+        const double ia = sizeof(P) == 8 ? 1.0 / a : rcp_newton(a);
         const P iap = (P)ia;
         const P vx = px * iap, vy = py * iap;
         const P wq = Q.w[p] * s;
+        // the laser's |A|^2 / 2 in the numerator of gamma (line after Eq. EoM_111)
+        const double ha2 = A.a2_base ? 0.5 * cic_gather(A.a2, cd) : 0.0;
         dep(Q.jx, c, wq * vx);
         dep(Q.jy, c, wq * vy);
         dep(Q.txx, c, wq * vx * vx);
         dep(Q.txy, c, wq * vx * vy);
         dep(Q.tyy, c, wq * vy * vy);
         if constexpr (sizeof(P) == 8) {
-            dep(Q.G, c, wq * ((1.0 + p2 + a * a) * (0.5 * ia)));  // gamma
+            dep(Q.G, c, wq * ((1.0 + p2 + a * a + ha2) * (0.5 * ia)));  // gamma
         } else {
             const double am1 = a - 1.0;  // gamma - 1 = (p^2 + psi^2) / (2 (1 + psi))
-            dep(Q.G, c, wq * (P)((p2 + am1 * am1) * (0.5 * ia)));
+            dep(Q.G, c, wq * (P)((p2 + am1 * am1 + ha2) * (0.5 * ia)));
         }
     }
     add_hits(A.sc, hits);
@@ -243,6 +266,21 @@ __device__ void phase_assemble1(const EngineArgs &A, const PS<P> &Q, const doubl
         }
         A.dpx[i] = dxo(A.psi, n, ix, i, inv2h);
         A.dpy[i] = dyo(A.psi, n, iy, i, inv2h);
+        if (A.dpx32) {
+            A.dpx32[i] = (float)A.dpx[i];
+            A.dpy32[i] = (float)A.dpy[i];
+        }
+        if (A.a2_base) {
+            // grad(|A|^2 / 4), even ghosts (the ghost repeats the edge cell)
+            const double *a2 = A.a2;
+            const double e = ix < n - 1 ? a2[i + 1] : a2[i];
+            const double w = ix > 0 ? a2[i - 1] : a2[i];
+            const double so = iy < n - 1 ? a2[i + n] : a2[i];
+            const double no = iy > 0 ? a2[i - n] : a2[i];
+            A.pondx[i] = 0.25 * (e - w) * inv2h;
+            A.pondy[i] = 0.25 * (so - no) * inv2h;
+            if (A.chi && q == 0) A.chi[(size_t)j * nn + i] = kap;  // Eq. laser_Enve
+        }
     }
     sez = block_sum(sez);
     if (threadIdx.x == 0) atomicAdd(&A.sc->fnorm[1][0], sez);
@@ -269,6 +307,7 @@ __device__ void phase_assemble2(const EngineArgs &A, const PS<P> &Q, const doubl
         if (a < A.psi_floor) a = A.psi_floor;
         const double jx = Q.jx[i], jy = Q.jy[i], txx = Q.txx[i], txy = Q.txy[i],
                      tyy = Q.tyy[i], G = g_total(Q.G, ncur, i), ez = A.ez[i], bz = A.bz[i];
+        if (A.bz32) A.bz32[i] = (float)bz;  // B_z is final here
         const double gx = A.dpx[i], gy = A.dpy[i];
         const double ia = 1.0 / a, Gia2 = G * ia * ia;
         double sx = dx0(A.jz, n, ix, i, inv2h) - dx0(Q.txx, n, ix, i, inv2h) -
@@ -277,6 +316,11 @@ __device__ void phase_assemble2(const EngineArgs &A, const PS<P> &Q, const doubl
         double sy = dy0(A.jz, n, iy, i, inv2h) - dx0(Q.txy, n, ix, i, inv2h) -
                     dy0(Q.tyy, n, iy, i, inv2h) + Gia2 * gy +
                     (jx * bz - jy * ez - txy * gx - tyy * gy) * ia;
+        if (A.a2_base) {  // -n_* grad(|A|^2/4) / (1+psi)^2 of Eq. FluxCurr1_A
+            const double nia2 = ncur[i] * ia * ia;
+            sx -= nia2 * A.pondx[i];
+            sy -= nia2 * A.pondy[i];
+        }
         A.f_bx[i] = sy;
         A.f_by[i] = -sx;
         sbx += sy * sy;
@@ -334,21 +378,42 @@ __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, b
     const double s = A.inv_h * A.inv_h;
     const P half = (P)(0.5 * dxi), dxp = (P)dxi;
     unsigned hits = 0;
-    double vmax = 0.0;
+    P vm = P(0);  // V_max (refined form: its square, in float32)
     for (int64_t p = T.t0; p < A.np; p += T.nt) {
         const double x = Q.x[p], y = Q.y[p];
         const Cic cd = cic_stencil_inv(x, y, A.x_min, A.y_min, A.inv_h, A.N);
         const CicP<P> c = cic_p<P>(cd);
         const double a = guard(1.0 + cic_gather(A.psi, cd), A.psi_floor, hits);
-        const double ia = 1.0 / a;
+        const double ia = sizeof(P) == 8 ? 1.0 / a : rcp_newton(a);
         const P iap = (P)ia;
-        const P gx = gat<P>(A.dpx, c), gy = gat<P>(A.dpy, c);
-        const P bx = gat<P>(A.bx, c), by = gat<P>(A.by, c), bz = gat<P>(A.bz, c);
+        P gx, gy, bx, by, bz;
+        if constexpr (sizeof(P) == 8) {
+            gx = gat<P>(A.dpx, c);
+            gy = gat<P>(A.dpy, c);
+            bx = gat<P>(A.bx, c);
+            by = gat<P>(A.by, c);
+            bz = gat<P>(A.bz, c);
+        } else {  // the float32 copies: no conversions
+            gx = gat<P>(A.dpx32, c);
+            gy = gat<P>(A.dpy32, c);
+            bx = gat<P>(A.bx32, c);
+            by = gat<P>(A.by32, c);
+            bz = gat<P>(A.bz32, c);
+        }
         P px = Q.px[p], py = Q.py[p];
-        // half kick: gamma grad psi / (1+psi) + e_z x B_perp
-        const double gam = (1.0 + (double)px * px + (double)py * py + a * a) * (0.5 * ia);
-        const P pxm = px + half * ((P)gam * gx * iap - by);
-        const P pym = py + half * ((P)gam * gy * iap + bx);
+        // laser (Eq. EoM_111): |A|^2 / 2 in gamma and the ponderomotive force
+        // -grad(|A|^2/4) / (1+psi); zero without a laser
+        double ha2 = 0.0;
+        P fx = P(0), fy = P(0);
+        if (A.a2_base) {
+            ha2 = 0.5 * cic_gather(A.a2, cd);
+            fx = gat<P>(A.pondx, c);
+            fy = gat<P>(A.pondy, c);
+        }
+        // half kick: (gamma grad psi - grad(|A|^2/4)) / (1+psi) + e_z x B_perp
+        const double gam = (1.0 + (double)px * px + (double)py * py + a * a + ha2) * (0.5 * ia);
+        const P pxm = px + half * (((P)gam * gx - fx) * iap - by);
+        const P pym = py + half * (((P)gam * gy - fy) * iap + bx);
         // rotation by the B_z term (e_z x p) B_z / (1+psi)
         const P tau = half * bz * iap;
         const P pxp = pxm - tau * pym;
@@ -356,9 +421,10 @@ __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, b
         const P sr = P(2) * tau / (P(1) + tau * tau);
         const P pxr = pxm - sr * pyp;
         const P pyr = pym + sr * pxp;
-        const double gam2 = (1.0 + (double)pxr * pxr + (double)pyr * pyr + a * a) * (0.5 * ia);
-        px = pxr + half * ((P)gam2 * gx * iap - by);
-        py = pyr + half * ((P)gam2 * gy * iap + bx);
+        const double gam2 =
+            (1.0 + (double)pxr * pxr + (double)pyr * pyr + a * a + ha2) * (0.5 * ia);
+        px = pxr + half * (((P)gam2 * gx - fx) * iap - by);
+        py = pyr + half * (((P)gam2 * gy - fy) * iap + bx);
         double nx = x + (double)(dxp * px * iap);
         double ny = y + (double)(dxp * py * iap);
         if (nx > A.x_max) { nx = 2.0 * A.x_max - nx; px = -px; }
@@ -369,16 +435,144 @@ __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, b
         Q.y[p] = ny;
         Q.px[p] = px;
         Q.py[p] = py;
-        vmax = fmax(vmax, sqrt((double)px * px + (double)py * py) * ia);
+        if constexpr (sizeof(P) == 8) {
+            vm = fmax(vm, sqrt((double)px * px + (double)py * py) * ia);
+        } else {  // float32 (the step rule needs a few digits); squared, root below
+            vm = fmaxf(vm, (px * px + py * py) * (iap * iap));
+        }
         const Cic c2 = cic_stencil_inv(nx, ny, A.x_min, A.y_min, A.inv_h, A.N);
         cic_deposit(nnext, c2, Q.wd[p] * s);
     }
     add_hits(A.sc, hits);
-    vmax = block_max(vmax);
+    double vmax = block_max((double)vm);
+    if (sizeof(P) == 4) vmax = sqrt(vmax);
     if (threadIdx.x == 0) {
         atomicMax(&A.sc->vmax_bits[pk & 1], (unsigned long long)__double_as_longlong(vmax));
         atomicMax(&A.sc->vmax_all_bits, (unsigned long long)__double_as_longlong(vmax));
     }
+}
+
+// ---------------------------------------------------------------------------
+// cell sort inside the slice loop
+// ---------------------------------------------------------------------------
+
+// exclusive scan of v over the block (any blockDim.x <= 1024); returns the
+// prefix of this thread and the block total in *total
+__device__ int block_exscan(int v, int *total) {
+    __shared__ int ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        int t = lane < nw ? ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;  // inclusive prefix of the warp sums
+    }
+    __syncthreads();
+    *total = ws[((blockDim.x + 31) >> 5) - 1];
+    return x - v + (wid > 0 ? ws[wid - 1] : 0);
+}
+
+// Stable counting sort of the plasma by (cell, id), cell = iy N + ix of the
+// position's cell (floor, clamped), the order of the standalone cell sort;
+// the arrays are gathered into the spare set and copied back (the slice
+// loop's particle pointers stay fixed: swapping them would keep two sets of
+// pointers live in registers through the whole loop).
+template <typename P>
+__device__ __noinline__ bool sort_plasma(const EngineArgs &A, const PS<P> &Q, const Sync &S,
+                                         int bid, int nblk) {
+    int32_t *const id = A.id, *const id2 = A.id2;
+    P *const px2 = (P *)A.px2, *const py2 = (P *)A.py2, *const w2 = (P *)A.w2;
+    const int nn = A.N * A.N;
+    const Thr T = grid_thr(bid, nblk);
+    for (int i = T.t0; i < nn; i += T.nt) A.s_count[i] = 0;
+    SYNC(90);
+    for (int64_t p = T.t0; p < A.np; p += T.nt) {
+        int ix = (int)floor((Q.x[p] - A.x_min) * A.inv_h);
+        int iy = (int)floor((Q.y[p] - A.y_min) * A.inv_h);
+        ix = min(max(ix, 0), A.N - 1);
+        iy = min(max(iy, 0), A.N - 1);
+        const int c = iy * A.N + ix;
+        A.s_cell[p] = c;
+        atomicAdd(A.s_count + c, 1);
+    }
+    SYNC(91);
+    // exclusive scan: each block its chunk of cells, then the chunk offsets
+    const int ch = (nn + nblk - 1) / nblk;
+    const int c0 = min(bid * ch, nn), c1 = min(c0 + ch, nn);
+    int run = 0;
+    for (int b = c0; b < c1; b += blockDim.x) {
+        const int i = b + (int)threadIdx.x;
+        int tot;
+        const int pre = block_exscan(i < c1 ? A.s_count[i] : 0, &tot);
+        if (i < c1) A.s_offset[i] = run + pre;
+        run += tot;
+    }
+    if (threadIdx.x == 0) A.s_bsum[bid] = run;
+    SYNC(92);
+    __shared__ int s_base;
+    if (threadIdx.x == 0) {
+        int base = 0;
+        for (int b = 0; b < bid; ++b) base += A.s_bsum[b];
+        s_base = base;
+        if (bid == nblk - 1) A.s_offset[nn] = base + run;
+    }
+    __syncthreads();
+    for (int i = c0 + (int)threadIdx.x; i < c1; i += blockDim.x) {
+        A.s_offset[i] += s_base;
+        A.s_cursor[i] = A.s_offset[i];
+    }
+    SYNC(93);
+    for (int64_t p = T.t0; p < A.np; p += T.nt)
+        A.s_order[atomicAdd(A.s_cursor + A.s_cell[p], 1)] = (int32_t)p;
+    SYNC(94);
+    // within a cell, ascending id (segments hold a few particles)
+    for (int i = T.t0; i < nn; i += T.nt) {
+        const int b = A.s_offset[i], e = A.s_offset[i + 1];
+        for (int k = b + 1; k < e; ++k) {
+            const int32_t v = A.s_order[k], key = id[v];
+            int m = k - 1;
+            while (m >= b && id[A.s_order[m]] > key) {
+                A.s_order[m + 1] = A.s_order[m];
+                --m;
+            }
+            A.s_order[m + 1] = v;
+        }
+    }
+    SYNC(95);
+    const bool sep_wd = (const void *)Q.wd != (const void *)Q.w;
+    for (int64_t s = T.t0; s < A.np; s += T.nt) {
+        const int32_t p = A.s_order[s];
+        A.x2[s] = Q.x[p];
+        A.y2[s] = Q.y[p];
+        px2[s] = Q.px[p];
+        py2[s] = Q.py[p];
+        w2[s] = Q.w[p];
+        if (sep_wd) A.wd2[s] = Q.wd[p];
+        id2[s] = id[p];
+    }
+    SYNC(96);
+    for (int64_t s = T.t0; s < A.np; s += T.nt) {
+        Q.x[s] = A.x2[s];
+        Q.y[s] = A.y2[s];
+        Q.px[s] = px2[s];
+        Q.py[s] = py2[s];
+        Q.w[s] = w2[s];
+        if (sep_wd) Q.wd[s] = A.wd2[s];
+        id[s] = id2[s];
+    }
+    SYNC(97);
+    return true;
 }
 
 // One 3D step of one instance on `nblk` blocks (this one is `bid`): the xi
@@ -405,19 +599,29 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
         Q = PS<P>{A.x, A.y, A.px, A.py, A.w, A.w, A.n_a, A.n_b,
                   A.jx, A.jy, A.txx, A.txy, A.tyy, A.G};
     }
+    // the spare particle set of the in-loop sort (not with the adjoint's
+    // checkpoints or slice store: those keep the lattice's order)
+    const bool sorting = A.sort_every > 0 && A.x2 && !A.ckpt && !A.seg_p;
+    int n_sorts = 0;
     double *ncur = Q.na, *nnext = Q.nb;
     phase_deposit_n<P>(A, Q, ncur, T);
     if (!S(1)) return false;
 
     const SolveSpec Vpsi{1, 0, {A.psi, nullptr}, {A.f_psi, nullptr}, false};
     const SolveSpec Veb{2, 1, {A.ez, A.bz}, {A.f_ez, A.f_bz}, false};
-    const SolveSpec Vbp{2, 2, {A.bx, A.by}, {A.f_bx, A.f_by}, true};
+    const SolveSpec Vbp{2, 2, {A.bx, A.by}, {A.f_bx, A.f_by}, true,
+                        {REF ? A.bx32 : nullptr, REF ? A.by32 : nullptr}};
 
     int m = A.m_sched ? A.m_sched[A.j_begin] : 1;
     int slot = 0, pk = 0, sub = 0;
     int have = 0;                        // previous solutions available for the guess
     double gx0 = 0.0, gx1 = 0.0, gx2 = 0.0;  // their xi
     for (int j = A.j_begin; j < A.j_end; ++j) {
+        if (sorting && j > A.j_begin && j % A.sort_every == 0) {
+            if (!sort_plasma<P>(A, Q, S, bid, nblk)) return false;
+            ++n_sorts;
+            if (lead) sc->sorts = n_sorts;
+        }
         if (lead && A.diag_m) {
             A.diag_m[j] = m;
             if (m > sc->max_m) sc->max_m = m;
@@ -437,7 +641,7 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
             const bool base = (q == 0);
             const double xs = j * A.dxi0 + q * dxi;  // xi of this slice (from xi_min)
             const Guess g = make_guess(A.ws_order, have, xs, gx0, gx1, gx2);
-            phase_psi_rhs<P>(A, Q, ncur, nnext, base, j, T, g);
+            phase_psi_rhs<P>(A, Q, ncur, nnext, base, j, q, m, T, g);
             if (!S(2)) return false;
             if (!mg_solve<REF>(A, S, Vpsi, slot, bid, nblk, smem, s_inv_ready)) return false;
             phase_moments<P>(A, Q, T);
@@ -504,7 +708,7 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(const __gri
     }
     __syncthreads();
     const Sync S{A.sc, &A.sc->bar_arrive, gridDim.x, A.spin_cycles, A.trace, A.trace_cap,
-                 &s_epoch, blockIdx.x == 0};
+                 &s_epoch, blockIdx.x == 0, A.cl_size};
     run_step<REF>(A, blockIdx.x, gridDim.x, S, smem, s_inv_ready);
 }
 

@@ -3,6 +3,7 @@
 // translation units (one per form), which hand out their launch handles.
 #include <cuda_runtime.h>
 
+#include "qs_cluster.cuh"
 #include "qs_tile.cuh"
 
 const void *qs_kernel_engine(int precision) {
@@ -14,7 +15,7 @@ const void *qs_kernel_engine_batched(int precision) {
                                         : qs_kernel_engine_batched_fp64();
 }
 
-int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks) {
+int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks, int cluster) {
     const void *fn = qs_kernel_engine(precision);
     int per_sm = 0, sms = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) !=
@@ -26,7 +27,31 @@ int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *bloc
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return -1;
     *blocks = per_sm * sms;
+    if (cluster > 1) {  // co-resident whole clusters (they must fit in the GPCs)
+        if (cluster > 8 &&
+            cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess)
+            return -1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(sms - sms % cluster));
+        cfg.blockDim = dim3(QS_ENGINE_THREADS);
+        cfg.dynamicSmemBytes = smem_bytes;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) != cudaSuccess) return -1;
+        if (nc * cluster < *blocks) *blocks = nc * cluster;
+    }
     return 0;
+}
+
+size_t qs_cluster_smem_bytes(const int *lev_n, int nlev, int cluster) {
+    return qsclu::cluster_layout(lev_n, nlev, cluster).total;
 }
 
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
@@ -83,6 +108,27 @@ cudaError_t qs_launch_engine(cudaStream_t st, const EngineArgs &a, int grid_bloc
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid_blocks), dim3(QS_ENGINE_THREADS), args,
-                                       smem_bytes, st);
+    if (a.cl_size <= 1)
+        return cudaLaunchCooperativeKernel(fn, dim3(grid_blocks), dim3(QS_ENGINE_THREADS), args,
+                                           smem_bytes, st);
+    // cooperative (every block resident: the grid barrier) and clustered
+    if (a.cl_size > 8) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid_blocks);
+    cfg.blockDim = dim3(QS_ENGINE_THREADS);
+    cfg.dynamicSmemBytes = smem_bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = (unsigned)a.cl_size;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }

@@ -25,6 +25,7 @@ struct DevScalars {
     long long vcycles[3];
     long long slices;
     long long pushes;
+    long long sorts;  // cell sorts of the plasma inside the slice loop
     int max_m;
     int not_converged;
     double max_relres;
@@ -99,14 +100,41 @@ struct EngineArgs {
     float lev_h2f[QS_MAX_LEV], lev_inv_h2f[QS_MAX_LEV];
     LevelArrays lev[QS_MAX_LEV];
     int block_level_n;  // levels with side <= this are relaxed by one block
+    // float64 solves of small grids by the launch's first thread-block
+    // cluster (qs_cluster.cuh): cluster size of the launch (<= 1: off) and
+    // the byte offset of the cluster's arrays in dynamic shared memory
+    int cl_size;
+    int cl_smem_offset;
     // refined form: float32 inner hierarchy (level 0: correction e, residual r)
     int precision;
     int tile_x, tile_y;  // output tile of the staged grid levels (refined form)
     int block_smem_offset; // byte offset of the coarse part in shared memory
     int tile_smem_offset;  // byte offset of the staged tile after the coarse part
     float *e32[2], *r32[2][2], *k32, *d32;  // r32[buffer][component]
+    // refined form: float32 copies of the push's fields (grad psi, B), so
+    // that its gathers need no float64 conversions
+    float *dpx32, *dpy32, *bx32, *by32, *bz32;
     double *r64[2];  // float64 residual of the refined iteration
     LevelArrays32 lev32[QS_MAX_LEV];
+    // cell sort of the plasma inside the slice loop: every sort_every base
+    // slices (0: never) the particle arrays are reordered by (cell, id) into
+    // the spare arrays x2 ... id2 (counting sort; count, offset and cursor
+    // have N^2 (+1) entries, cell and order np, bsum one per block)
+    int sort_every;
+    int32_t *id, *id2;
+    double *x2, *y2, *wd2;
+    void *px2, *py2, *w2;  // in the particle precision
+    int32_t *s_count, *s_offset, *s_cursor, *s_cell, *s_order, *s_bsum;
+    // laser driver (Eq. EoM_111 and the line after it, Eq. FluxCurr1_A):
+    // |A|^2 of the envelope on the base slices [n_xi][N*N] (nullptr: no
+    // laser); the value at the current slice (linear in xi between base
+    // slices, like the driver current), grad(|A|^2 / 4) by central
+    // differences with even ghosts (A is odd at the walls), and
+    // chi = n_* / (1+psi) stored at the base slices [n_xi][N*N] for the
+    // envelope advance of Eq. laser_Enve (nullptr: not stored)
+    const double *a2_base;
+    double *a2, *pondx, *pondy;
+    double *chi;
     // outputs
     double *hist;        // [5][n_xi][N*N]
     const double *jzb;   // [n_xi][N*N]
@@ -264,7 +292,16 @@ cudaError_t qs_launch_beam_deposit(cudaStream_t st, const qs_beam &b, int n, dou
 cudaError_t qs_launch_beam_push(cudaStream_t st, const qs_beam &b, int n, double x_min,
                                 double x_max, double y_min, double y_max, double h, int n_xi,
                                 double xi_min, double dxi0, const double *hist, double dt);
+cudaError_t qs_launch_beam_push_dla(cudaStream_t st, const qs_beam &b, int n, double x_min,
+                                    double x_max, double y_min, double y_max, double h,
+                                    int n_xi, double xi_min, double dxi0, const double *hist,
+                                    const double *env_n, const double *env_np1, double k0,
+                                    double dt, int n_sub);
 cudaError_t qs_launch_convert(cudaStream_t st, const double *src, float *dst, int64_t n);
+// |a|^2 of n interleaved complex128 values
+cudaError_t qs_launch_abs2(cudaStream_t st, const double *a, double *out, int64_t n);
+// implemented in qs_laser.cu
+void qs_laser_shape(const qs_laser *s, int *n, double *width, int *n_xi, double *dxi);
 // implemented in qs_grad_aux.cu
 cudaError_t qs_launch_beam_gain(cudaStream_t st, const qs_beam &b, int n, double x_min,
                                 double x_max, double y_min, double y_max, double h, int n_xi,
@@ -303,7 +340,9 @@ int qs_engine_batched_max_blocks(int device, int precision, size_t smem_bytes, i
 cudaError_t qs_launch_adjoint(cudaStream_t st, const EngineArgs &a, const AdjArgs &d,
                               int grid_blocks, size_t smem_bytes);
 int qs_adjoint_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
-int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
+int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks,
+                         int cluster = 1);
+size_t qs_cluster_smem_bytes(const int *lev_n, int nlev, int cluster);
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
                             int tile_x, int tile_y, int nu, int nu2, size_t *block_offset,
                             size_t *tile_offset);

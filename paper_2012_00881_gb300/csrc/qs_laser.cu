@@ -339,6 +339,7 @@ int cuda_status(cudaError_t e) {
 
 struct qs_laser {
     int n = 0, n_xi = 0;
+    double width = 0.0, dxi = 0.0;
     cudaStream_t stream = nullptr;
     int grid_blocks = 0;
     LzArgs args{};
@@ -357,6 +358,8 @@ extern "C" int qs_laser_create(int n, double width, int n_xi, double k0, double 
     if (!s) return QS_ERR_OOM;
     s->n = n;
     s->n_xi = n_xi;
+    s->width = width;
+    s->dxi = dxi;
     s->stream = static_cast<cudaStream_t>(cuda_stream);
     LzArgs &A = s->args;
     A.n = n;
@@ -459,4 +462,13 @@ extern "C" void qs_laser_destroy(qs_laser *s) {
     if (s->dev) cudaFree(s->dev);
     if (s->pinned) cudaFreeHost(s->pinned);
     delete s;
+}
+
+// Grid of an envelope object (for the laser-driven 3D step, which checks that
+// the slice loop and the envelope share cells, box and slices).
+void qs_laser_shape(const qs_laser *s, int *n, double *width, int *n_xi, double *dxi) {
+    *n = s->n;
+    *width = s->width;
+    *n_xi = s->n_xi;
+    *dxi = s->dxi;
 }

@@ -43,9 +43,13 @@ __device__ __forceinline__ int walls(int ix, int iy, int n) {
     return (ix == 0) + (ix == n - 1) + (iy == 0) + (iy == n - 1);
 }
 
+// 1 / (4 + walls) without a divide (a float64 divide is a long sequence on
+// GB300's 1/64-rate float64 pipe, and a select may evaluate it regardless)
 template <typename T>
 __device__ __forceinline__ T const_inv_diag(int nw) {
-    return nw == 0 ? T(0.25) : (nw == 1 ? T(0.2) : (nw == 2 ? T(1.0 / 6.0) : T(1) / T(4 + nw)));
+    return nw == 0 ? T(0.25)
+                   : (nw == 1 ? T(0.2)
+                              : (nw == 2 ? T(1.0 / 6.0) : (nw == 3 ? T(1.0 / 7.0) : T(0.125))));
 }
 
 // Walk q = t0, t0 + nt, ... over a row-major index space with `w` columns,
@@ -82,10 +86,18 @@ __device__ __forceinline__ void cp_async(T *dst, const T *src, bool valid) {
 struct Walk {
     int q, row, col, nt, drow, dcol, w;
     __device__ __forceinline__ Walk(int t0, int nt_, int w_) : q(t0), nt(nt_), w(w_) {
-        row = t0 / w;
-        col = t0 - row * w;
-        drow = nt / w;
-        dcol = nt - drow * w;
+        if ((w & (w - 1)) == 0) {  // power of two: shifts instead of divides
+            const int sh = __ffs(w) - 1;
+            row = t0 >> sh;
+            col = t0 & (w - 1);
+            drow = nt >> sh;
+            dcol = nt & (w - 1);
+        } else {
+            row = t0 / w;
+            col = t0 - row * w;
+            drow = nt / w;
+            dcol = nt - drow * w;
+        }
     }
     __device__ __forceinline__ void next() {
         q += nt;
@@ -165,7 +177,7 @@ __device__ void relax_half(const Lvl<T> L, int color, Thr R) {
 // C.f = 4-cell average of the residual of F; C.u = 0; screened levels also
 // get C.k (4-cell average of F.k) and C.d
 template <typename T, int NC>
-__device__ void restrict_res(const Lvl<T> F, const Lvl<T> C, Thr R) {
+__device__ void restrict_res(const Lvl<T> F, const Lvl<T> C, Thr R, bool with_k = true) {
     const int n = F.n, m = C.n;
     const T inv_h2 = F.inv_h2t;
     const T *const k = F.k;
@@ -184,7 +196,7 @@ __device__ void restrict_res(const Lvl<T> F, const Lvl<T> C, Thr R) {
             C.f[c][w.q] = T(0.25) * s;
             C.u[c][w.q] = T(0);
         }
-        if (k) {
+        if (k && with_k) {
             const T kk = T(0.25) * (k[i0] + k[i0 + 1] + k[i0 + n] + k[i0 + n + 1]);
             C.k[w.q] = kk;
             C.d[w.q] = T(1) / (T(4 + walls(I, J, m)) + ch2 * kk);

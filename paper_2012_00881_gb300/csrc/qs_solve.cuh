@@ -9,6 +9,7 @@
 
 #include <type_traits>
 
+#include "qs_cluster.cuh"
 #include "qs_tile.cuh"
 
 namespace {
@@ -52,6 +53,8 @@ struct Sync {
     int trace_cap;
     unsigned long long *epoch;  // this block's barrier count (shared memory)
     bool tracer;                // this block records the phase trace
+    int cl = 1;                 // cluster size of the launch (> 1: the first
+                                // cluster solves alone, see mg_solve_cluster)
     __device__ bool operator()(int where) const {
         __shared__ int s_ok;
         __syncthreads();
@@ -89,6 +92,25 @@ struct Sync {
             }
         }
         __syncthreads();
+        if (cl > 1 && (int)blockIdx.x < cl) {
+            // The first cluster's blocks take one decision: after a timed-out
+            // wait some blocks may see the barrier complete and others the
+            // error word, and a block that went on into the cluster solve
+            // would wait at a cluster barrier for one that has left.
+            namespace cg = cooperative_groups;
+            cg::cluster_group clu = cg::this_cluster();
+            __shared__ int s_oks[16];
+            if (threadIdx.x == 0)
+                clu.map_shared_rank(s_oks, 0)[clu.block_rank()] = s_ok;
+            clu.sync();
+            if (threadIdx.x == 0) {
+                const int *all = clu.map_shared_rank(s_oks, 0);
+                int ok = 1;
+                for (int b = 0; b < cl; ++b) ok &= all[b] != 0;
+                s_ok = ok;
+            }
+            clu.sync();  // s_oks is rewritten at the next barrier
+        }
         return s_ok != 0;
     }
 };
@@ -114,6 +136,30 @@ __device__ double block_sum(double v) {
     }
     return t;
 }
+// four float32 sums over the block in one pass (one block barrier); valid in
+// thread 0
+__device__ void block_sum4f(float v[4]) {
+    __shared__ float red4[32][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        for (int o = 16; o; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red4[wid][k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float t = lane < nw ? red4[lane][k] : 0.f;
+            for (int o = 16; o; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            v[k] = t;
+        }
+    }
+    __syncthreads();  // red4 is reused by the next call
+}
+
 __device__ double block_max(double v) {
     __shared__ double red[32];
     for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -142,6 +188,7 @@ struct SolveSpec {
     double *u[2];
     double *f[2];
     bool screened;
+    float *u32[2] = {nullptr, nullptr};  // refined form: float32 copy of the solution
 };
 
 // The hierarchy descriptors live in shared memory, one copy per block:
@@ -324,16 +371,18 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
     // every up leg and the level-0 update in one phase
     int TX, TY;
     level_tile(A, H.lv[0].n, nblk, TX, TY);
-    double nrm[4] = {0.0, 0.0, 0.0, 0.0};
+    // ||r||^2, ||u||^2 of the tile in float32: the stopping test needs a
+    // few digits of them
+    float nrm[4] = {0.f, 0.f, 0.f, 0.f};
     qstile::up_cascade_fused<NC>(H, lg, (const float *)smem, (const float *)smem + 2 * mg2,
                                  A.nu2, TX, TY, sm, bid, nblk, *fused, nrm, mk);
+    block_sum4f(nrm);
+    if (threadIdx.x == 0)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        double t = block_sum(nrm[c]);
-        if (threadIdx.x == 0) atomicAdd(norms_out + c, t);
-        t = block_sum(nrm[2 + c]);
-        if (threadIdx.x == 0) atomicAdd(norms_out + 2 + c, t);
-    }
+        for (int c = 0; c < NC; ++c) {
+            atomicAdd(norms_out + c, (double)nrm[c]);
+            atomicAdd(norms_out + 2 + c, (double)nrm[2 + c]);
+        }
     if (bid == 0 && threadIdx.x == 0)
         for (int e = 0; e < 4; ++e) norms_clear[e] = 0.0;
     mk(67);
@@ -385,6 +434,237 @@ __device__ void residual_norm(const EngineArgs &A, const SolveSpec &V, double *o
     }
 }
 
+// Float64 solve by the launch's first cluster (see qs_cluster.cuh); the
+// other blocks return at once.  fn: ||f||^2 per component (thread 0).
+// Returns the V-cycles done; the caller's grid barrier follows.
+template <int NC>
+__device__ void mg_solve_cluster(const EngineArgs &A, const SolveSpec &V, int bid,
+                                 void *smem_base, qsmg::CoarseInv ci, const double *fn) {
+    namespace cg = cooperative_groups;
+    if (bid >= A.cl_size) return;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = A.cl_size, rank = (int)cl.block_rank();
+    void *cb = (char *)smem_base + A.cl_smem_offset;
+    __shared__ qsclu::Layout Y;
+    __shared__ int s_conv;
+    __shared__ double s_rel;
+    if (threadIdx.x == 0) Y = qsclu::cluster_layout(A.lev_n, A.nlev, C);
+    __syncthreads();
+    const int ld = Y.ld, L = Y.L;
+    const bool scr = V.screened;
+    auto dl = [&](int l) {
+        qsclu::DLvl D;
+        D.n = Y.n[l];
+        D.R = Y.R[l];
+        D.row0 = rank * D.R;
+        for (int c = 0; c < 2; ++c) {
+            const int cc = c < NC ? c : 0;
+            D.u[c] = qsclu::arr(cb, Y, l, cc);
+            D.f[c] = qsclu::arr(cb, Y, l, 2 + cc);
+            D.up_u[c] = rank > 0 ? cl.map_shared_rank(D.u[c], rank - 1) : nullptr;
+            D.dn_u[c] = rank < C - 1 ? cl.map_shared_rank(D.u[c], rank + 1) : nullptr;
+        }
+        D.k = scr ? qsclu::arr(cb, Y, l, 4) : nullptr;
+        D.d = scr ? qsclu::arr(cb, Y, l, 5) : nullptr;
+        D.up_k = D.dn_k = nullptr;
+        D.h2 = A.lev_h2[l];
+        D.inv_h2 = A.lev_inv_h2[l];
+        D.omega = A.omega;
+        return D;
+    };
+    auto lv = [&](int l) {  // a local level of block 0 (this block's copy of the layout)
+        Lvl<double> v;
+        for (int c = 0; c < 2; ++c) {
+            const int cc = c < NC ? c : 0;
+            v.u[c] = qsclu::arr(cb, Y, l, cc);
+            v.f[c] = qsclu::arr(cb, Y, l, 2 + cc);
+        }
+        v.k = scr ? qsclu::arr(cb, Y, l, 4) : nullptr;
+        v.d = scr ? qsclu::arr(cb, Y, l, 5) : nullptr;
+        v.n = Y.n[l];
+        v.h2 = v.h2t = A.lev_h2[l];
+        v.inv_h2 = v.inv_h2t = A.lev_inv_h2[l];
+        v.omega = A.omega;
+        return v;
+    };
+    // level 0: this block's rows of the warm start, the source and kappa
+    {
+        const qsclu::DLvl D = dl(0);
+        const size_t g0 = (size_t)D.row0 * D.n;
+        for (int q = threadIdx.x; q < D.R * D.n; q += blockDim.x) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                D.u[c][q] = V.u[c][g0 + q];
+                D.f[c][q] = V.f[c][g0 + q];
+            }
+            if (scr) {
+                D.k[q] = A.kap[g0 + q];
+                D.d[q] = A.invd0[g0 + q];
+            }
+        }
+    }
+    cl.sync();
+    double *const slots0 = cl.map_shared_rank((double *)((char *)cb + Y.slots), 0);
+    const double fl = 1e-13 * A.lev_inv_h2[0];
+    const qsmg::Marks mk{A.trace, &A.sc->trace_n, A.trace_cap};  // block 0, thread 0
+    int it = 0;
+    bool conv = false;
+    for (;;) {
+        if (it > 0) {  // ||f - A u||^2 and ||u||^2 of the cluster's level 0
+            const qsclu::DLvl D = dl(0);
+            double s[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int q = threadIdx.x; q < D.R * D.n; q += blockDim.x) {
+                const int ly = q / D.n, x = q - ly * D.n;
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const double r = qsclu::d_res(D, c, x, D.row0 + ly, q);
+                    s[c] += r * r;
+                    s[2 + c] += D.u[c][q] * D.u[c][q];
+                }
+            }
+            for (int e = 0; e < 4; ++e) {
+                const double t = block_sum(s[e]);
+                if (threadIdx.x == 0) slots0[rank * 4 + e] = t;
+            }
+            cl.sync();
+            __shared__ double s_tot[4];
+            if (threadIdx.x < 32) {  // warp 0: one remote load per lane, then a warp sum
+                double tot[4];
+                for (int e = 0; e < 4; ++e) {
+                    double v = 0.0;
+                    for (int b = threadIdx.x; b < C; b += 32) v += slots0[b * 4 + e];
+                    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                    tot[e] = v;
+                }
+                if (threadIdx.x == 0)
+                    for (int e = 0; e < 4; ++e) s_tot[e] = tot[e];
+            }
+            if (threadIdx.x == 0) {
+                const double *tot = s_tot;
+                int cv = 1;
+                double rel = 0.0;
+                for (int c = 0; c < NC; ++c) {
+                    if (fn[c] == 0.0) continue;
+                    double thr = fmax(A.mg_tol * A.mg_tol * fn[c], A.mg_atol * A.mg_atol);
+                    thr = fmax(thr, fl * fl * tot[2 + c]);
+                    if (tot[c] > thr) cv = 0;
+                    rel = fmax(rel, sqrt(tot[c] / fn[c]));
+                }
+                s_conv = cv;
+                s_rel = rel;
+            }
+            __syncthreads();
+            conv = s_conv != 0;
+            mk(70);
+            if (conv || it >= A.mg_max_vcycles) break;
+        }
+        // down: the distributed levels
+        for (int l = 0; l < ld; ++l) {
+            const qsclu::DLvl D = dl(l);
+            const int nu = D.n > A.block_level_n ? A.nu1 : A.nu1c;
+            for (int s = 0; s < nu; ++s) {
+                qsclu::d_relax<NC>(D, 0);
+                cl.sync();
+                qsclu::d_relax<NC>(D, 1);
+                cl.sync();
+            }
+            const int m = Y.n[l + 1];
+            double *cu[2], *cf[2], *ck = nullptr, *cd = nullptr;
+            int crow0;
+            if (l + 1 < ld) {  // into this block's strip of the next level
+                for (int c = 0; c < 2; ++c) {
+                    cu[c] = qsclu::arr(cb, Y, l + 1, c < NC ? c : 0);
+                    cf[c] = qsclu::arr(cb, Y, l + 1, 2 + (c < NC ? c : 0));
+                }
+                if (scr) {
+                    ck = qsclu::arr(cb, Y, l + 1, 4);
+                    cd = qsclu::arr(cb, Y, l + 1, 5);
+                }
+                crow0 = D.row0 >> 1;
+            } else {  // into block 0's whole first local level
+                for (int c = 0; c < 2; ++c) {
+                    cu[c] = cl.map_shared_rank(qsclu::arr(cb, Y, ld, c < NC ? c : 0), 0);
+                    cf[c] = cl.map_shared_rank(qsclu::arr(cb, Y, ld, 2 + (c < NC ? c : 0)), 0);
+                }
+                if (scr) {
+                    ck = cl.map_shared_rank(qsclu::arr(cb, Y, ld, 4), 0);
+                    cd = cl.map_shared_rank(qsclu::arr(cb, Y, ld, 5), 0);
+                }
+                crow0 = 0;
+            }
+            qsclu::d_restrict<NC>(D, m, crow0, cu, cf, ck, cd, A.lev_h2[l + 1], it == 0);
+            cl.sync();
+            mk(71 + l);
+        }
+        // the local levels in block 0 (all its warps: each SM sub-partition
+        // holds a quarter of the float64 pipe), down to the coarsest inverse
+        if (rank == 0) {
+            const Thr B{(int)threadIdx.x, (int)blockDim.x};
+            for (int l = ld; l < L - 1; ++l) {
+                const Lvl<double> F = lv(l), Cc = lv(l + 1);
+                const int nu = F.n > A.block_level_n ? A.nu1 : A.nu1c;
+                for (int s = 0; s < nu; ++s) {
+                    qsmg::relax_half<double, NC>(F, 0, B);
+                    __syncthreads();
+                    qsmg::relax_half<double, NC>(F, 1, B);
+                    __syncthreads();
+                }
+                qsmg::restrict_res<double, NC>(F, Cc, B, it == 0);
+                __syncthreads();
+            }
+            double *work = (double *)((char *)cb + Y.work);
+            qsmg::coarse_solve<double, NC>(lv(L - 1), work, ci);
+            for (int l = L - 2; l >= ld; --l) {
+                const Lvl<double> F = lv(l), Cc = lv(l + 1);
+                qsmg::prolong_add<double, NC>(F, Cc, B);
+                __syncthreads();
+                for (int s = 0; s < A.nu2; ++s) {
+                    qsmg::relax_half<double, NC>(F, 0, B);
+                    __syncthreads();
+                    qsmg::relax_half<double, NC>(F, 1, B);
+                    __syncthreads();
+                }
+            }
+        }
+        cl.sync();
+        mk(78);
+        // up: the distributed levels
+        for (int l = ld - 1; l >= 0; --l) {
+            const qsclu::DLvl D = dl(l);
+            if (l + 1 == ld) {
+                const double *u0 = cl.map_shared_rank(qsclu::arr(cb, Y, ld, 0), 0);
+                const double *u1 = cl.map_shared_rank(qsclu::arr(cb, Y, ld, NC > 1 ? 1 : 0), 0);
+                qsclu::d_prolong_w<NC>(D, u0, u1, Y.n[ld]);
+            } else {
+                qsclu::d_prolong_d<NC>(D, dl(l + 1));
+            }
+            cl.sync();
+            for (int s = 0; s < A.nu2; ++s) {
+                qsclu::d_relax<NC>(D, 0);
+                cl.sync();
+                qsclu::d_relax<NC>(D, 1);
+                cl.sync();
+            }
+            mk(81 + l);
+        }
+        ++it;
+    }
+    {  // this block's rows of the solution
+        const qsclu::DLvl D = dl(0);
+        const size_t g0 = (size_t)D.row0 * D.n;
+        for (int q = threadIdx.x; q < D.R * D.n; q += blockDim.x)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) V.u[c][g0 + q] = D.u[c][q];
+    }
+    if (bid == 0 && threadIdx.x == 0) {
+        DevScalars *sc = A.sc;
+        sc->vcycles[V.kind] += it;
+        if (s_rel > sc->max_relres) sc->max_relres = s_rel;
+        if (!conv) sc->not_converged = 1;
+    }
+    cl.sync();  // no block leaves while another may still read its shared memory
+}
+
 // Iterate until, for every component,
 //   ||f - A u|| <= max(tol ||f||, 1e-13 ||u|| / h^2, atol)
 // (the second bound is a small multiple of the rounding level of the
@@ -427,10 +707,19 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
         const int nn = A.N * A.N;
         for (int c = 0; c < V.nc; ++c)
             if (zero_mask & (1 << c))
-                for (int k = T.t0; k < nn; k += T.nt) V.u[c][k] = 0.0;
+                for (int k = T.t0; k < nn; k += T.nt) {
+                    V.u[c][k] = 0.0;
+                    if (V.u32[c]) V.u32[c][k] = 0.f;
+                }
         SYNC(20);
     }
     if (zero_mask == (1 << V.nc) - 1) return true;
+    if (!REF && A.cl_size > 1) {  // small grid: the first cluster solves alone
+        if (V.nc == 1) mg_solve_cluster<1>(A, V, bid, smem_base, ci, s_fn);
+        else mg_solve_cluster<2>(A, V, bid, smem_base, ci, s_fn);
+        SYNC(22);
+        return true;
+    }
     __shared__ Hier<double> H64;
     __shared__ Hier<float> H32;
     __syncthreads();
@@ -445,6 +734,7 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
     // the other buffer of a pair: the current one is still read as halo by
     // other blocks while it is written.
     int rbuf = 0;
+    bool u32_fresh = false;  // the last cycle wrote the float32 copy of u
     for (;;) {
         if (REF || it > 0) {
             if (!norms_ready) {
@@ -482,6 +772,7 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
             const qstile::Fused fz{{V.u[0], V.u[V.nc - 1]},
                                    {A.r64[0], A.r64[V.nc - 1]},
                                    {A.r32[1 - rbuf][0], A.r32[1 - rbuf][V.nc - 1]},
+                                   {V.u32[0], V.u32[V.nc - 1]},
                                    V.screened ? A.kap : nullptr,
                                    A.lev_inv_h2[0]};
             double *nout = sc->rnorm[slot & 3], *nclr = sc->rnorm[(slot + 2) & 3];
@@ -500,6 +791,7 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
                            : vcycle<double, 2>(A, S, H64, bid, nblk, smem, ci, nullptr, nullptr);
         }
         if (!ok) return false;
+        u32_fresh = REF && norms_ready;
         if (REF && norms_ready) {  // all blocks are past the cycle's last barrier
             rbuf ^= 1;
             if (threadIdx.x == 0)
@@ -512,6 +804,12 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
         sc->vcycles[V.kind] += it;
         if (rel > sc->max_relres) sc->max_relres = rel;
         if (!conv) sc->not_converged = 1;
+    }
+    if (V.u32[0] && !u32_fresh) {  // no cycle, or a cycle without the fused update
+        const int nn = A.N * A.N;
+        for (int c = 0; c < V.nc; ++c)
+            for (int k = T.t0; k < nn; k += T.nt) V.u32[c][k] = (float)V.u[c][k];
+        SYNC(23);
     }
     return true;
 }

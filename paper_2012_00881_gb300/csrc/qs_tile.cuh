@@ -53,18 +53,21 @@ template <int NC>
 __device__ void staged_sweeps(const Region &g, int n, float h2, float *const su0,
                               float *const su1, const float *const sf0, const float *const sf1,
                               const float *const sd, int ns, float omega) {
-    // cells are visited through the in-domain part of the region only
-    const int wx = g.bx - g.ax + 1, wy = g.by - g.ay + 1;
+    // Half sweep s updates, within the in-domain part of the region, the
+    // cells of its colour at least s + 1 cells from every cut side: a
+    // rectangle shrinking by one cell per half sweep on the cut sides.  Only
+    // those cells are visited (the colour's cells of each row, two apart).
     const int RX = g.RX;
-    const int lo_x = g.cl ? g.ax : -(1 << 20), hi_x = g.cr ? g.bx : (1 << 20);
-    const int lo_y = g.cb ? g.ay : -(1 << 20), hi_y = g.ct ? g.by : (1 << 20);
     for (int s = 0; s < ns; ++s) {
         const int color = s & 1;
-        for (Walk w(threadIdx.x, blockDim.x, wx); w.q < wx * wy; w.next()) {
-            const int x = g.ax + w.col, y = g.ay + w.row;
-            if (((x + y) & 1) != color) continue;
-            const int d = min(min(x - lo_x, hi_x - x), min(y - lo_y, hi_y - y));
-            if (d < s + 1) continue;
+        const int X0 = g.cl ? g.ax + s + 1 : g.ax, X1 = g.cr ? g.bx - s - 1 : g.bx;
+        const int Y0 = g.cb ? g.ay + s + 1 : g.ay, Y1 = g.ct ? g.by - s - 1 : g.by;
+        const int rows = Y1 - Y0 + 1, hw = (X1 - X0 + 2) >> 1;
+        const int cnt = (rows > 0 && X1 >= X0) ? rows * hw : 0;
+        for (Walk w(threadIdx.x, blockDim.x, hw > 0 ? hw : 1); w.q < cnt; w.next()) {
+            const int y = Y0 + w.row;
+            const int x = X0 + ((X0 + y + color) & 1) + 2 * w.col;
+            if (x > X1) continue;
             const int li = (y - g.oy) * RX + (x - g.ox);
             const float di = sd ? sd[li] : qsmg::const_inv_diag<float>(qsmg::walls(x, y, n));
 #pragma unroll
@@ -300,6 +303,7 @@ struct Fused {
     double *u64[2];
     double *r64[2];
     float *r32[2];
+    float *u32[2];      // float32 copy of u64 (nullptr: none)
     const double *kap;  // float64 kappa (screened) or nullptr
     double inv_h2;
 };
@@ -389,13 +393,14 @@ __device__ void stage_cascade(const Lvl<float> F, const Region &g, const Cascade
 template <int NC>
 __device__ void up_cascade_fused(const qsmg::Hier<float> &Hh, int lg, const float *cs0,
                                  const float *cs1, int nu2, int TX, int TY, float *sm, int bid,
-                                 int nblk, const Fused &o, double norms[4],
+                                 int nblk, const Fused &o, float norms[4],
                                  qsmg::Marks mark = qsmg::Marks{nullptr, nullptr, 0}) {
     const int n = Hh.lv[0].n;
     const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
     double *const u64_0 = o.u64[0], *const u64_1 = o.u64[NC - 1];
     double *const r64_0 = o.r64[0], *const r64_1 = o.r64[NC - 1];
     float *const r32_0 = o.r32[0], *const r32_1 = o.r32[NC - 1];
+    float *const u32_0 = o.u32[0], *const u32_1 = o.u32[NC - 1];
     const double *const kap = o.kap;
     const double inv_h2 = o.inv_h2;
     for (int tile = bid; tile < ntx * nty; tile += nblk) {
@@ -483,13 +488,14 @@ __device__ void up_cascade_fused(const qsmg::Hier<float> &Hh, int lg, const floa
                 (c ? u64_1 : u64_0)[gi] = u;
                 (c ? r64_1 : r64_0)[gi] = r;
                 (c ? r32_1 : r32_0)[gi] = rf;
+                if (u32_0) (c ? u32_1 : u32_0)[gi] = uf;
                 // the convergence test needs the norms to a few digits only
                 nrm32[c] = __fmaf_rn(rf, rf, nrm32[c]);
                 nrm32[2 + c] = __fmaf_rn(uf, uf, nrm32[2 + c]);
             }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) norms[k] += (double)nrm32[k];
+        for (int k = 0; k < 4; ++k) norms[k] += nrm32[k];
         __syncthreads();
     }
 }

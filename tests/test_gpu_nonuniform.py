@@ -6,8 +6,9 @@ compared element by element; the multigrid solution against the oracle's
 sparse-LU solution of the same discrete system.  Solves here run to a
 relative residual of 1e-13 (1e-12 from 127^2 up, where the float64 residual
 of these grids levels off at 1e-13 .. 6e-13), so two exact solvers of the
-system agree to about cond(A) times that (cond ~ (L / h_min)^2 ~ 1e5 here):
-the bound is 1e-8 relative in L2.
+system agree to about cond(A) times that (cond ~ (L / h_min)^2 ~ 1e5 here);
+the agreement observed is 1e-13 .. 1e-15, and the bound is the float64 bar
+of the slice advance, 1e-9 relative in L2.
 """
 import numpy as np
 import pytest
@@ -18,7 +19,7 @@ from workloads.nonuniform import (alternating_axis, bubble_sources, nonuniform_w
 
 pytestmark = pytest.mark.gpu
 
-PARITY = 1e-8
+PARITY = 1e-9
 
 
 def _solve_tol(n):

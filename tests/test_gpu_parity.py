@@ -165,3 +165,63 @@ def test_errors_are_statuses(qs):
     ctx3 = qs.Context(qs.config_from_workload(wl.with_(n_xi=8, xi_len=2.0)))
     ctx3.init_plasma(4)
     assert ctx3.step3d([])["status"] == 0
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_cluster_solves_match_the_oracle_and_the_grid_solves(qs, n):
+    """Float64 solves by one thread-block cluster (cluster_size 8 and 16: the
+    grid's rows split over the cluster's shared memory) against the oracle
+    and against the grid-wide solves (cluster_size 1), on the linear wake."""
+    wl = W.workload("linear64").with_(n=n, n_xi=32, xi_len=3.0)
+    beams_np = [W.sample_beam(b.with_(xi_c=1.5)) for b in wl.beams]
+    cfg = O.config_from_workload(wl)
+    pl, n_ion = O.plasma_from_workload(wl)
+    ref = O.step3d(cfg, pl, n_ion, beams_np).history
+    scale = np.linalg.norm(ref[0])
+    out = {}
+    for cs in (1, 8, 16):
+        if cs > 1 and n % (2 * cs):
+            continue
+        ctx = qs.Context(qs.config_from_workload(wl, mg_tol=1e-12, cluster_size=cs))
+        ctx.init_plasma(wl.ppc)
+        st = ctx.step3d([qs.Beam(b) for b in beams_np])
+        out[cs] = ctx.fields(qs.FIELD_ALL, device=False).numpy(), st
+        ctx.close()
+        got = out[cs][0]
+        for i in range(5):
+            err = np.linalg.norm(got[i] - ref[i]) / max(np.linalg.norm(ref[i]), scale)
+            assert err < 1e-9, (cs, i, err)
+    for cs in out:
+        assert np.linalg.norm(out[cs][0] - out[1][0]) <= 1e-10 * np.linalg.norm(out[1][0])
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32r"])
+def test_plasma_sorted_by_cell_inside_the_loop(qs, form):
+    """sort_every = 1 reorders the plasma by (cell, id) before every base
+    slice (the last slice has no push, so the final order is that of the
+    final positions): bit-exact against the oracle's counting sort; the wake
+    and the particles (matched by id) equal those of the unsorted loop."""
+    wl = W.workload("linear64").with_(n_xi=24, xi_len=3.0)
+    beams_np = [W.sample_beam(b.with_(xi_c=1.5, amplitude=2.0)) for b in wl.beams]
+    out = {}
+    for K in (0, 1, 5):
+        ctx = qs.Context(qs.config_from_workload(wl, precision=form, mg_tol=1e-12,
+                                                 sort_every=K))
+        ctx.init_plasma(wl.ppc)
+        st = ctx.step3d([qs.Beam(b) for b in beams_np])
+        out[K] = (ctx.fields(qs.FIELD_ALL, device=False).numpy(), ctx.plasma(), st)
+        ctx.close()
+    assert out[0][2]["sorts"] == 0
+    assert out[1][2]["sorts"] == wl.n_xi - 1 and out[5][2]["sorts"] == (wl.n_xi - 1) // 5
+    p = out[1][1]
+    cell, count, offset, perm = O.cell_sort(p["x"], p["y"], p["id"], O.Grid.square(wl.n, wl.half_width))
+    assert np.array_equal(perm, np.arange(len(perm)))  # already in (cell, id) order
+    tol = 1e-11 if form == "fp64" else 2e-6
+    base = out[0][0]
+    for K in (1, 5):
+        assert np.linalg.norm(out[K][0] - base) <= tol * np.linalg.norm(base)
+        a, b = out[0][1], out[K][1]
+        ia, ib = np.argsort(a["id"]), np.argsort(b["id"])
+        assert np.array_equal(a["id"][ia], b["id"][ib])
+        for k in ("x", "y", "px", "py", "w"):
+            assert np.max(np.abs(a[k][ia] - b[k][ib])) <= (1e-9 if form == "fp64" else 1e-4), k

@@ -147,3 +147,16 @@ NONUNIFORM_WORKLOADS = {
 
 def nonuniform_workload(name: str) -> NonuniformWorkload:
     return NONUNIFORM_WORKLOADS[name]
+
+
+def driver_current_nodes(xn: np.ndarray, yn: np.ndarray, n_xi: int, xi_len: float,
+                         amplitude: float, sigma_r: float, sigma_z: float,
+                         xi_c: float) -> np.ndarray:
+    """j_z of a bi-Gaussian electron driver, amplitude exp(-r^2/sigma_r^2 -
+    (xi - xi_c)^2/sigma_z^2) (Sec. 5.1's convention, v_z = 1), at the interior
+    nodes of the base slices xi_j = j xi_len / n_xi: float64 [n_xi, ny, nx]."""
+    X, Y = np.meshgrid(np.asarray(xn)[1:-1], np.asarray(yn)[1:-1])
+    xi = np.arange(n_xi) * xi_len / n_xi
+    prof = np.exp(-((xi - xi_c) / sigma_z) ** 2)
+    return np.ascontiguousarray(amplitude * prof[:, None, None] *
+                                np.exp(-(X * X + Y * Y) / sigma_r ** 2)[None])
