@@ -16,8 +16,10 @@ a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import atexit
 import json
 import os
+import signal
 import statistics
 import subprocess
 import sys
@@ -257,11 +259,27 @@ def algorithmic_bytes(stats, wl, form: str, n_xi: int) -> float:
 
 
 # ---------------------------------------------------------------- clocks
+def _die_with_parent():
+    """Child side of Popen: receive SIGTERM when the parent process dies, so
+    that a sampler never outlives a bench run that ended by an exception or a
+    signal (a profiler waits for every process of the tree)."""
+    try:
+        import ctypes
+        ctypes.CDLL(None, use_errno=True).prctl(1, int(signal.SIGTERM))  # PR_SET_PDEATHSIG
+    except (OSError, AttributeError):
+        pass
+
+
 class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.path = None
+        atexit.register(self._kill)
+
+    def _kill(self):
+        if self.proc and self.proc.poll() is None:
+            self.proc.kill()
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -273,7 +291,8 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL,
+                preexec_fn=_die_with_parent)
         except (OSError, FileNotFoundError):
             self.proc = None
 

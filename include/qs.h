@@ -116,13 +116,26 @@ typedef struct {
                                 /* loop, in SM clock cycles; a wait that runs   */
                                 /* out records QS_ERR_TIMEOUT and the kernel    */
                                 /* returns; 0 = default 4e9 (about 2 s)         */
-    int cluster_size;           /* QS_FP64: the multigrid solves of small grids */
-                                /* run in one thread-block cluster of this many */
-                                /* blocks (8 or 16; N must divide by 2 * size), */
-                                /* the rest of the slice loop on every block;   */
-                                /* 0 = automatic (N <= 64: 16 when N divides by */
-                                /* 32, else 8 when N divides by 16),            */
-                                /* 1 = off                                      */
+    int cluster_size;           /* multigrid cycles in thread-block clusters of */
+                                /* this many blocks (8 or 16; N must divide by  */
+                                /* 2 * size), one cluster per component, the    */
+                                /* rest of the slice loop on every block:       */
+                                /* QS_FP64 solves of grids N <= 128, the float32 */
+                                /* inner cycles of QS_FP32_REFINED up to 256;   */
+                                /* 0 = automatic (float64: 16 for N <= 64      */
+                                /* dividing by 32, 8 dividing by 16; refined:   */
+                                /* off, its grid-wide cycles being faster), 1 = */
+                                /* off                                           */
+    int deposit_band_rows;      /* privatised deposits of the moments and n_*:  */
+                                /* each block adds its contiguous chunk of the  */
+                                /* (cell-sorted) plasma into a band of at most  */
+                                /* this many grid rows in shared memory, then   */
+                                /* the band to the grid once per cell; stencils */
+                                /* outside the band go to the grid directly;    */
+                                /* 0 = off (every stencil to the grid: faster  */
+                                /* on the cases measured), -1 = as many rows   */
+                                /* as shared memory holds (>= 8 where 200 KB   */
+                                /* allow), else >= 3 rows at most              */
 } qs_config;
 
 /* Driver-beam macroparticles: structure of arrays of float64, n entries each.

@@ -52,6 +52,7 @@ class QsConfig(ctypes.Structure):
         ("checkpoint_every", ctypes.c_int),
         ("barrier_wait_cycles", ctypes.c_int64),
         ("cluster_size", ctypes.c_int),
+        ("deposit_band_rows", ctypes.c_int),
     ]
 
 

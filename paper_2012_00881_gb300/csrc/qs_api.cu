@@ -80,6 +80,7 @@ struct qs_ctx {
     size_t engine_smem = 0;
     int cl_size = 1;          // thread-block cluster of the float64 small-grid solves
     size_t cl_offset = 0;     // its arrays in the engine's dynamic shared memory
+    int band_rows = 0, band_rows_n = 0;  // privatised deposit bands (rows)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     char msg[512] = {0};
 };
@@ -204,13 +205,18 @@ int validate(const qs_config *cfg, char *why, size_t nwhy) {
         snprintf(why, nwhy, "barrier_wait_cycles must be >= 0");
         return QS_ERR_ARG;
     }
+    if (cfg->deposit_band_rows < -1 || (cfg->deposit_band_rows > 0 && cfg->deposit_band_rows < 3)) {
+        snprintf(why, nwhy, "deposit_band_rows must be -1, 0 or >= 3");
+        return QS_ERR_ARG;
+    }
     const int cs = cfg->cluster_size;
     if (cs != 0 && cs != 1 && cs != 8 && cs != 16) {
         snprintf(why, nwhy, "cluster_size must be 0, 1, 8 or 16");
         return QS_ERR_ARG;
     }
-    if (cs > 1 && (cfg->precision != QS_FP64 || cfg->nx % (2 * cs) != 0 || cfg->nx > 128)) {
-        snprintf(why, nwhy, "cluster_size %d needs QS_FP64 and N <= 128 divisible by %d", cs,
+    const int cl_max_n = cfg->precision == QS_FP64 ? 128 : 256;
+    if (cs > 1 && (cfg->nx % (2 * cs) != 0 || cfg->nx > cl_max_n)) {
+        snprintf(why, nwhy, "cluster_size %d needs N <= %d divisible by %d", cs, cl_max_n,
                  2 * cs);
         return QS_ERR_ARG;
     }
@@ -299,12 +305,35 @@ int create_impl(qs_ctx *c) {
                                           c->tile_x, c->tile_y, nu, g.post_sweeps,
                                           &c->block_offset, &c->tile_offset);
     int cs = g.cluster_size;
-    if (cs == 0)  // 16 blocks where the grid splits into strips of >= 2 rows
-        cs = (!ref && c->N <= 64 && c->N % 32 == 0) ? 16
-                                                     : (!ref && c->N <= 64 && c->N % 16 == 0) ? 8 : 1;
+    if (cs == 0) {
+        if (!ref)  // float64: small grids, 16 blocks where the strips keep >= 2 rows
+            cs = (c->N <= 64 && c->N % 32 == 0) ? 16 : (c->N <= 64 && c->N % 16 == 0) ? 8 : 1;
+        else  // refined: the grid-wide cycles were faster at every size measured
+            cs = 1;
+    }
     if (cs > 1) {
-        c->cl_offset = (c->engine_smem + 255) & ~(size_t)255;
-        c->engine_smem = c->cl_offset + qs_cluster_smem_bytes(c->lev_n, c->nlev, cs);
+        // the cluster arrays follow the coarsest inverses; they overlap the
+        // shared-memory coarse part and tiles of the grid-wide cycle, which
+        // a clustered launch does not use (the adjoint's launch does)
+        c->cl_offset = c->block_offset;
+        const size_t need =
+            c->cl_offset + qs_cluster_smem_bytes(c->lev_n, c->nlev, cs, ref ? 4 : 8) + 256;
+        if (need > c->engine_smem) c->engine_smem = need;
+    }
+    if (g.deposit_band_rows != 0) {
+        // privatised deposits: the bands reuse the shared memory of the
+        // cycles after the coarsest inverses (free between solves); room for
+        // at least 8 rows of the six moments where 200 KB allow it
+        const size_t row_m = (size_t)6 * c->N * (ref ? 4 : 8), row_n = (size_t)8 * c->N;
+        const size_t want = c->block_offset + 8 * row_m + 256;
+        const size_t cap = 200 * 1024;
+        if (want > c->engine_smem) c->engine_smem = want < cap ? want : cap;
+        const size_t avail = c->engine_smem - 256 - c->block_offset;
+        const size_t rm = avail / row_m, rn = avail / row_n;
+        const size_t lim = g.deposit_band_rows > 0 ? (size_t)g.deposit_band_rows : (size_t)c->N;
+        const size_t cap_m = rm < lim ? rm : lim, cap_n = rn < lim ? rn : lim;
+        c->band_rows = g.deposit_band_rows != 0 && cap_m >= 3 ? (int)cap_m : 0;
+        c->band_rows_n = g.deposit_band_rows != 0 && cap_n >= 3 ? (int)cap_n : 0;
     }
     if (c->engine_smem > 220 * 1024)
         return fail(c, QS_ERR_ARG,
@@ -631,6 +660,9 @@ static int step_prepare(qs_ctx *c, const qs_beam *beams, int n_beams, const int3
     a.block_level_n = c->block_level_n;
     a.cl_size = c->cl_size;
     a.cl_smem_offset = (int)c->cl_offset;
+    a.band_rows = c->band_rows;
+    a.band_rows_n = c->band_rows_n;
+    a.band_off = (int)c->block_offset;
     a.id = c->id;
     if (g.sort_every > 0 && c->x2) {
         a.sort_every = g.sort_every;
@@ -701,7 +733,11 @@ static int step_finish(qs_ctx *c, qs_step_stats *stats, double gpu_ms) {
     int status = QS_OK;
     if (hs.err != 0) {
         status = hs.err;
-        fail(c, status, "device wait timed out at phase %d", hs.err_where);
+        if (hs.err == QS_ERR_CUDA && hs.err_where == -1)
+            fail(c, status, "the slice engine ran without its %d-block thread-block clusters",
+                 c->cl_size);
+        else
+            fail(c, status, "device wait timed out at phase %d", hs.err_where);
     } else if (hs.not_converged) {
         status = fail(c, QS_ERR_NOT_CONVERGED, "a multigrid solve reached %d V-cycles (relres %g)",
                       g.mg_max_vcycles, hs.max_relres);

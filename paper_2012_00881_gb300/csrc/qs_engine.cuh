@@ -87,6 +87,96 @@ __device__ __forceinline__ double rcp_newton(double a) {
     return r;
 }
 
+// ---------------------------------------------------------------------------
+// Privatised deposits.  With the plasma sorted by cell, a block that takes a
+// contiguous chunk of the particle array finds its CIC stencils in a narrow
+// band of grid rows (a 262,144-particle chunk of 1/152 covers about two rows
+// of a 256^2 grid).  The block accumulates the band in shared memory and
+// adds it to the grid once per cell: one global atomic per cell and moment
+// instead of four per particle and moment.  A stencil outside the band (a
+// particle that moved far since the last sort) is added to the grid directly.
+// ---------------------------------------------------------------------------
+
+// the block's contiguous chunk [p0, p1) of np particles
+__device__ __forceinline__ void chunk_of(int64_t np, int bid, int nblk, int64_t &p0,
+                                         int64_t &p1) {
+    const int64_t cs = (np + nblk - 1) / nblk;
+    p0 = min(np, (int64_t)bid * cs);
+    p1 = min(np, p0 + cs);
+}
+
+// Rows [r0, r0 + rows) holding the CIC stencils (rows of y - h/2 and the
+// next) of the chunk's particles, widened by `margin` rows on each side and
+// clipped to the grid and to max_rows; rows = 0 for an empty chunk.
+struct Band {
+    int r0, rows;
+};
+
+__device__ Band band_of(const EngineArgs &A, const double *y, int64_t p0, int64_t p1, int margin,
+                        int max_rows) {
+    __shared__ int s_lo, s_hi;
+    if (threadIdx.x == 0) {
+        s_lo = A.N;
+        s_hi = -1;
+    }
+    __syncthreads();
+    int lo = A.N, hi = -1;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const int a = (int)floor((y[p] - A.y_min) * A.inv_h - 0.5);
+        lo = min(lo, a);
+        hi = max(hi, a + 1);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&s_lo, lo);
+        atomicMax(&s_hi, hi);
+    }
+    __syncthreads();
+    Band b{0, 0};
+    if (s_hi >= 0) {
+        const int r0 = max(0, s_lo - margin);
+        const int r1 = min(A.N - 1, s_hi + margin);
+        b.r0 = r0;
+        b.rows = min(r1 - r0 + 1, max_rows);
+    }
+    __syncthreads();  // s_lo, s_hi are rewritten by the next call
+    return b;
+}
+
+// deposit q into the band s (cells lo .. hi - 1 of the grid) when the whole
+// stencil is inside, else into the grid g
+template <typename P, typename W>
+__device__ __forceinline__ void dep_band(P *g, P *s, int lo, int hi, const W &c, P q) {
+    const int a = min(min(c.i00, c.i01), min(c.i10, c.i11));
+    const int b = max(max(c.i00, c.i01), max(c.i10, c.i11));
+    if (a >= lo && b < hi) {
+        atomicAdd(s + (c.i00 - lo), q * (P)c.w00);
+        atomicAdd(s + (c.i01 - lo), q * (P)c.w01);
+        atomicAdd(s + (c.i10 - lo), q * (P)c.w10);
+        atomicAdd(s + (c.i11 - lo), q * (P)c.w11);
+    } else {
+        atomicAdd(g + c.i00, q * (P)c.w00);
+        atomicAdd(g + c.i01, q * (P)c.w01);
+        atomicAdd(g + c.i10, q * (P)c.w10);
+        atomicAdd(g + c.i11, q * (P)c.w11);
+    }
+}
+
+// the band's nonzero cells added to the grid, one atomic per cell
+template <typename P>
+__device__ __forceinline__ void flush_band(P *g, const P *s, int lo, int cells) {
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+        const P v = s[k];
+        if (v != P(0)) atomicAdd(g + lo + k, v);
+    }
+}
+
+template <typename P>
+__device__ __forceinline__ void zero_band(P *s, int cells) {
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) s[k] = P(0);
+}
+
 // n_* of the initial particles
 template <typename P>
 __device__ void phase_deposit_n(const EngineArgs &A, const PS<P> &Q, double *ng, Thr T) {
@@ -170,10 +260,34 @@ __device__ void phase_psi_rhs(const EngineArgs &A, const PS<P> &Q, const double 
 // gather psi at every particle; deposit j_perp, T, G (Eqs. Jr, FluxPres);
 // gamma from the constant of motion is always evaluated in float64
 template <typename P>
-__device__ void phase_moments(const EngineArgs &A, const PS<P> &Q, Thr T) {
+__device__ void phase_moments(const EngineArgs &A, const PS<P> &Q, Thr T, int bid, int nblk,
+                              void *smem) {
     const P s = (P)(A.inv_h * A.inv_h);
     unsigned hits = 0;
-    for (int64_t p = T.t0; p < A.np; p += T.nt) {
+    // privatised: this block's chunk into the six bands of sb
+    const bool banded = A.band_rows > 0;
+    int64_t p0 = T.t0, p1 = A.np, pst = T.nt;
+    P *sb = nullptr;
+    int lo = 0, hi = 0, cells = 0;
+    if (banded) {
+        int64_t c0, c1;
+        chunk_of(A.np, bid, nblk, c0, c1);
+        const Band b = band_of(A, Q.y, c0, c1, 0, A.band_rows);
+        cells = b.rows * A.N;
+        lo = b.r0 * A.N;
+        hi = lo + cells;
+        sb = (P *)((char *)smem + A.band_off);
+        zero_band(sb, 6 * cells);
+        __syncthreads();
+        p0 = c0 + threadIdx.x;
+        p1 = c1;
+        pst = blockDim.x;
+    }
+    auto put = [&](P *g, int k, const CicP<P> &c, P q) {
+        if (banded) dep_band(g, sb + k * cells, lo, hi, c, q);
+        else dep(g, c, q);
+    };
+    for (int64_t p = p0; p < p1; p += pst) {
         const Cic cd = cic_stencil_inv(Q.x[p], Q.y[p], A.x_min, A.y_min, A.inv_h, A.N);
         const CicP<P> c = cic_p<P>(cd);
         const double a = guard(1.0 + cic_gather(A.psi, cd), A.psi_floor, hits);
@@ -186,19 +300,25 @@ __device__ void phase_moments(const EngineArgs &A, const PS<P> &Q, Thr T) {
         const P wq = Q.w[p] * s;
         // the laser's |A|^2 / 2 in the numerator of gamma (line after Eq. EoM_111)
         const double ha2 = A.a2_base ? 0.5 * cic_gather(A.a2, cd) : 0.0;
-        dep(Q.jx, c, wq * vx);
-        dep(Q.jy, c, wq * vy);
-        dep(Q.txx, c, wq * vx * vx);
-        dep(Q.txy, c, wq * vx * vy);
-        dep(Q.tyy, c, wq * vy * vy);
+        put(Q.jx, 0, c, wq * vx);
+        put(Q.jy, 1, c, wq * vy);
+        put(Q.txx, 2, c, wq * vx * vx);
+        put(Q.txy, 3, c, wq * vx * vy);
+        put(Q.tyy, 4, c, wq * vy * vy);
         if constexpr (sizeof(P) == 8) {
-            dep(Q.G, c, wq * ((1.0 + p2 + a * a + ha2) * (0.5 * ia)));  // gamma
+            put(Q.G, 5, c, wq * ((1.0 + p2 + a * a + ha2) * (0.5 * ia)));  // gamma
         } else {
             const double am1 = a - 1.0;  // gamma - 1 = (p^2 + psi^2) / (2 (1 + psi))
-            dep(Q.G, c, wq * (P)((p2 + am1 * am1 + ha2) * (0.5 * ia)));
+            put(Q.G, 5, c, wq * (P)((p2 + am1 * am1 + ha2) * (0.5 * ia)));
         }
     }
     add_hits(A.sc, hits);
+    if (banded) {
+        __syncthreads();
+        P *const g[6] = {Q.jx, Q.jy, Q.txx, Q.txy, Q.tyy, Q.G};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) flush_band(g[k], sb + k * cells, lo, cells);
+    }
 }
 
 // central differences: zero ghosts (moments) and odd ghosts (fields)
@@ -336,7 +456,8 @@ __device__ void phase_assemble2(const EngineArgs &A, const PS<P> &Q, const doubl
 // deposit n_* of the next slice; V_max.  gamma is evaluated in float64.
 template <typename P>
 __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, bool base,
-                           bool last, int j, double dxi, int pk, int sub, Thr T) {
+                           bool last, int j, double dxi, int pk, int sub, Thr T, int bid,
+                           int nblk, void *smem) {
     const int nn = A.N * A.N;
     if (A.seg_g && sub < A.seg_cap) {  // segment store for the adjoint (float64)
         double *g = A.seg_g + (size_t)sub * SG_COUNT * nn;
@@ -379,7 +500,27 @@ __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, b
     const P half = (P)(0.5 * dxi), dxp = (P)dxi;
     unsigned hits = 0;
     P vm = P(0);  // V_max (refined form: its square, in float32)
-    for (int64_t p = T.t0; p < A.np; p += T.nt) {
+    // privatised n_* of the next slice: the band of the chunk's present rows
+    // widened by two rows for the particles' motion
+    const bool banded = A.band_rows_n > 0;
+    int64_t p0 = T.t0, p1 = A.np, pst = T.nt;
+    double *sb = nullptr;
+    int lo = 0, hi = 0, cells = 0;
+    if (banded) {
+        int64_t c0, c1;
+        chunk_of(A.np, bid, nblk, c0, c1);
+        const Band b = band_of(A, Q.y, c0, c1, 2, A.band_rows_n);
+        cells = b.rows * A.N;
+        lo = b.r0 * A.N;
+        hi = lo + cells;
+        sb = (double *)((char *)smem + A.band_off);
+        zero_band(sb, cells);
+        __syncthreads();
+        p0 = c0 + threadIdx.x;
+        p1 = c1;
+        pst = blockDim.x;
+    }
+    for (int64_t p = p0; p < p1; p += pst) {
         const double x = Q.x[p], y = Q.y[p];
         const Cic cd = cic_stencil_inv(x, y, A.x_min, A.y_min, A.inv_h, A.N);
         const CicP<P> c = cic_p<P>(cd);
@@ -441,9 +582,14 @@ __device__ void phase_push(const EngineArgs &A, const PS<P> &Q, double *nnext, b
             vm = fmaxf(vm, (px * px + py * py) * (iap * iap));
         }
         const Cic c2 = cic_stencil_inv(nx, ny, A.x_min, A.y_min, A.inv_h, A.N);
-        cic_deposit(nnext, c2, Q.wd[p] * s);
+        if (banded) dep_band(nnext, sb, lo, hi, c2, Q.wd[p] * s);
+        else cic_deposit(nnext, c2, Q.wd[p] * s);
     }
     add_hits(A.sc, hits);
+    if (banded) {
+        __syncthreads();
+        flush_band(nnext, sb, lo, cells);
+    }
     double vmax = block_max((double)vm);
     if (sizeof(P) == 4) vmax = sqrt(vmax);
     if (threadIdx.x == 0) {
@@ -644,7 +790,7 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
             phase_psi_rhs<P>(A, Q, ncur, nnext, base, j, q, m, T, g);
             if (!S(2)) return false;
             if (!mg_solve<REF>(A, S, Vpsi, slot, bid, nblk, smem, s_inv_ready)) return false;
-            phase_moments<P>(A, Q, T);
+            phase_moments<P>(A, Q, T, bid, nblk, smem);
             if (!S(3)) return false;
             phase_assemble1<P>(A, Q, ncur, j, q, m, T, g);
             if (!S(4)) return false;
@@ -652,7 +798,7 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
             phase_assemble2<P>(A, Q, ncur, T, g);
             if (!S(5)) return false;
             if (!mg_solve<REF>(A, S, Vbp, slot, bid, nblk, smem, s_inv_ready)) return false;
-            phase_push<P>(A, Q, nnext, base, last, j, dxi, pk, sub, T);
+            phase_push<P>(A, Q, nnext, base, last, j, dxi, pk, sub, T, bid, nblk, smem);
             ++sub;
             if (lead) {
                 sc->slices += 1;
@@ -707,6 +853,15 @@ __global__ void __launch_bounds__(QS_ENGINE_THREADS, 1) slice_engine(const __gri
         s_inv_ready[0] = s_inv_ready[1] = 0;
     }
     __syncthreads();
+    // A launch without the configured thread-block clusters (a profiler's
+    // kernel replay can drop the attribute) would reach distributed shared
+    // memory of blocks that are not there: every block returns at once with
+    // an error instead, before the first grid barrier.
+    if (A.cl_size > 1 && (int)cooperative_groups::this_cluster().num_blocks() != A.cl_size) {
+        if (threadIdx.x == 0 && atomicCAS(&A.sc->err, 0, QS_ERR_CUDA) == 0)
+            A.sc->err_where = -1;
+        return;
+    }
     const Sync S{A.sc, &A.sc->bar_arrive, gridDim.x, A.spin_cycles, A.trace, A.trace_cap,
                  &s_epoch, blockIdx.x == 0, A.cl_size};
     run_step<REF>(A, blockIdx.x, gridDim.x, S, smem, s_inv_ready);

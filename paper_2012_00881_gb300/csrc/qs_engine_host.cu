@@ -50,8 +50,8 @@ int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *bloc
     return 0;
 }
 
-size_t qs_cluster_smem_bytes(const int *lev_n, int nlev, int cluster) {
-    return qsclu::cluster_layout(lev_n, nlev, cluster).total;
+size_t qs_cluster_smem_bytes(const int *lev_n, int nlev, int cluster, int tsize) {
+    return qsclu::cluster_layout(lev_n, nlev, cluster, tsize).total;
 }
 
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,

@@ -17,7 +17,7 @@
 struct DevScalars {
     unsigned long long bar_arrive; // grid barrier: total arrivals (monotonic)
     int err;                       // first error status seen on the device
-    int err_where;                 // phase id of a timeout
+    int err_where;                 // phase id of a timeout; -1: no clusters
     double rnorm[4][4];            // ||r||^2 (comps 0,1) and ||u||^2 (2,3), ring of 4
     double fnorm[3][2];            // ||f||^2 of the psi / (Ez,Bz) / (Bx,By) solves
     unsigned long long vmax_bits[2];  // V_max of a push (bits of a double >= 0)
@@ -28,6 +28,7 @@ struct DevScalars {
     long long sorts;  // cell sorts of the plasma inside the slice loop
     int max_m;
     int not_converged;
+    int cl_cycles;  // V-cycles of the last cluster solve (the largest over its clusters)
     double max_relres;
     unsigned long long vmax_all_bits;
     unsigned long long trace_n;
@@ -100,11 +101,17 @@ struct EngineArgs {
     float lev_h2f[QS_MAX_LEV], lev_inv_h2f[QS_MAX_LEV];
     LevelArrays lev[QS_MAX_LEV];
     int block_level_n;  // levels with side <= this are relaxed by one block
-    // float64 solves of small grids by the launch's first thread-block
-    // cluster (qs_cluster.cuh): cluster size of the launch (<= 1: off) and
-    // the byte offset of the cluster's arrays in dynamic shared memory
+    // multigrid cycles in thread-block clusters (qs_cluster.cuh; the float64
+    // solves of small grids, the refined form's float32 inner cycles):
+    // cluster size of the launch (<= 1: off) and the byte offset of the
+    // cluster's arrays in dynamic shared memory
     int cl_size;
     int cl_smem_offset;
+    // privatised deposits: each block deposits a contiguous chunk of the
+    // particle array into a band of grid rows held in shared memory at byte
+    // offset band_off, at most band_rows rows for the six moments and
+    // band_rows_n for n_* (0: plain global atomics, particles grid-strided)
+    int band_rows, band_rows_n, band_off;
     // refined form: float32 inner hierarchy (level 0: correction e, residual r)
     int precision;
     int tile_x, tile_y;  // output tile of the staged grid levels (refined form)
@@ -342,7 +349,7 @@ cudaError_t qs_launch_adjoint(cudaStream_t st, const EngineArgs &a, const AdjArg
 int qs_adjoint_max_blocks(int device, int precision, size_t smem_bytes, int *blocks);
 int qs_engine_max_blocks(int device, int precision, size_t smem_bytes, int *blocks,
                          int cluster = 1);
-size_t qs_cluster_smem_bytes(const int *lev_n, int nlev, int cluster);
+size_t qs_cluster_smem_bytes(const int *lev_n, int nlev, int cluster, int tsize);
 size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int precision,
                             int tile_x, int tile_y, int nu, int nu2, size_t *block_offset,
                             size_t *tile_offset);

@@ -53,8 +53,8 @@ struct Sync {
     int trace_cap;
     unsigned long long *epoch;  // this block's barrier count (shared memory)
     bool tracer;                // this block records the phase trace
-    int cl = 1;                 // cluster size of the launch (> 1: the first
-                                // cluster solves alone, see mg_solve_cluster)
+    int cl = 1;                 // cluster size of the launch (> 1: clusters run
+                                // the multigrid cycles, see qs_cluster.cuh)
     __device__ bool operator()(int where) const {
         __shared__ int s_ok;
         __syncthreads();
@@ -92,10 +92,10 @@ struct Sync {
             }
         }
         __syncthreads();
-        if (cl > 1 && (int)blockIdx.x < cl) {
-            // The first cluster's blocks take one decision: after a timed-out
+        if (cl > 1) {
+            // The blocks of a cluster take one decision: after a timed-out
             // wait some blocks may see the barrier complete and others the
-            // error word, and a block that went on into the cluster solve
+            // error word, and a block that went on into a cluster solve
             // would wait at a cluster barrier for one that has left.
             namespace cg = cooperative_groups;
             cg::cluster_group clu = cg::this_cluster();
@@ -116,8 +116,18 @@ struct Sync {
 };
 
 using qsmg::Thr;
+// The first index of this thread in the grid-wide loops
+// `for (i = t0; i < count; i += nt)`.  Runs of 32 consecutive indices go to
+// the blocks in turn (run w * nblk + b to warp w of block b), so that a loop
+// shorter than the launch (a coarse level, a 64^2 grid, the cells of a small
+// grid) still spreads over every SM, while each warp's accesses stay
+// contiguous.  float64 work is throughput-bound on GB300 (about two FMA per
+// clock per SM): the same loop on the first few blocks alone took several
+// times longer.  t0 ranges over a permutation of [0, nt) (blockDim.x is a
+// multiple of 32), so every index is visited exactly once.
 __device__ __forceinline__ Thr grid_thr(int bid, int nblk) {
-    return Thr{bid * (int)blockDim.x + (int)threadIdx.x, nblk * (int)blockDim.x};
+    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    return Thr{((w * nblk + bid) << 5) + lane, nblk * (int)blockDim.x};
 }
 
 // sum over the block; valid in thread 0
@@ -434,235 +444,387 @@ __device__ void residual_norm(const EngineArgs &A, const SolveSpec &V, double *o
     }
 }
 
-// Float64 solve by the launch's first cluster (see qs_cluster.cuh); the
-// other blocks return at once.  fn: ||f||^2 per component (thread 0).
-// Returns the V-cycles done; the caller's grid barrier follows.
-template <int NC>
-__device__ void mg_solve_cluster(const EngineArgs &A, const SolveSpec &V, int bid,
-                                 void *smem_base, qsmg::CoarseInv ci, const double *fn) {
+// ---------------------------------------------------------------------------
+// V-cycles inside thread-block clusters (qs_cluster.cuh): one cluster per
+// component, cluster k = blocks [k C, (k + 1) C) of the launch.
+// ---------------------------------------------------------------------------
+
+// The cluster's view of its hierarchy: distributed level l (l < Y.ld) and
+// the local levels of block 0.
+template <typename T>
+struct ClusterView {
+    void *cb;  // the cluster region of this block's shared memory
+    const qsclu::Layout *Y;
+    int rank, C;
+    bool scr;
+    __device__ qsclu::DLvl<T> dl(const EngineArgs &A, cooperative_groups::cluster_group &cl,
+                                 int l) const {
+        qsclu::DLvl<T> D;
+        D.n = Y->n[l];
+        D.R = Y->R[l];
+        D.row0 = rank * D.R;
+        D.u = qsclu::arr<T>(cb, *Y, l, 0);
+        D.f = qsclu::arr<T>(cb, *Y, l, 1);
+        D.k = scr ? qsclu::arr<T>(cb, *Y, l, 2) : nullptr;
+        D.d = scr ? qsclu::arr<T>(cb, *Y, l, 3) : nullptr;
+        D.up_u = rank > 0 ? cl.map_shared_rank(D.u, rank - 1) : nullptr;
+        D.dn_u = rank < C - 1 ? cl.map_shared_rank(D.u, rank + 1) : nullptr;
+        D.h2 = (T)A.lev_h2[l];
+        D.inv_h2 = (T)A.lev_inv_h2[l];
+        D.omega = (T)A.omega;
+        return D;
+    }
+    __device__ Lvl<T> lv(const EngineArgs &A, int l) const {
+        Lvl<T> v;
+        v.u[0] = v.u[1] = qsclu::arr<T>(cb, *Y, l, 0);
+        v.f[0] = v.f[1] = qsclu::arr<T>(cb, *Y, l, 1);
+        v.k = scr ? qsclu::arr<T>(cb, *Y, l, 2) : nullptr;
+        v.d = scr ? qsclu::arr<T>(cb, *Y, l, 3) : nullptr;
+        v.n = Y->n[l];
+        v.h2 = A.lev_h2[l];
+        v.inv_h2 = A.lev_inv_h2[l];
+        v.h2t = (T)A.lev_h2[l];
+        v.inv_h2t = (T)A.lev_inv_h2[l];
+        v.omega = (T)A.omega;
+        return v;
+    }
+};
+
+// One V(nu1, nu2) cycle of the cluster's component on the hierarchy held in
+// its shared memory (level 0's u and f already there).  with_k: restrict
+// kappa too (the first cycle of a solve).
+template <typename T>
+__device__ void cluster_vcycle(const EngineArgs &A, cooperative_groups::cluster_group &cl,
+                               const ClusterView<T> &V, qsmg::CoarseInv ci, bool with_k,
+                               const qsmg::Marks &mk) {
+    const qsclu::Layout &Y = *V.Y;
+    const int ld = Y.ld, L = Y.L;
+    for (int l = 0; l < ld; ++l) {
+        const qsclu::DLvl<T> D = V.dl(A, cl, l);
+        const int nu = D.n > A.block_level_n ? A.nu1 : A.nu1c;
+        for (int s = 0; s < nu; ++s) {
+            qsclu::d_relax<T>(D, 0);
+            cl.sync();
+            qsclu::d_relax<T>(D, 1);
+            cl.sync();
+        }
+        const int m = Y.n[l + 1];
+        T *cu, *cf, *ck = nullptr, *cd = nullptr;
+        int crow0;
+        if (l + 1 < ld) {  // into this block's strip of the next level
+            cu = qsclu::arr<T>(V.cb, Y, l + 1, 0);
+            cf = qsclu::arr<T>(V.cb, Y, l + 1, 1);
+            if (V.scr) {
+                ck = qsclu::arr<T>(V.cb, Y, l + 1, 2);
+                cd = qsclu::arr<T>(V.cb, Y, l + 1, 3);
+            }
+            crow0 = D.row0 >> 1;
+        } else {  // into block 0's whole first local level
+            cu = cl.map_shared_rank(qsclu::arr<T>(V.cb, Y, ld, 0), 0);
+            cf = cl.map_shared_rank(qsclu::arr<T>(V.cb, Y, ld, 1), 0);
+            if (V.scr) {
+                ck = cl.map_shared_rank(qsclu::arr<T>(V.cb, Y, ld, 2), 0);
+                cd = cl.map_shared_rank(qsclu::arr<T>(V.cb, Y, ld, 3), 0);
+            }
+            crow0 = 0;
+        }
+        qsclu::d_restrict<T>(D, m, crow0, cu, cf, ck, cd, (T)A.lev_h2[l + 1], with_k);
+        cl.sync();
+        mk(71 + l);
+    }
+    if (V.rank == 0) {  // the local levels, all of block 0's warps
+        const Thr B{(int)threadIdx.x, (int)blockDim.x};
+        for (int l = ld; l < L - 1; ++l) {
+            const Lvl<T> F = V.lv(A, l), Cc = V.lv(A, l + 1);
+            const int nu = F.n > A.block_level_n ? A.nu1 : A.nu1c;
+            for (int s = 0; s < nu; ++s) {
+                qsmg::relax_half<T, 1>(F, 0, B);
+                __syncthreads();
+                qsmg::relax_half<T, 1>(F, 1, B);
+                __syncthreads();
+            }
+            qsmg::restrict_res<T, 1>(F, Cc, B, with_k);
+            __syncthreads();
+        }
+        qsmg::coarse_solve<T, 1>(V.lv(A, L - 1), (double *)((char *)V.cb + Y.work), ci);
+        for (int l = L - 2; l >= ld; --l) {
+            const Lvl<T> F = V.lv(A, l), Cc = V.lv(A, l + 1);
+            qsmg::prolong_add<T, 1>(F, Cc, B);
+            __syncthreads();
+            for (int s = 0; s < A.nu2; ++s) {
+                qsmg::relax_half<T, 1>(F, 0, B);
+                __syncthreads();
+                qsmg::relax_half<T, 1>(F, 1, B);
+                __syncthreads();
+            }
+        }
+    }
+    cl.sync();
+    mk(78);
+    for (int l = ld - 1; l >= 0; --l) {
+        const qsclu::DLvl<T> D = V.dl(A, cl, l);
+        if (l + 1 == ld)
+            qsclu::d_prolong_w<T>(D, cl.map_shared_rank(qsclu::arr<T>(V.cb, Y, ld, 0), 0),
+                                  Y.n[ld]);
+        else
+            qsclu::d_prolong_d<T>(D, V.dl(A, cl, l + 1));
+        cl.sync();
+        for (int s = 0; s < A.nu2; ++s) {
+            qsclu::d_relax<T>(D, 0);
+            cl.sync();
+            qsclu::d_relax<T>(D, 1);
+            cl.sync();
+        }
+        mk(81 + l);
+    }
+}
+
+// Float64 form: the solve of component bid / C by its cluster, to the grid
+// path's stopping test; fn: ||f||^2 per component (thread 0).  Blocks of
+// other clusters return at once; the caller's grid barrier follows.
+__device__ __noinline__ void mg_solve_cluster64(const EngineArgs &A, const SolveSpec &V, int bid,
+                                   void *smem_base, qsmg::CoarseInv ci, const double *fn) {
     namespace cg = cooperative_groups;
-    if (bid >= A.cl_size) return;
+    const int C = A.cl_size, comp = bid / C;
+    if (comp >= V.nc) return;
     cg::cluster_group cl = cg::this_cluster();
-    const int C = A.cl_size, rank = (int)cl.block_rank();
-    void *cb = (char *)smem_base + A.cl_smem_offset;
     __shared__ qsclu::Layout Y;
     __shared__ int s_conv;
     __shared__ double s_rel;
-    if (threadIdx.x == 0) Y = qsclu::cluster_layout(A.lev_n, A.nlev, C);
+    if (threadIdx.x == 0) Y = qsclu::cluster_layout(A.lev_n, A.nlev, C, sizeof(double));
     __syncthreads();
-    const int ld = Y.ld, L = Y.L;
-    const bool scr = V.screened;
-    auto dl = [&](int l) {
-        qsclu::DLvl D;
-        D.n = Y.n[l];
-        D.R = Y.R[l];
-        D.row0 = rank * D.R;
-        for (int c = 0; c < 2; ++c) {
-            const int cc = c < NC ? c : 0;
-            D.u[c] = qsclu::arr(cb, Y, l, cc);
-            D.f[c] = qsclu::arr(cb, Y, l, 2 + cc);
-            D.up_u[c] = rank > 0 ? cl.map_shared_rank(D.u[c], rank - 1) : nullptr;
-            D.dn_u[c] = rank < C - 1 ? cl.map_shared_rank(D.u[c], rank + 1) : nullptr;
-        }
-        D.k = scr ? qsclu::arr(cb, Y, l, 4) : nullptr;
-        D.d = scr ? qsclu::arr(cb, Y, l, 5) : nullptr;
-        D.up_k = D.dn_k = nullptr;
-        D.h2 = A.lev_h2[l];
-        D.inv_h2 = A.lev_inv_h2[l];
-        D.omega = A.omega;
-        return D;
-    };
-    auto lv = [&](int l) {  // a local level of block 0 (this block's copy of the layout)
-        Lvl<double> v;
-        for (int c = 0; c < 2; ++c) {
-            const int cc = c < NC ? c : 0;
-            v.u[c] = qsclu::arr(cb, Y, l, cc);
-            v.f[c] = qsclu::arr(cb, Y, l, 2 + cc);
-        }
-        v.k = scr ? qsclu::arr(cb, Y, l, 4) : nullptr;
-        v.d = scr ? qsclu::arr(cb, Y, l, 5) : nullptr;
-        v.n = Y.n[l];
-        v.h2 = v.h2t = A.lev_h2[l];
-        v.inv_h2 = v.inv_h2t = A.lev_inv_h2[l];
-        v.omega = A.omega;
-        return v;
-    };
-    // level 0: this block's rows of the warm start, the source and kappa
-    {
-        const qsclu::DLvl D = dl(0);
+    const ClusterView<double> cv{(char *)smem_base + A.cl_smem_offset, &Y,
+                                 (int)cl.block_rank(), C, V.screened};
+    const double *const gu = V.u[comp];
+    const double *const gf = V.f[comp];
+    {  // level 0: this block's rows of the warm start, the source and kappa
+        const qsclu::DLvl<double> D = cv.dl(A, cl, 0);
         const size_t g0 = (size_t)D.row0 * D.n;
         for (int q = threadIdx.x; q < D.R * D.n; q += blockDim.x) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                D.u[c][q] = V.u[c][g0 + q];
-                D.f[c][q] = V.f[c][g0 + q];
-            }
-            if (scr) {
+            D.u[q] = gu[g0 + q];
+            D.f[q] = gf[g0 + q];
+            if (cv.scr) {
                 D.k[q] = A.kap[g0 + q];
                 D.d[q] = A.invd0[g0 + q];
             }
         }
     }
     cl.sync();
-    double *const slots0 = cl.map_shared_rank((double *)((char *)cb + Y.slots), 0);
+    double *const slots0 = cl.map_shared_rank((double *)((char *)cv.cb + Y.slots), 0);
     const double fl = 1e-13 * A.lev_inv_h2[0];
     const qsmg::Marks mk{A.trace, &A.sc->trace_n, A.trace_cap};  // block 0, thread 0
     int it = 0;
     bool conv = false;
     for (;;) {
-        if (it > 0) {  // ||f - A u||^2 and ||u||^2 of the cluster's level 0
-            const qsclu::DLvl D = dl(0);
-            double s[4] = {0.0, 0.0, 0.0, 0.0};
+        if (it > 0) {  // ||f - A u||^2 and ||u||^2 of the component
+            const qsclu::DLvl<double> D = cv.dl(A, cl, 0);
+            double s[2] = {0.0, 0.0};
             for (int q = threadIdx.x; q < D.R * D.n; q += blockDim.x) {
                 const int ly = q / D.n, x = q - ly * D.n;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const double r = qsclu::d_res(D, c, x, D.row0 + ly, q);
-                    s[c] += r * r;
-                    s[2 + c] += D.u[c][q] * D.u[c][q];
-                }
+                const double r = qsclu::d_res(D, x, D.row0 + ly, q);
+                s[0] += r * r;
+                s[1] += D.u[q] * D.u[q];
             }
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < 2; ++e) {
                 const double t = block_sum(s[e]);
-                if (threadIdx.x == 0) slots0[rank * 4 + e] = t;
+                if (threadIdx.x == 0) slots0[cv.rank * 2 + e] = t;
             }
             cl.sync();
-            __shared__ double s_tot[4];
+            __shared__ double s_tot[2];
             if (threadIdx.x < 32) {  // warp 0: one remote load per lane, then a warp sum
-                double tot[4];
-                for (int e = 0; e < 4; ++e) {
+                for (int e = 0; e < 2; ++e) {
                     double v = 0.0;
-                    for (int b = threadIdx.x; b < C; b += 32) v += slots0[b * 4 + e];
+                    for (int b = threadIdx.x; b < C; b += 32) v += slots0[b * 2 + e];
                     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                    tot[e] = v;
+                    if (threadIdx.x == 0) s_tot[e] = v;
                 }
-                if (threadIdx.x == 0)
-                    for (int e = 0; e < 4; ++e) s_tot[e] = tot[e];
             }
             if (threadIdx.x == 0) {
-                const double *tot = s_tot;
-                int cv = 1;
-                double rel = 0.0;
-                for (int c = 0; c < NC; ++c) {
-                    if (fn[c] == 0.0) continue;
-                    double thr = fmax(A.mg_tol * A.mg_tol * fn[c], A.mg_atol * A.mg_atol);
-                    thr = fmax(thr, fl * fl * tot[2 + c]);
-                    if (tot[c] > thr) cv = 0;
-                    rel = fmax(rel, sqrt(tot[c] / fn[c]));
-                }
-                s_conv = cv;
-                s_rel = rel;
+                const double f2 = fn[comp];
+                double thr = fmax(A.mg_tol * A.mg_tol * f2, A.mg_atol * A.mg_atol);
+                thr = fmax(thr, fl * fl * s_tot[1]);
+                s_conv = f2 == 0.0 || s_tot[0] <= thr;
+                s_rel = f2 > 0.0 ? sqrt(s_tot[0] / f2) : 0.0;
             }
             __syncthreads();
             conv = s_conv != 0;
             mk(70);
             if (conv || it >= A.mg_max_vcycles) break;
         }
-        // down: the distributed levels
-        for (int l = 0; l < ld; ++l) {
-            const qsclu::DLvl D = dl(l);
-            const int nu = D.n > A.block_level_n ? A.nu1 : A.nu1c;
-            for (int s = 0; s < nu; ++s) {
-                qsclu::d_relax<NC>(D, 0);
-                cl.sync();
-                qsclu::d_relax<NC>(D, 1);
-                cl.sync();
-            }
-            const int m = Y.n[l + 1];
-            double *cu[2], *cf[2], *ck = nullptr, *cd = nullptr;
-            int crow0;
-            if (l + 1 < ld) {  // into this block's strip of the next level
-                for (int c = 0; c < 2; ++c) {
-                    cu[c] = qsclu::arr(cb, Y, l + 1, c < NC ? c : 0);
-                    cf[c] = qsclu::arr(cb, Y, l + 1, 2 + (c < NC ? c : 0));
-                }
-                if (scr) {
-                    ck = qsclu::arr(cb, Y, l + 1, 4);
-                    cd = qsclu::arr(cb, Y, l + 1, 5);
-                }
-                crow0 = D.row0 >> 1;
-            } else {  // into block 0's whole first local level
-                for (int c = 0; c < 2; ++c) {
-                    cu[c] = cl.map_shared_rank(qsclu::arr(cb, Y, ld, c < NC ? c : 0), 0);
-                    cf[c] = cl.map_shared_rank(qsclu::arr(cb, Y, ld, 2 + (c < NC ? c : 0)), 0);
-                }
-                if (scr) {
-                    ck = cl.map_shared_rank(qsclu::arr(cb, Y, ld, 4), 0);
-                    cd = cl.map_shared_rank(qsclu::arr(cb, Y, ld, 5), 0);
-                }
-                crow0 = 0;
-            }
-            qsclu::d_restrict<NC>(D, m, crow0, cu, cf, ck, cd, A.lev_h2[l + 1], it == 0);
-            cl.sync();
-            mk(71 + l);
-        }
-        // the local levels in block 0 (all its warps: each SM sub-partition
-        // holds a quarter of the float64 pipe), down to the coarsest inverse
-        if (rank == 0) {
-            const Thr B{(int)threadIdx.x, (int)blockDim.x};
-            for (int l = ld; l < L - 1; ++l) {
-                const Lvl<double> F = lv(l), Cc = lv(l + 1);
-                const int nu = F.n > A.block_level_n ? A.nu1 : A.nu1c;
-                for (int s = 0; s < nu; ++s) {
-                    qsmg::relax_half<double, NC>(F, 0, B);
-                    __syncthreads();
-                    qsmg::relax_half<double, NC>(F, 1, B);
-                    __syncthreads();
-                }
-                qsmg::restrict_res<double, NC>(F, Cc, B, it == 0);
-                __syncthreads();
-            }
-            double *work = (double *)((char *)cb + Y.work);
-            qsmg::coarse_solve<double, NC>(lv(L - 1), work, ci);
-            for (int l = L - 2; l >= ld; --l) {
-                const Lvl<double> F = lv(l), Cc = lv(l + 1);
-                qsmg::prolong_add<double, NC>(F, Cc, B);
-                __syncthreads();
-                for (int s = 0; s < A.nu2; ++s) {
-                    qsmg::relax_half<double, NC>(F, 0, B);
-                    __syncthreads();
-                    qsmg::relax_half<double, NC>(F, 1, B);
-                    __syncthreads();
-                }
-            }
-        }
-        cl.sync();
-        mk(78);
-        // up: the distributed levels
-        for (int l = ld - 1; l >= 0; --l) {
-            const qsclu::DLvl D = dl(l);
-            if (l + 1 == ld) {
-                const double *u0 = cl.map_shared_rank(qsclu::arr(cb, Y, ld, 0), 0);
-                const double *u1 = cl.map_shared_rank(qsclu::arr(cb, Y, ld, NC > 1 ? 1 : 0), 0);
-                qsclu::d_prolong_w<NC>(D, u0, u1, Y.n[ld]);
-            } else {
-                qsclu::d_prolong_d<NC>(D, dl(l + 1));
-            }
-            cl.sync();
-            for (int s = 0; s < A.nu2; ++s) {
-                qsclu::d_relax<NC>(D, 0);
-                cl.sync();
-                qsclu::d_relax<NC>(D, 1);
-                cl.sync();
-            }
-            mk(81 + l);
-        }
+        cluster_vcycle<double>(A, cl, cv, ci, it == 0, mk);
         ++it;
     }
     {  // this block's rows of the solution
-        const qsclu::DLvl D = dl(0);
+        const qsclu::DLvl<double> D = cv.dl(A, cl, 0);
         const size_t g0 = (size_t)D.row0 * D.n;
-        for (int q = threadIdx.x; q < D.R * D.n; q += blockDim.x)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) V.u[c][g0 + q] = D.u[c][q];
+        double *const u = V.u[comp];
+        for (int q = threadIdx.x; q < D.R * D.n; q += blockDim.x) u[g0 + q] = D.u[q];
     }
-    if (bid == 0 && threadIdx.x == 0) {
+    if (cv.rank == 0 && threadIdx.x == 0) {
         DevScalars *sc = A.sc;
-        sc->vcycles[V.kind] += it;
-        if (s_rel > sc->max_relres) sc->max_relres = s_rel;
+        atomicMax(&sc->cl_cycles, it);
+        atomicMax((unsigned long long *)&sc->max_relres,
+                  (unsigned long long)__double_as_longlong(s_rel));
         if (!conv) sc->not_converged = 1;
     }
     cl.sync();  // no block leaves while another may still read its shared memory
+}
+
+// Refined form, the cluster part of an outer iteration: the float32 V-cycle
+// of the correction e (from zero) with the float32 residual as right-hand
+// side, by the cluster of component bid / C; e is written to A.e32[comp].
+__device__ __noinline__ void cluster_inner_cycle(const EngineArgs &A, const SolveSpec &V, int bid,
+                                    void *smem_base, qsmg::CoarseInv ci, bool first) {
+    namespace cg = cooperative_groups;
+    const int C = A.cl_size, comp = bid / C;
+    if (comp >= V.nc) return;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ qsclu::Layout Y;
+    if (threadIdx.x == 0) Y = qsclu::cluster_layout(A.lev_n, A.nlev, C, sizeof(float));
+    __syncthreads();
+    const ClusterView<float> cv{(char *)smem_base + A.cl_smem_offset, &Y,
+                                (int)cl.block_rank(), C, V.screened};
+    const qsmg::Marks mk{A.trace, &A.sc->trace_n, A.trace_cap};
+    {
+        const qsclu::DLvl<float> D = cv.dl(A, cl, 0);
+        const size_t g0 = (size_t)D.row0 * D.n;
+        const float *const r = A.r32[0][comp];
+        for (int q = threadIdx.x; q < D.R * D.n; q += blockDim.x) {
+            D.u[q] = 0.f;
+            D.f[q] = r[g0 + q];
+            if (first && cv.scr) {  // kappa is fixed during a solve
+                D.k[q] = A.k32[g0 + q];
+                D.d[q] = A.d32[g0 + q];
+            }
+        }
+    }
+    cl.sync();
+    cluster_vcycle<float>(A, cl, cv, ci, first, mk);
+    {
+        const qsclu::DLvl<float> D = cv.dl(A, cl, 0);
+        const size_t g0 = (size_t)D.row0 * D.n;
+        float *const e = A.e32[comp];
+        for (int q = threadIdx.x; q < D.R * D.n; q += blockDim.x) e[g0 + q] = D.u[q];
+    }
+    cl.sync();
+}
+
+// Refined form, the grid-wide part of an outer iteration: in float64,
+// u += e and r <- r - (lap_h - kappa) e (= f - A(u + e)), with the 5-point
+// sum of the float32 e formed exactly as a float32 pair (error-free sums and
+// an FMA product) before it is widened; r32 = (float) r for the next cycle;
+// the float32 copy of u where asked; ||r||^2, ||u||^2 into norms_out.
+template <int NC>
+__device__ __noinline__ void update_from_e(const EngineArgs &A, const SolveSpec &V, Thr T,
+                              double *norms_out) {
+    const int n = A.N;
+    const double inv_h2 = A.lev_inv_h2[0];
+    const double *const kap = V.screened ? A.kap : nullptr;
+    float nrm[4] = {0.f, 0.f, 0.f, 0.f};
+    for (qsmg::Walk w(T.t0, T.nt, n); w.q < n * n; w.next()) {
+        const int x = w.col, y = w.row, i = w.q;
+        const float cw = (float)(4 + qsmg::walls(x, y, n));
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const float *e = A.e32[c];
+            const float ef = e[i];
+            float hi = 0.f, lo = 0.f;
+            if (x > 0) qstile::two_sum_acc(hi, lo, e[i - 1]);
+            if (x < n - 1) qstile::two_sum_acc(hi, lo, e[i + 1]);
+            if (y > 0) qstile::two_sum_acc(hi, lo, e[i - n]);
+            if (y < n - 1) qstile::two_sum_acc(hi, lo, e[i + n]);
+            const float pc = __fmul_rn(cw, ef);
+            const float pe = __fmaf_rn(cw, ef, -pc);  // cw ef = pc + pe exactly
+            qstile::two_sum_acc(hi, lo, -pc);
+            lo = __fsub_rn(lo, pe);
+            const double ec = (double)ef;
+            double ae = ((double)hi + (double)lo) * inv_h2;
+            if (kap) ae -= kap[i] * ec;
+            const double u = V.u[c][i] + ec;
+            const double r = A.r64[c][i] - ae;
+            const float rf = (float)r, uf = (float)u;
+            V.u[c][i] = u;
+            A.r64[c][i] = r;
+            A.r32[0][c][i] = rf;
+            if (V.u32[c]) V.u32[c][i] = uf;
+            nrm[c] = __fmaf_rn(rf, rf, nrm[c]);
+            nrm[2 + c] = __fmaf_rn(uf, uf, nrm[2 + c]);
+        }
+    }
+    block_sum4f(nrm);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            atomicAdd(norms_out + c, (double)nrm[c]);
+            atomicAdd(norms_out + 2 + c, (double)nrm[2 + c]);
+        }
+}
+
+// Refined form in clusters: each outer iteration is one float32 V-cycle of
+// the correction per component, by that component's cluster, then the
+// float64 update of u and r by the whole grid (two grid barriers).  A
+// separate function: inlined, its registers made the slice engine spill.
+__device__ __noinline__ bool mg_solve_ref_cluster(const EngineArgs &A, const Sync &S,
+                                                  const SolveSpec &V, int &slot, int bid,
+                                                  int nblk, void *smem_base, qsmg::CoarseInv ci,
+                                                  const double *s_fn) {
+    DevScalars *sc = A.sc;
+    const Thr T = grid_thr(bid, nblk);
+    __shared__ int s_conv;
+    // Refined form in clusters: each outer iteration is one float32
+    // V-cycle of the correction per component, by that component's
+    // cluster, then the float64 update of u and r by the whole grid.
+    if (V.nc == 1) residual_norm<1>(A, V, sc->rnorm[slot & 3], T, true, A.r32[0]);
+    else residual_norm<2>(A, V, sc->rnorm[slot & 3], T, true, A.r32[0]);
+    if (bid == 0 && threadIdx.x == 0)
+        for (int e = 0; e < 4; ++e) sc->rnorm[(slot + 2) & 3][e] = 0.0;
+    SYNC(21);
+    double rel = 0.0;
+    int it = 0;
+    bool conv = false;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const double fl = 1e-13 * A.lev_inv_h2[0];
+            int cv = 1;
+            rel = 0.0;
+            for (int c = 0; c < V.nc; ++c) {
+                const double fn = s_fn[c];
+                if (fn == 0.0) continue;
+                const double rn = vload(&sc->rnorm[slot & 3][c]);
+                const double un = vload(&sc->rnorm[slot & 3][2 + c]);
+                double thr = fmax(A.mg_tol * A.mg_tol * fn, A.mg_atol * A.mg_atol);
+                thr = fmax(thr, fl * fl * un);
+                if (rn > thr) cv = 0;
+                rel = fmax(rel, sqrt(rn / fn));
+            }
+            s_conv = cv;
+        }
+        __syncthreads();
+        conv = s_conv != 0;
+        __syncthreads();
+        ++slot;
+        if (conv || it >= A.mg_max_vcycles) break;
+        cluster_inner_cycle(A, V, bid, smem_base, ci, it == 0);
+        SYNC(24);
+        if (V.nc == 1) update_from_e<1>(A, V, T, sc->rnorm[slot & 3]);
+        else update_from_e<2>(A, V, T, sc->rnorm[slot & 3]);
+        if (bid == 0 && threadIdx.x == 0)
+            for (int e = 0; e < 4; ++e) sc->rnorm[(slot + 2) & 3][e] = 0.0;
+        SYNC(25);
+        ++it;
+    }
+    if (bid == 0 && threadIdx.x == 0) {
+        sc->vcycles[V.kind] += it;
+        if (rel > sc->max_relres) sc->max_relres = rel;
+        if (!conv) sc->not_converged = 1;
+    }
+    if (V.u32[0] && it == 0) {  // converged at once: the float32 copy of u
+        const int nn = A.N * A.N;
+        for (int c = 0; c < V.nc; ++c)
+            for (int k = T.t0; k < nn; k += T.nt) V.u32[c][k] = (float)V.u[c][k];
+        SYNC(23);
+    }
+    return true;
 }
 
 // Iterate until, for every component,
@@ -714,12 +876,21 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
         SYNC(20);
     }
     if (zero_mask == (1 << V.nc) - 1) return true;
-    if (!REF && A.cl_size > 1) {  // small grid: the first cluster solves alone
-        if (V.nc == 1) mg_solve_cluster<1>(A, V, bid, smem_base, ci, s_fn);
-        else mg_solve_cluster<2>(A, V, bid, smem_base, ci, s_fn);
+#ifndef QS_NO_CLUSTER_SOLVES
+    if (!REF && A.cl_size > 1) {  // one cluster per component solves alone
+        mg_solve_cluster64(A, V, bid, smem_base, ci, s_fn);
         SYNC(22);
+        if (bid == 0 && threadIdx.x == 0) {
+            A.sc->vcycles[V.kind] += A.sc->cl_cycles;
+            A.sc->cl_cycles = 0;
+        }
         return true;
     }
+#endif
+#ifndef QS_NO_CLUSTER_SOLVES
+    if (REF && A.cl_size > 1)
+        return mg_solve_ref_cluster(A, S, V, slot, bid, nblk, smem_base, ci, s_fn);
+#endif
     __shared__ Hier<double> H64;
     __shared__ Hier<float> H32;
     __syncthreads();
