@@ -223,12 +223,11 @@ __device__ __forceinline__ void apply_guess(double *u, double *h1, double *h2, i
 // moment accumulators and the next-slice density buffer
 template <typename P>
 __device__ void phase_psi_rhs(const EngineArgs &A, const PS<P> &Q, const double *ncur,
-                              double *nnext, bool base, int j, int q, int m, Thr T,
+                              double *nnext, bool base, int j, int q, double frac, Thr T,
                               const Guess &g) {
     const int nn = A.N * A.N;
     double s = 0.0, cs = 0.0;
     if (A.a2_base) {  // |A|^2 of this slice, linear in xi between base slices
-        const double frac = (double)q / (double)m;
         const double *a0 = A.a2_base + (size_t)j * nn;
         const double *a1 = (j + 1 < A.n_xi) ? a0 + nn : nullptr;
         for (int i = T.t0; i < nn; i += T.nt)
@@ -349,10 +348,9 @@ __device__ __forceinline__ double dyo(const double *u, int n, int iy, int i, dou
 // driver), kappa = n_* / (1+psi) with the smoother's inverse diagonal, grad psi
 template <typename P>
 __device__ void phase_assemble1(const EngineArgs &A, const PS<P> &Q, const double *ncur, int j,
-                                int q, int m, Thr T, const Guess &g) {
+                                int q, double frac, Thr T, const Guess &g) {
     const int n = A.N, nn = n * n;
     const double inv2h = 0.5 * A.inv_h;
-    const double frac = (double)q / (double)m;
     const double *J0 = A.jzb + (size_t)j * nn;
     const double *J1 = (j + 1 < A.n_xi) ? A.jzb + (size_t)(j + 1) * nn : nullptr;
     unsigned hits = 0;
@@ -759,6 +757,15 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
                         {REF ? A.bx32 : nullptr, REF ? A.by32 : nullptr}};
 
     int m = A.m_sched ? A.m_sched[A.j_begin] : 1;
+    // per-slice scalars computed by thread 0 and read by every thread
+    __shared__ struct {
+        Guess g;
+        double frac, dxi;
+        int m;
+    } s_ctl;
+    __syncthreads();
+    if (threadIdx.x == 0) s_ctl.dxi = A.dxi0 / m;
+    __syncthreads();
     int slot = 0, pk = 0, sub = 0;
     int have = 0;                        // previous solutions available for the guess
     double gx0 = 0.0, gx1 = 0.0, gx2 = 0.0;  // their xi
@@ -773,7 +780,7 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
             if (m > sc->max_m) sc->max_m = m;
         }
         const bool last = (j == A.n_xi - 1);
-        const double dxi = A.dxi0 / m;
+        const double dxi = s_ctl.dxi;
         if (A.ckpt && j % A.ckpt_every == 0) {  // plasma state before slice j
             double *cp = A.ckpt + (size_t)(j / A.ckpt_every) * 4 * A.np;
             for (int64_t p = T.t0; p < A.np; p += T.nt) {
@@ -786,13 +793,22 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
         for (int q = 0; q < m; ++q) {
             const bool base = (q == 0);
             const double xs = j * A.dxi0 + q * dxi;  // xi of this slice (from xi_min)
-            const Guess g = make_guess(A.ws_order, have, xs, gx0, gx1, gx2);
-            phase_psi_rhs<P>(A, Q, ncur, nnext, base, j, q, m, T, g);
+            // the guess weights and the sub-step fraction by one thread
+            // (float64 divides repeated by every thread cost microseconds)
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_ctl.g = make_guess(A.ws_order, have, xs, gx0, gx1, gx2);
+                s_ctl.frac = (double)q / (double)m;
+            }
+            __syncthreads();
+            const Guess g = s_ctl.g;
+            const double frac = s_ctl.frac;
+            phase_psi_rhs<P>(A, Q, ncur, nnext, base, j, q, frac, T, g);
             if (!S(2)) return false;
             if (!mg_solve<REF>(A, S, Vpsi, slot, bid, nblk, smem, s_inv_ready)) return false;
             phase_moments<P>(A, Q, T, bid, nblk, smem);
             if (!S(3)) return false;
-            phase_assemble1<P>(A, Q, ncur, j, q, m, T, g);
+            phase_assemble1<P>(A, Q, ncur, j, q, frac, T, g);
             if (!S(4)) return false;
             if (!mg_solve<REF>(A, S, Veb, slot, bid, nblk, smem, s_inv_ready)) return false;
             phase_assemble2<P>(A, Q, ncur, T, g);
@@ -822,17 +838,27 @@ __device__ bool run_step(const EngineArgs &A, int bid, int nblk, const Sync &S, 
             ++pk;
         }
         if (last) break;
-        const double vm = __longlong_as_double((long long)vload(&sc->vmax_bits[(pk - 1) & 1]));
-        if (lead && A.diag_vmax) A.diag_vmax[j] = vm;
-        if (A.m_sched) {
-            m = A.m_sched[j + 1];
-        } else if (vm <= A.V0) {
-            m = 1;
-        } else {
-            double r = ceil(vm / A.V0);
-            m = r > (double)A.refine_k ? A.refine_k : (int)r;
-            if (m < 1) m = 1;
+        // the next base slice's sub-steps (Sec. 5.1), by one thread
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double vm =
+                __longlong_as_double((long long)vload(&sc->vmax_bits[(pk - 1) & 1]));
+            if (lead && A.diag_vmax) A.diag_vmax[j] = vm;
+            int mn;
+            if (A.m_sched) {
+                mn = A.m_sched[j + 1];
+            } else if (vm <= A.V0) {
+                mn = 1;
+            } else {
+                double r = ceil(vm / A.V0);
+                mn = r > (double)A.refine_k ? A.refine_k : (int)r;
+                if (mn < 1) mn = 1;
+            }
+            s_ctl.m = mn;
+            s_ctl.dxi = A.dxi0 / mn;
         }
+        __syncthreads();
+        m = s_ctl.m;
     }
     return true;
 }

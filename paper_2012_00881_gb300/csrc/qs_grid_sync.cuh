@@ -74,6 +74,18 @@ struct Team {
     int t, nt;
 };
 
+// The grid-wide team of a persistent launch with runs of 32 consecutive
+// indices handed to the blocks in turn (run w * gridDim.x + b to warp w of
+// block b): a loop shorter than the launch (a coarse level) still spreads
+// over every SM, which float64 work needs on GB300 (about two FMA per clock
+// per SM), while each warp's accesses stay contiguous.  t ranges over a
+// permutation of [0, nt) (blockDim.x a multiple of 32).
+__device__ __forceinline__ Team spread_team() {
+    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    return Team{((w * (int)gridDim.x + (int)blockIdx.x) << 5) + lane,
+                (int)(gridDim.x * blockDim.x)};
+}
+
 // Adds the block's sums of vals[0 .. k) into dst[0 .. k) (one atomic each).
 template <int kThreadsMax>
 __device__ void block_sum_add(const double *vals, int k, double *dst) {

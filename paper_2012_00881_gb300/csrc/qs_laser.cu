@@ -22,8 +22,11 @@
 // Execution: one persistent cooperative launch per call runs every time step
 // and slice: a right-hand-side phase per slice (which also writes the
 // previous slice's new envelope back), the kappa hierarchy, then the cycles.
-// Levels of side <= 32 run in block 0 on __syncthreads, larger ones on the
-// bounded grid barrier of qs_grid_sync.cuh.
+// Levels of side <= 8 run in block 0 on __syncthreads; larger ones are
+// staged tile by tile in shared memory (see "Staged grid levels" below), one
+// bounded grid barrier (qs_grid_sync.cuh) per level and leg.  Grid-wide
+// loops hand runs of 32 cells to the blocks in turn, so that float64 work
+// spreads over every SM.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,7 +43,9 @@ using qsync::Team;
 
 constexpr int kMaxLevels = 14;
 constexpr int kThreads = 512;
-constexpr int kLocalN = 32;            // levels this small run in block 0
+constexpr int kLocalN = 8;             // levels this small run in block 0
+constexpr int kNu = 2;                 // pre- and post-sweeps, V(2, 2)
+constexpr int kTileX = 32, kTileY = 16;  // largest staged output tile
 constexpr int kCoarseSweeps = 20;
 constexpr long long kBarrierLimit = 4000000000LL;  // clock cycles, ~2 s
 
@@ -193,6 +198,284 @@ __device__ void prolong_correct(const LzLevel &F, const LzLevel &C, Team tm) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Staged grid levels.  A grid-wide level costs a grid barrier per colour
+// sweep, residual, restriction and prolongation (eleven per V-cycle).  Here
+// every block takes an output tile plus a halo, stages u, f, kappa and the
+// inverse diagonal in shared memory and runs all the half sweeps of a leg
+// there, recomputing the halo: after half sweep s only the cells at least
+// s + 1 from a cut side of the region are exact, and those are the only ones
+// updated.  A down leg (pre-sweeps, residual, restriction) and an up leg
+// (prolongation, post-sweeps) each cost one grid barrier; the level-0 up leg
+// also sums |f - A u|^2 of its tile for the stopping test.
+// ---------------------------------------------------------------------------
+
+struct Reg {
+    int ox, oy, RX, RY, R;  // staged region: origin and extent
+    int ax, bx, ay, by;     // its intersection with the domain
+    bool cl, cr, cb, ct;    // which sides are cut (not the domain wall)
+};
+
+__device__ __forceinline__ Reg make_reg(int tx0, int ty0, int TX, int TY, int H, int n) {
+    Reg g;
+    g.ox = tx0 - H;
+    g.oy = ty0 - H;
+    g.RX = TX + 2 * H;
+    g.RY = TY + 2 * H;
+    g.R = g.RX * g.RY;
+    g.ax = max(g.ox, 0);
+    g.bx = min(g.ox + g.RX - 1, n - 1);
+    g.ay = max(g.oy, 0);
+    g.by = min(g.oy + g.RY - 1, n - 1);
+    g.cl = g.ax > 0;
+    g.cr = g.bx < n - 1;
+    g.cb = g.ay > 0;
+    g.ct = g.by < n - 1;
+    return g;
+}
+
+// output tile of a staged level: halved (down to 8) while the level has
+// fewer tiles than half the blocks, so that its work still spreads
+__device__ __forceinline__ void lz_tile(int n, int nblk, int &TX, int &TY) {
+    TX = kTileX;
+    TY = kTileY;
+    for (;;) {
+        const int tiles = ((n + TX - 1) / TX) * ((n + TY - 1) / TY);
+        if (2 * tiles >= nblk) break;
+        if (TX >= TY && TX > 8) TX >>= 1;
+        else if (TY > 8) TY >>= 1;
+        else break;
+    }
+}
+
+// staged arrays of a region of R cells: u, f, kappa, inverse diagonal
+struct LzSmem {
+    double2 *u, *f, *k, *d;
+};
+
+__device__ __forceinline__ LzSmem lz_layout(double2 *sm, int R) {
+    return LzSmem{sm, sm + R, sm + 2 * R, sm + 3 * R};
+}
+
+// shared memory of the largest staged region (tile + halo 2 kNu + 1)
+__host__ __device__ constexpr size_t lz_smem_bytes() {
+    return (size_t)4 * (kTileX + 2 * (2 * kNu + 1)) * (kTileY + 2 * (2 * kNu + 1)) *
+           sizeof(double2);
+}
+
+// 16-byte global -> shared copy, zero-filled when !valid (source size 0)
+__device__ __forceinline__ void cp16(double2 *dst, const double2 *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// (lap - kappa) u at staged cell li = (x, y) (odd ghosts: a wall adds to the
+// diagonal)
+__device__ __forceinline__ double2 staged_apply(const LzSmem &t, int RX, int n, double ih2, int li,
+                                                int x, int y) {
+    double2 nb = make_double2(0.0, 0.0);
+    if (x > 0) nb = cadd(nb, t.u[li - 1]);
+    if (x < n - 1) nb = cadd(nb, t.u[li + 1]);
+    if (y > 0) nb = cadd(nb, t.u[li - RX]);
+    if (y < n - 1) nb = cadd(nb, t.u[li + RX]);
+    const int w = (x == 0) + (x == n - 1) + (y == 0) + (y == n - 1);
+    const double2 lap = cscale(ih2, csub(nb, cscale(4.0 + w, t.u[li])));
+    return csub(lap, cmul(t.k[li], t.u[li]));
+}
+
+// half sweeps 0 .. ns - 1 (colour s & 1) on the staged region
+__device__ void staged_sweeps(const Reg &g, int n, double ih2, const LzSmem &t, int ns) {
+    for (int s = 0; s < ns; ++s) {
+        const int colour = s & 1;
+        const int X0 = g.cl ? g.ax + s + 1 : g.ax, X1 = g.cr ? g.bx - s - 1 : g.bx;
+        const int Y0 = g.cb ? g.ay + s + 1 : g.ay, Y1 = g.ct ? g.by - s - 1 : g.by;
+        const int rows = Y1 - Y0 + 1, hw = (X1 - X0 + 2) >> 1;
+        const int cnt = (rows > 0 && hw > 0) ? rows * hw : 0;
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const int r = q / hw, y = Y0 + r;
+            const int x = X0 + ((X0 + y + colour) & 1) + 2 * (q - r * hw);
+            if (x > X1) continue;
+            const int li = (y - g.oy) * g.RX + (x - g.ox);
+            const double2 res = csub(t.f[li], staged_apply(t, g.RX, n, ih2, li, x, y));
+            t.u[li] = cadd(t.u[li], cmul(res, t.d[li]));
+        }
+        __syncthreads();
+    }
+}
+
+// stage f, kappa, 1/diag of level F and u from usrc (nullptr: zero) on g
+__device__ void stage(const LzLevel &F, const Reg &g, const LzSmem &t, const double2 *usrc) {
+    const int n = F.n;
+    for (int q = threadIdx.x; q < g.R; q += blockDim.x) {
+        const int r = q / g.RX, x = g.ox + (q - r * g.RX), y = g.oy + r;
+        const bool in = x >= 0 && x < n && y >= 0 && y < n;
+        const int gi = in ? y * n + x : 0;
+        cp16(t.f + q, F.f + gi, in);
+        cp16(t.k + q, F.kap + gi, in);
+        cp16(t.d + q, F.idg + gi, in);
+        if (usrc) cp16(t.u + q, usrc + gi, in);
+        else t.u[q] = make_double2(0.0, 0.0);
+    }
+    cp_wait();
+    __syncthreads();
+}
+
+// Down leg of level F -> C for this block's tiles: pre-sweeps from the
+// warm start F.u (level 0) or zero, residual, restriction into C.f
+// (C.u = 0).  The smoothed tile goes to F.r, not F.u: other blocks still
+// stage F.u around their tiles during this leg.
+__device__ void staged_down(const LzLevel &F, const LzLevel &C, bool warm, double2 *sm, int bid,
+                            int nblk) {
+    const int n = F.n, m = C.n;
+    int TX, TY;
+    lz_tile(n, nblk, TX, TY);
+    const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
+    for (int tile = bid; tile < ntx * nty; tile += nblk) {
+        const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
+        const Reg g = make_reg(tx0, ty0, TX, TY, 2 * kNu + 1, n);
+        const LzSmem t = lz_layout(sm, g.R);
+        stage(F, g, t, warm ? F.u : nullptr);
+        staged_sweeps(g, n, F.ih2, t, 2 * kNu);
+        const int CX = TX / 2, CY = TY / 2;
+        for (int q = threadIdx.x; q < CX * CY; q += blockDim.x) {
+            const int r = q / CX;
+            const int I = tx0 / 2 + (q - r * CX), J = ty0 / 2 + r;
+            if (I >= m || J >= m) continue;
+            double2 s = make_double2(0.0, 0.0);
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    const int x = 2 * I + a, y = 2 * J + b;
+                    const int li = (y - g.oy) * g.RX + (x - g.ox);
+                    s = cadd(s, csub(t.f[li], staged_apply(t, g.RX, n, F.ih2, li, x, y)));
+                }
+            C.f[J * m + I] = cscale(0.25, s);
+            C.u[J * m + I] = make_double2(0.0, 0.0);
+        }
+        for (int q = threadIdx.x; q < TX * TY; q += blockDim.x) {
+            const int r = q / TX, x = tx0 + (q - r * TX), y = ty0 + r;
+            if (x < n && y < n) F.r[y * n + x] = t.u[(y - g.oy) * g.RX + (x - g.ox)];
+        }
+        __syncthreads();  // the next tile reuses the staged arrays
+    }
+}
+
+// Up leg of level F for this block's tiles: the pre-smoothed u (F.r, from
+// the down leg) plus the bilinear prolongation of C.u, post-sweeps, the tile
+// to F.u.  With `norm` (level 0) the halo is one cell wider and
+// |f - A u|^2 of the tile is added to *norm_sum (this thread's share).
+__device__ void staged_up(const LzLevel &F, const LzLevel &C, double2 *sm, int bid, int nblk,
+                          bool norm, double *norm_sum) {
+    const int n = F.n, nc = C.n;
+    int TX, TY;
+    lz_tile(n, nblk, TX, TY);
+    const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
+    for (int tile = bid; tile < ntx * nty; tile += nblk) {
+        const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
+        const Reg g = make_reg(tx0, ty0, TX, TY, 2 * kNu + (norm ? 1 : 0), n);
+        const LzSmem t = lz_layout(sm, g.R);
+        stage(F, g, t, F.r);
+        for (int q = threadIdx.x; q < g.R; q += blockDim.x) {
+            const int r = q / g.RX, i = g.ox + (q - r * g.RX), j = g.oy + r;
+            if (i < 0 || i >= n || j < 0 || j >= n) continue;
+            const int I = i >> 1, J = j >> 1;
+            const int di = (i & 1) ? 1 : -1, dj = (j & 1) ? 1 : -1;
+            const double2 e = cadd(cadd(cscale(9.0 / 16.0, ghost_at(C.u, nc, I, J)),
+                                        cscale(3.0 / 16.0, ghost_at(C.u, nc, I + di, J))),
+                                   cadd(cscale(3.0 / 16.0, ghost_at(C.u, nc, I, J + dj)),
+                                        cscale(1.0 / 16.0, ghost_at(C.u, nc, I + di, J + dj))));
+            t.u[q] = cadd(t.u[q], e);
+        }
+        __syncthreads();
+        staged_sweeps(g, n, F.ih2, t, 2 * kNu);
+        for (int q = threadIdx.x; q < TX * TY; q += blockDim.x) {
+            const int r = q / TX, x = tx0 + (q - r * TX), y = ty0 + r;
+            if (x >= n || y >= n) continue;
+            const int li = (y - g.oy) * g.RX + (x - g.ox);
+            F.u[y * n + x] = t.u[li];
+            if (norm) *norm_sum += cabs2(csub(t.f[li], staged_apply(t, g.RX, n, F.ih2, li, x, y)));
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The coarse part (levels of side <= kLocalN) in every block's own shared
+// memory, redundantly: no block waits for block 0 at a grid barrier, and the
+// up leg of the first staged level prolongs from the block's own copy.  The
+// coarsest level (up to kMaxExact unknowns) is solved with its exact
+// inverse, formed once per slice by complex Gauss-Jordan elimination (no
+// pivoting: -A has a positive definite Hermitian part, the 5-point -lap
+// plus kappa with Re kappa = chi + q >= 0); larger coarsest levels take
+// kCoarseSweeps red-black sweeps.
+// ---------------------------------------------------------------------------
+constexpr int kMaxExact = 16;
+constexpr int kCoarseCells = 128;  // room for the levels of side <= kLocalN
+constexpr size_t kCoarseBytes =
+    (size_t)5 * kCoarseCells * sizeof(double2) + (size_t)kMaxExact * 2 * kMaxExact * sizeof(double2);
+
+// the shared-memory hierarchy of levels loc .. Lc (pointers into sm)
+__device__ void coarse_levels(const LzArgs &A, int loc, int Lc, double2 *sm, LzLevel *S) {
+    double2 *p = sm;
+    for (int l = loc; l <= Lc; ++l) {
+        const int m = A.lv[l].n * A.lv[l].n;
+        S[l].n = A.lv[l].n;
+        S[l].ih2 = A.lv[l].ih2;
+        S[l].u = p;
+        S[l].f = p + m;
+        S[l].r = p + 2 * m;
+        S[l].kap = p + 3 * m;
+        S[l].idg = p + 4 * m;
+        p += 5 * m;
+    }
+}
+
+// [A | I] -> [I | A^{-1}] for the coarsest operator A = lap - kappa
+// (m = n^2 unknowns) in work (m x 2m, row-major): the inverse is the right
+// half, work[i * 2m + m + j]
+__device__ void coarse_inverse(const LzLevel &C, double2 *work) {
+    const int n = C.n, m = n * n, W = 2 * m;
+    __shared__ double2 s_piv;
+    __shared__ double2 fac[kMaxExact];
+    for (int e = threadIdx.x; e < m * W; e += blockDim.x) {
+        const int i = e / W, j = e - i * W;
+        double2 v = make_double2(0.0, 0.0);
+        if (j >= m) {
+            if (j - m == i) v.x = 1.0;
+        } else {
+            const int ix = i % n, iy = i / n, jx = j % n, jy = j / n;
+            if (i == j) {
+                const int w = (ix == 0) + (ix == n - 1) + (iy == 0) + (iy == n - 1);
+                v = make_double2(-(4.0 + w) * C.ih2 - C.kap[i].x, -C.kap[i].y);
+            } else if (abs(ix - jx) + abs(iy - jy) == 1) {
+                v.x = C.ih2;
+            }
+        }
+        work[e] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        if (threadIdx.x == 0) s_piv = cinv(work[k * W + k]);
+        __syncthreads();
+        const double2 piv = s_piv;
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            fac[i] = i == k ? make_double2(0.0, 0.0) : cmul(work[i * W + k], piv);
+        __syncthreads();
+        for (int e = threadIdx.x; e < m * (W - k); e += blockDim.x) {
+            const int i = e / (W - k), j = k + (e - i * (W - k));
+            if (i != k) work[i * W + j] = csub(work[i * W + j], cmul(fac[i], work[k * W + j]));
+        }
+        __syncthreads();
+        for (int j = k + threadIdx.x; j < W; j += blockDim.x) work[k * W + j] = cmul(work[k * W + j], piv);
+        __syncthreads();
+    }
+}
+
 template <typename Sync>
 __device__ bool down(const LzLevel *H, int from, int to, Team tm, const Sync &sync) {
     for (int l = from; l < to; ++l) {
@@ -216,6 +499,7 @@ __device__ bool up(const LzLevel *H, int from, int to, Team tm, const Sync &sync
 }
 
 __global__ void __launch_bounds__(kThreads, 1) laser_kernel(const __grid_constant__ LzArgs P) {
+    extern __shared__ double2 lz_dyn[];  // the staged regions
     __shared__ LzArgs A;
     __shared__ unsigned long long epoch;
     if (threadIdx.x == 0) {
@@ -225,11 +509,22 @@ __global__ void __launch_bounds__(kThreads, 1) laser_kernel(const __grid_constan
     __syncthreads();
     LzScalars *sc = A.sc;
     const qsync::GridBarrier<LzScalars> gsync{sc, &epoch, kBarrierLimit};
-    const Team grid{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x)};
+    const Team grid = qsync::spread_team();
     const Team blk{(int)threadIdx.x, (int)blockDim.x};
     const int n = A.n, nn = n * n, Lc = A.levels - 1;
-    int loc = 0;  // first level run by block 0 alone
+    int loc = 0;  // first level of the coarse part
     while (loc < Lc && A.lv[loc].n > kLocalN) ++loc;
+    // the coarse part's levels in shared memory, after the staged regions
+    // (used when loc > 0; the host checks that they fit)
+    __shared__ LzLevel S[kMaxLevels];
+    double2 *const csm = lz_dyn + lz_smem_bytes() / sizeof(double2);
+    const bool exact = A.lv[Lc].n * A.lv[Lc].n <= kMaxExact;
+    double2 *const cwork = csm + 5 * kCoarseCells;  // [I | A^{-1}] of the coarsest level
+    int coarse_cells = 0;
+    for (int l = loc; l <= Lc; ++l) coarse_cells += A.lv[l].n * A.lv[l].n;
+    const bool local = loc > 0 && coarse_cells <= kCoarseCells;
+    if (threadIdx.x == 0 && local) coarse_levels(A, loc, Lc, csm, S);
+    __syncthreads();
     long long kglob = 0;  // residual-norm computations so far (slot kglob % 3)
     long long g = 0;      // slices so far
 
@@ -278,9 +573,10 @@ __global__ void __launch_bounds__(kThreads, 1) laser_kernel(const __grid_constan
                     __syncthreads();
                 }
             }
-            // initial residual, then V-cycles until converged
+            // initial residual, then V-cycles until converged; each cycle's
+            // level-0 up leg sums the residual of its result
             int cyc = 0;
-            for (;;) {
+            {
                 double rn = 0.0;
                 if (blockIdx.x == 0 && threadIdx.x == 0) sc->norm[(kglob + 1) % 3] = 0.0;
                 for (int p = grid.t; p < nn; p += grid.nt) {
@@ -289,6 +585,8 @@ __global__ void __launch_bounds__(kThreads, 1) laser_kernel(const __grid_constan
                 }
                 qsync::block_sum_add<kThreads>(&rn, 1, &sc->norm[kglob % 3]);
                 if (!gsync(4)) return;
+            }
+            for (;;) {
                 const double r2 = qsync::vload(&sc->norm[kglob % 3]);
                 const double f2 = qsync::vload(&sc->fnorm[g % 3]);
                 ++kglob;
@@ -303,23 +601,79 @@ __global__ void __launch_bounds__(kThreads, 1) laser_kernel(const __grid_constan
                     break;
                 }
                 ++cyc;
-                if (Lc == 0) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) sc->norm[(kglob + 1) % 3] = 0.0;
+                double rn = 0.0;
+                if (loc == 0) {  // a grid this small: block 0 alone, then the residual
                     if (blockIdx.x == 0) {
                         const BlockSync bs;
-                        smooth(A.lv[0], kCoarseSweeps, blk, bs, 5);
+                        if (Lc == 0) {
+                            smooth(A.lv[0], kCoarseSweeps, blk, bs, 5);
+                        } else {
+                            down(A.lv, 0, Lc, blk, bs);
+                            smooth(A.lv[Lc], kCoarseSweeps, blk, bs, 5);
+                            up(A.lv, Lc - 1, 0, blk, bs);
+                        }
                     }
                     if (!gsync(3)) return;
-                    continue;
+                    for (int p = grid.t; p < nn; p += grid.nt) {
+                        const int jj = p / n, i = p - jj * n;
+                        rn += cabs2(csub(L0.f[p], apply_at(L0, U, i, jj)));
+                    }
+                } else {
+                    for (int l = 0; l < loc; ++l) {
+                        staged_down(A.lv[l], A.lv[l + 1], l == 0, lz_dyn, blockIdx.x, gridDim.x);
+                        if (!gsync(10 + l)) return;
+                    }
+                    if (!local) {  // block 0 in global memory
+                        if (blockIdx.x == 0) {
+                            const BlockSync bs;
+                            down(A.lv, loc, Lc, blk, bs);
+                            smooth(A.lv[Lc], kCoarseSweeps, blk, bs, 5);
+                            up(A.lv, Lc - 1, loc, blk, bs);
+                        }
+                        if (!gsync(3)) return;
+                    } else {  // the coarse part, redundantly in every block's shared memory
+                        const BlockSync bs;
+                        const LzLevel &G = A.lv[loc];
+                        const int m0 = G.n * G.n;
+                        for (int p = threadIdx.x; p < m0; p += blockDim.x) {
+                            cp16(S[loc].f + p, G.f + p, true);
+                            S[loc].u[p] = make_double2(0.0, 0.0);
+                        }
+                        if (cyc == 1) {  // kappa and 1/diag change once per slice
+                            for (int l = loc; l <= Lc; ++l)
+                                for (int p = threadIdx.x; p < S[l].n * S[l].n; p += blockDim.x) {
+                                    cp16(S[l].kap + p, A.lv[l].kap + p, true);
+                                    cp16(S[l].idg + p, A.lv[l].idg + p, true);
+                                }
+                        }
+                        cp_wait();
+                        __syncthreads();
+                        if (cyc == 1 && exact) coarse_inverse(S[Lc], cwork);
+                        down(S, loc, Lc, blk, bs);
+                        if (exact) {
+                            const int mc = S[Lc].n * S[Lc].n;
+                            const double2 *inv = cwork + mc;  // row i at inv + 2 mc i
+                            for (int i = threadIdx.x; i < mc; i += blockDim.x) {
+                                double2 s = make_double2(0.0, 0.0);
+                                for (int k = 0; k < mc; ++k)
+                                    s = cadd(s, cmul(inv[2 * mc * i + k], S[Lc].f[k]));
+                                S[Lc].u[i] = s;
+                            }
+                            __syncthreads();
+                        } else {
+                            smooth(S[Lc], kCoarseSweeps, blk, bs, 5);
+                        }
+                        up(S, Lc - 1, loc, blk, bs);
+                    }
+                    for (int l = loc - 1; l >= 0; --l) {
+                        staged_up(A.lv[l], (local && l + 1 == loc) ? S[loc] : A.lv[l + 1], lz_dyn,
+                                  blockIdx.x, gridDim.x, l == 0, &rn);
+                        if (l > 0 && !gsync(30 + l)) return;
+                    }
                 }
-                if (!down(A.lv, 0, loc, grid, gsync)) return;
-                if (blockIdx.x == 0) {
-                    const BlockSync bs;
-                    down(A.lv, loc, Lc, blk, bs);
-                    smooth(A.lv[Lc], kCoarseSweeps, blk, bs, 5);
-                    up(A.lv, Lc - 1, loc, blk, bs);
-                }
-                if (!gsync(3)) return;
-                if (loc > 0 && !up(A.lv, loc - 1, 0, grid, gsync)) return;
+                qsync::block_sum_add<kThreads>(&rn, 1, &sc->norm[kglob % 3]);
+                if (!gsync(4)) return;
             }
         }
         // the last slice's new envelope
@@ -415,7 +769,12 @@ extern "C" int qs_laser_create(int n, double width, int n_xi, double k0, double 
     st = cuda_status(cudaGetDevice(&dev));
     if (st == QS_OK) st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (st == QS_OK)
-        st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, laser_kernel, kThreads, 0));
+        st = cuda_status(cudaFuncSetAttribute((const void *)laser_kernel,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(lz_smem_bytes() + kCoarseBytes)));
+    if (st == QS_OK)
+        st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, laser_kernel, kThreads,
+                                                                       lz_smem_bytes() + kCoarseBytes));
     if (st == QS_OK && per_sm < 1) st = QS_ERR_CUDA;
     if (st != QS_OK) {
         qs_laser_destroy(s);
@@ -444,7 +803,8 @@ extern "C" int qs_laser_advance(qs_laser *s, const double *d_chi, double *d_a, i
     if (st != QS_OK) return st;
     void *params[] = {&A};
     st = cuda_status(cudaLaunchCooperativeKernel((const void *)laser_kernel, dim3(s->grid_blocks),
-                                                 dim3(kThreads), params, 0, s->stream));
+                                                 dim3(kThreads), params,
+                                                 lz_smem_bytes() + kCoarseBytes, s->stream));
     if (st != QS_OK) return st;
     st = cuda_status(cudaMemcpyAsync(s->pinned, A.sc, sizeof(LzScalars), cudaMemcpyDeviceToHost,
                                      s->stream));

@@ -765,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, 1) nu_solve_kernel(const __grid_cons
     }
     __syncthreads();
     const GridBarrier gsync{A.sc, &epoch, kBarrierLimit};
-    const Team grid{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x)};
+    const Team grid = qsync::spread_team();
     const Team blk{(int)threadIdx.x, (int)blockDim.x};
     NuScalars *sc = A.sc;
     const Level<T> *H = hier<T>(A);

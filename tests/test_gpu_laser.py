@@ -32,8 +32,13 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("n,n_xi,dxi", [(32, 8, 0.2), (48, 5, 0.1), (64, 3, math.inf),
-                                        (16, 12, 0.05)])
+                                        (16, 12, 0.05), (34, 4, 0.2), (40, 4, 0.1)])
 def test_advance_matches_oracle(qs, n, n_xi, dxi):
+    """Sizes cover each form of the coarse part: staged levels above 8 with
+    the levels of side <= 8 in every block's shared memory and an exact
+    coarsest inverse (32, 48, 64, 16), a 5^2 coarsest level too large for
+    the inverse (40: sweeps), a 17^2 coarsest level too large for shared
+    memory (34: block 0 in global memory)."""
     width = 8.0
     g = Grid.square(n, width / 2)
     rng = np.random.default_rng(n)
