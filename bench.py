@@ -230,7 +230,18 @@ def measured_traffic(kernel: str, workload: str, form: str, profiles_dir: str = 
 
 
 # ---------------------------------------------------------------- roofline model
-def algorithmic_bytes(stats, wl, form: str, n_xi: int) -> float:
+def cycle_sweeps(form: str, over=None) -> int:
+    """Red-black sweeps per level and V-cycle (pre + post) of a context made
+    with these overrides: pre_sweeps -1 is the library's default for the form
+    (3 refined, 2 float64), post_sweeps defaults to 2."""
+    over = over or {}
+    pre = over.get("pre_sweeps", -1)
+    if pre < 0:
+        pre = 3 if form == "fp32r" else 2
+    return pre + over.get("post_sweeps", 2)
+
+
+def algorithmic_bytes(stats, wl, form: str, n_xi: int, sweeps: int = None) -> float:
     """Bytes one slice-engine launch must move at minimum (the byte model).
 
     b = 8 (float64 form) or 4 (refined form: float32 momenta, weights, moment
@@ -244,7 +255,11 @@ def algorithmic_bytes(stats, wl, form: str, n_xi: int) -> float:
         grids (clears, deposits, reads in the assembly: b) and 29 float64
         (sources, fields, gradients, kappa, guesses); per base slice the
         history store 10 float64 words per point;
-      multigrid, per V-cycle and component: 24b per point, plus 8b per point
+      multigrid, per V-cycle and component, with nu sweeps per level (pre +
+        post): the fine level 3 nu b (read u, f, write u) + 4.5b (residual and
+        restriction 2.25b, prolongation and correction 2.25b) + 2b (residual
+        norm), the coarse levels a third of the fine level's 3 nu b + 4.5b
+        (24b for nu = 4, 28b for nu = 5), plus 8b per point
         for kappa in a screened cycle; the refined form adds its float64
         outer residual and correction, 40 B per point and component (read u,
         r, write u, r, float32 r), and 32 B per point and component for the
@@ -257,7 +272,9 @@ def algorithmic_bytes(stats, wl, form: str, n_xi: int) -> float:
     grid = ((21 * b + 29 * 8) * slices + 10 * 8 * n_xi) * nn
     v = stats["vcycles"]
     comp_cycles = v[0] + 2 * v[1] + 2 * v[2]
-    mg = (comp_cycles * 24 * b + v[2] * 8 * b) * nn
+    nu = sweeps if sweeps is not None else cycle_sweeps(form)
+    fine = 3 * nu * b + 4.5 * b
+    mg = (comp_cycles * (fine + 2 * b + fine / 3) + v[2] * 8 * b) * nn
     if form != "fp64":
         mg += (comp_cycles * 40 + 5 * slices * 32) * nn
     return float(part + grid + mg)
@@ -589,8 +606,8 @@ def run_batched(args):
                  for wl in insts]
     t0 = time.perf_counter()
     tuned = AT.tune(insts, precision="fp32r", n_slices=16,
-                    cands=AT.candidates(tiles=((32, 16), (64, 32)), sweeps=((2, 2), (2, 1)),
-                                        coarse=(16, 32)))
+                    cands=AT.candidates(tiles=((32, 16), (64, 32)),
+                                        sweeps=((3, 2), (2, 2), (2, 1)), coarse=(16, 32)))
     team = AT.tune_team(insts, tuned, precision="fp32r", n_slices=16)
     tune_s = time.perf_counter() - t0
     beams_np = [[W.sample_beam(b) for b in wl.beams] for wl in insts]
@@ -639,7 +656,8 @@ def run_batched(args):
         for s_, wl in zip(st, insts):
             slices += s_["slices"]
             pushes += s_["pushes"]
-            bytes_alg += algorithmic_bytes(s_, wl, "fp32r", wl.n_xi)
+            bytes_alg += algorithmic_bytes(s_, wl, "fp32r", wl.n_xi,
+                                           sweeps=cycle_sweeps("fp32r", AT.apply(wl, tuned)))
     clocks = sampler.stop()
     total_ms = max_over_ranks(sum(times), dev)
     # end to end: beams from pinned host memory each step, read back after

@@ -88,6 +88,8 @@ typedef struct {
                                 /* store checkpoints for the adjoint); 0 = the  */
                                 /* lattice order throughout                     */
     int pre_sweeps, post_sweeps;/* red-black Gauss-Seidel sweeps per level      */
+                                /* (0 .. 8, not both 0); pre_sweeps -1 = the    */
+                                /* form's default (3 refined, 2 QS_FP64)        */
     int coarse_block_n;         /* multigrid levels of side <= this are relaxed  */
                                 /* by one thread block in shared memory;         */
                                 /* 0 = default (16 for QS_FP64, 32 for refined) */

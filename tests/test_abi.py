@@ -45,7 +45,7 @@ def test_default_config_through_the_abi(lib):
     assert cfg.nx == 64 and cfg.ny == 64 and cfg.refine_k == 8 and cfg.mg_tol == 1e-10
     assert cfg.x_min == -6.0 and cfg.xi_max == 12.0 and cfg.n_xi == 128
     assert cfg.max_psi_guard_hits == -1 and cfg.sort_every == 16
-    assert cfg.pre_sweeps == 2 and cfg.post_sweeps == 2 and cfg.coarse_block_n == 0
+    assert cfg.pre_sweeps == -1 and cfg.post_sweeps == 2 and cfg.coarse_block_n == 0
     assert cfg.trace_capacity == 0 and cfg.warm_start_order == 2
     assert cfg.tile_x == 0 and cfg.tile_y == 0 and cfg.checkpoint_every == 0
     assert cfg.omega_pct == 0 and cfg.coarse_pre_sweeps == 1
@@ -66,7 +66,9 @@ def test_invalid_config_rejected_without_gpu(lib):
     h = ctypes.c_void_p()
     for bad in (dict(nx=64, ny=32), dict(nx=100, ny=100), dict(refine_k=0),
                 dict(precision=7), dict(mg_tol=0.0), dict(x_max=7.0), dict(tile_x=7, tile_y=8),
-                dict(warm_start_order=3), dict(omega_pct=40), dict(omega_pct=200), dict(coarse_pre_sweeps=9), dict(checkpoint_every=-1)):
+                dict(warm_start_order=3), dict(omega_pct=40), dict(omega_pct=200), dict(coarse_pre_sweeps=9), dict(checkpoint_every=-1),
+                dict(pre_sweeps=-2), dict(pre_sweeps=0, post_sweeps=0), dict(post_sweeps=9),
+                dict(deposit_band_rows=2), dict(deposit_band_rows=-2), dict(cluster_size=4)):
         cfg = qs.default_config(**bad)
         assert l.qs_create(ctypes.byref(cfg), None, ctypes.byref(h)) == qs.QS_ERR_ARG, bad
     assert l.qs_create(None, None, ctypes.byref(h)) == qs.QS_ERR_ARG
