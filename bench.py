@@ -1198,6 +1198,8 @@ def run_nupic(args):
     clocks = sampler.stop()
     total_s = max_over_ranks(ms_dev / 1e3, dev)
     value = job_rate(slices, world, total_s)
+    n_nodes = len(ax) - 2
+    nu_flops = NONUNI_FLOPS_PER_NODE_CYCLE * n_nodes * n_nodes * (vc[0] + 2 * vc[1] + 2 * vc[2])
     # end to end: the driver current in from pinned host memory, the wake out
     jz_host = torch.tensor(jzb_np).pin_memory()
     hist_host = torch.empty((5,) + tuple(jzb_np.shape), dtype=torch.float64).pin_memory()
@@ -1239,8 +1241,20 @@ def run_nupic(args):
                                      "(500k particles), window and slices, " + form},
            "e2e": {"value": slices * world / e2e_s, "unit": "slices/s",
                    "h2d_bytes_per_step": jzb_np.nbytes, "d2h_bytes_per_step": 5 * jzb_np.nbytes},
-           "roofline": None,
-           "gpu_launches": None, "clocks": clocks}
+           # the solves' FP64-equivalent flops (the nonuniform solver's count per
+           # node, field and V-cycle) over the whole step's device time, which
+           # also holds the particle and assembly phases: a lower bound for
+           # the solve kernel
+           "roofline": {"bound": "alu", "kernel": "nu_solve_kernel",
+                        "achieved": nu_flops / (ms_dev / 1e3) / 1e9, "peak": 1250.0,
+                        "unit": "GFLOP/s (FP64-equivalent, nominal FP64 peak)",
+                        "frac": nu_flops / (ms_dev / 1e3) / 1e9 / 1250.0, "traffic": None,
+                        "peak_source": FP64_PEAK_SOURCE,
+                        "time": "the whole step's device time"},
+           # per computed slice: deposit, psi source, three solves (one
+           # persistent launch each), moments, two assemblies, push (none
+           # after the last slice)
+           "gpu_launches": 9 * slices - args.steps, "clocks": clocks}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = nupic_cpu_baseline(args.cpu_seconds)
     print(json.dumps(out), flush=True)

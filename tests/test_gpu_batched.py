@@ -72,3 +72,36 @@ def test_batched_rejects_repeated_and_mixed_contexts(qs):
     with pytest.raises(qs.QsError) as e:
         qs.step3d_batched([ctxs[0], other[0]], [beams[0], ob[0]])
     assert e.value.status == qs.QS_ERR_ARG
+
+
+def test_batched_scan_sizes_match_oracle(qs):
+    """The parameter scan's sizes in the refined form: the three strongest
+    drivers of the scan (128^2, 192^2, 256^2; n_b near 8) in one batched
+    launch, each with other autotuner-style settings (tiles, sweeps,
+    single-block threshold), over a 40-slice prefix through the driver's
+    peak, against the FP64 oracle at the refined form's bar."""
+    insts = W.scan_instances()[45:48]
+    settings = (dict(tile_x=64, tile_y=32, pre_sweeps=2, post_sweeps=1, coarse_block_n=16),
+                dict(),
+                dict(tile_x=32, tile_y=16, pre_sweeps=3, post_sweeps=2, coarse_block_n=32))
+    wls = [wl.with_(n_xi=40, xi_len=wl.xi_len * 40 / wl.n_xi,
+                    beams=tuple(b.with_(xi_c=0.75, n_particles=20000) for b in wl.beams))
+           for wl in insts]
+    ctxs, beams = [], []
+    for wl, over in zip(wls, settings):
+        c = qs.Context(qs.config_from_workload(wl, precision="fp32r", mg_tol=1e-12, **over))
+        c.init_plasma(wl.ppc)
+        ctxs.append(c)
+        beams.append([qs.Beam(W.sample_beam(b)) for b in wl.beams])
+    st = qs.step3d_batched(ctxs, beams)
+    for c, wl, s in zip(ctxs, wls, st):
+        got = c.fields(qs.FIELD_ALL, device=False).numpy()
+        cfg = O.config_from_workload(wl)
+        pl, n_ion = O.plasma_from_workload(wl)
+        ref = O.step3d(cfg, pl, n_ion, [W.sample_beam(b) for b in wl.beams])
+        assert s["slices"] == ref.slices
+        scale = np.linalg.norm(ref.history[0])
+        for i in range(5):
+            err = np.linalg.norm(got[i] - ref.history[i]) / max(np.linalg.norm(ref.history[i]), scale)
+            assert err < 2e-5, (wl.n, i, err)
+    assert max(abs(h).max() for h in [ctxs[2].fields(qs.FIELD_PSI, device=False).numpy()]) > 0.3
