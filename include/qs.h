@@ -98,8 +98,8 @@ typedef struct {
     int warm_start_order;       /* initial guess of each solve: 0 = previous    */
                                 /* slice's solution (Sec. 7.1); 1, 2 = that     */
                                 /* history extrapolated in xi, linear/quadratic */
-    int tile_x, tile_y;         /* refined form: output tile of the grid-wide   */
-                                /* multigrid levels staged in shared memory;    */
+    int tile_x, tile_y;         /* output tile of the grid-wide multigrid      */
+                                /* levels staged in shared memory (both forms); */
                                 /* even, 0 = default 32 x 16                     */
     int omega_pct;              /* red-black smoother over-relaxation, percent: */
                                 /* u += omega (u_GS - u), omega = omega_pct/100 */

@@ -262,7 +262,13 @@ int create_impl(qs_ctx *c) {
             AL(L, c->lev[l].f[1], m);
             AL(L, c->lev[l].kap, m);
             AL(L, c->lev[l].d, m);
+            AL(L, c->lev[l].s[0], m);  // the staged down legs' pre-smoothed iterate
+            AL(L, c->lev[l].s[1], m);
         }
+    }
+    if (!ref) {  // level 0's scratch pair of the staged float64 cycle
+        AL(L, c->lev[0].s[0], nn);
+        AL(L, c->lev[0].s[1], nn);
     }
     if (ref)
         for (int k = 0; k < 5; ++k) AL(L, c->f32[k], nn);
@@ -298,8 +304,9 @@ int create_impl(qs_ctx *c) {
     CK(cudaMemsetAsync(c->hist, 0, 5 * (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
     CK(cudaMemsetAsync(c->jzb, 0, (size_t)g.n_xi * nn * sizeof(double), c->st), "memset");
     c->block_level_n = g.coarse_block_n > 0 ? g.coarse_block_n : (ref ? 32 : 16);
-    c->tile_x = ref ? (g.tile_x > 0 ? g.tile_x : 32) : 0;
-    c->tile_y = ref ? (g.tile_y > 0 ? g.tile_y : 16) : 0;
+    // staged grid levels in both forms (32 x 16 output tiles by default)
+    c->tile_x = g.tile_x > 0 ? g.tile_x : 32;
+    c->tile_y = g.tile_y > 0 ? g.tile_y : 16;
     const int nu = g.pre_sweeps > g.post_sweeps ? g.pre_sweeps : g.post_sweeps;
     c->engine_smem = qs_engine_smem_bytes(c->lev_n, c->nlev, c->block_level_n, g.precision,
                                           c->tile_x, c->tile_y, nu, g.post_sweeps,

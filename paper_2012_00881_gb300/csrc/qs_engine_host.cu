@@ -68,6 +68,8 @@ size_t qs_engine_smem_bytes(const int *lev_n, int nlev, int block_level_n, int p
     size_t total = inv + b;
     if (precision == QS_FP32_REFINED && tile_x > 0)
         total += qstile::tile_smem_bytes(tile_x, tile_y, nu, nu2);
+    else if (tile_x > 0)  // the float64 form's staged legs: six float64 arrays a region
+        total += qstile::tile64_smem_bytes(tile_x, tile_y, nu, nu2);
     return total + 256;
 }
 

@@ -51,6 +51,7 @@ struct LevelArrays {
     double *f[2];
     double *kap;
     double *d;
+    double *s[2];  // the staged down leg's pre-smoothed iterate (float64 form)
 };
 struct LevelArrays32 {
     float *u[2];   // pre-smoothed iterate (tiled down leg) / block-level result

@@ -371,8 +371,10 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
     for (int l = 0; l < lg; ++l) {
         int TX, TY;
         level_tile(A, H.lv[l].n, nblk, TX, TY);
-        qstile::down_level<NC>(H.lv[l], H.lv[l + 1], A.nu1, TX, TY, sm, bid,
-                               nblk, mk);
+        // the correction starts from zero; its pre-smoothed tile goes to
+        // the level's own array (the up cascade reads it there)
+        qstile::down_level<float, NC>(H.lv[l], H.lv[l + 1], A.nu1, TX, TY, sm, bid, nblk,
+                                      H.lv[l].u, nullptr, mk);
         mk(62);
         SYNC(30);
     }
@@ -398,6 +400,50 @@ __device__ bool vcycle_staged(const EngineArgs &A, const Sync &S, const Hier<flo
     mk(67);
     *fused_done = true;
     SYNC(32);
+    return true;
+}
+
+// Float64 form: one V-cycle with the grid-wide levels staged tile by tile
+// (qs_tile.cuh): a down leg per level (pre-sweeps from the iterate at level
+// 0, from zero below, residual, restriction; the pre-smoothed tile to the
+// level's scratch pair), the coarse levels by block 0, an up leg per level
+// (prolongation, post-sweeps) reading the scratch pair; the level-0 up leg
+// also sums ||f - A u||^2 and ||u||^2 of its tile into norms_out for the
+// stopping test.  One grid barrier per level and leg instead of one per
+// colour sweep, restriction and prolongation.
+template <int NC>
+__device__ bool vcycle_staged64(const EngineArgs &A, const Sync &S, const Hier<double> &H,
+                                int bid, int nblk, void *smem, qsmg::CoarseInv ci,
+                                double *norms_out, double *norms_clear) {
+    const int L = H.L;
+    int lg = 0;
+    while (lg < L - 1 && H.lv[lg].n > A.block_level_n) ++lg;
+    double *sm = (double *)((char *)smem + A.tile_smem_offset);
+    for (int l = 0; l < lg; ++l) {
+        int TX, TY;
+        level_tile(A, H.lv[l].n, nblk, TX, TY);
+        qstile::down_level<double, NC>(H.lv[l], H.lv[l + 1], A.nu1, TX, TY, sm, bid, nblk,
+                                       A.lev[l].s, l == 0 ? H.lv[0].u : nullptr);
+        SYNC(40);
+    }
+    if (bid == 0) qsmg::block_vcycle<double, NC>(H, lg, A.nu1c, A.nu2, smem, ci);
+    SYNC(41);
+    double nrm[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = lg - 1; l >= 0; --l) {
+        int TX, TY;
+        level_tile(A, H.lv[l].n, nblk, TX, TY);
+        qstile::up_level<double, NC>(H.lv[l], H.lv[l + 1], A.lev[l].s, A.nu2, TX, TY, sm, bid,
+                                     nblk, l == 0, nrm);
+        if (l > 0) SYNC(42);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double t = block_sum(nrm[k]);
+        if (threadIdx.x == 0 && (k & 1) < NC) atomicAdd(norms_out + k, t);
+    }
+    if (bid == 0 && threadIdx.x == 0)
+        for (int e = 0; e < 4; ++e) norms_clear[e] = 0.0;
+    SYNC(43);
     return true;
 }
 
@@ -957,6 +1003,11 @@ __device__ bool mg_solve(const EngineArgs &A, const Sync &S, const SolveSpec &V,
                          ? vcycle_staged<2>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[1], &fz,
                                             nout, nclr, &norms_ready)
                          : vcycle<float, 2>(A, S, H32, bid, nblk, smem, ci, V.u[0], V.u[1]);
+        } else if (A.tile_x > 0 && H64.lv[0].n > A.block_level_n) {
+            double *nout = sc->rnorm[slot & 3], *nclr = sc->rnorm[(slot + 2) & 3];
+            ok = V.nc == 1 ? vcycle_staged64<1>(A, S, H64, bid, nblk, smem, ci, nout, nclr)
+                           : vcycle_staged64<2>(A, S, H64, bid, nblk, smem, ci, nout, nclr);
+            norms_ready = true;  // the level-0 up leg summed the stopping test's norms
         } else {
             ok = V.nc == 1 ? vcycle<double, 1>(A, S, H64, bid, nblk, smem, ci, nullptr, nullptr)
                            : vcycle<double, 2>(A, S, H64, bid, nblk, smem, ci, nullptr, nullptr);

@@ -49,10 +49,10 @@ __device__ __forceinline__ Region make_region(int tx0, int ty0, int TX, int TY, 
 
 // Half sweeps 0 .. ns-1 on the staged region: a cell is updated in half
 // sweep s only if it is at least s + 1 cells from every cut side.
-template <int NC>
-__device__ void staged_sweeps(const Region &g, int n, float h2, float *const su0,
-                              float *const su1, const float *const sf0, const float *const sf1,
-                              const float *const sd, int ns, float omega) {
+template <int NC, typename T>
+__device__ void staged_sweeps(const Region &g, int n, T h2, T *const su0, T *const su1,
+                              const T *const sf0, const T *const sf1, const T *const sd, int ns,
+                              T omega) {
     // Half sweep s updates, within the in-domain part of the region, the
     // cells of its colour at least s + 1 cells from every cut side: a
     // rectangle shrinking by one cell per half sweep on the cut sides.  Only
@@ -69,17 +69,17 @@ __device__ void staged_sweeps(const Region &g, int n, float h2, float *const su0
             const int x = X0 + ((X0 + y + color) & 1) + 2 * w.col;
             if (x > X1) continue;
             const int li = (y - g.oy) * RX + (x - g.ox);
-            const float di = sd ? sd[li] : qsmg::const_inv_diag<float>(qsmg::walls(x, y, n));
+            const T di = sd ? sd[li] : qsmg::const_inv_diag<T>(qsmg::walls(x, y, n));
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                float *u = c ? su1 : su0;
-                float nb = 0.f;
+                T *u = c ? su1 : su0;
+                T nb = T(0);
                 if (x > 0) nb += u[li - 1];
                 if (x < n - 1) nb += u[li + 1];
                 if (y > 0) nb += u[li - RX];
                 if (y < n - 1) nb += u[li + RX];
-                const float gv = (nb - h2 * (c ? sf1 : sf0)[li]) * di;
-                const float uo = u[li];
+                const T gv = (nb - h2 * (c ? sf1 : sf0)[li]) * di;
+                const T uo = u[li];
                 u[li] = uo + omega * (gv - uo);
             }
         }
@@ -87,26 +87,29 @@ __device__ void staged_sweeps(const Region &g, int n, float h2, float *const su0
     }
 }
 
-__device__ __forceinline__ float staged_op(const float *u, const float *k, int RX, int n,
-                                           float inv_h2, int li, int x, int y) {
-    float nb = 0.f;
+template <typename T>
+__device__ __forceinline__ T staged_op(const T *u, const T *k, int RX, int n, T inv_h2, int li,
+                                       int x, int y) {
+    T nb = T(0);
     if (x > 0) nb += u[li - 1];
     if (x < n - 1) nb += u[li + 1];
     if (y > 0) nb += u[li - RX];
     if (y < n - 1) nb += u[li + RX];
-    float r = (nb - (float)(4 + qsmg::walls(x, y, n)) * u[li]) * inv_h2;
+    T r = (nb - (T)(4 + qsmg::walls(x, y, n)) * u[li]) * inv_h2;
     if (k) r -= k[li] * u[li];
     return r;
 }
 
 // Layout of a staged down-leg region in shared memory: six arrays (u0, u1,
 // f0, f1, kappa, inverse diagonal) of R cells.
+template <typename T>
 struct TileSmem {
-    float *su0, *su1, *sf0, *sf1, *sk, *sd;
+    T *su0, *su1, *sf0, *sf1, *sk, *sd;
 };
 
-__device__ __forceinline__ TileSmem tile_layout(float *sm, int R) {
-    TileSmem t;
+template <typename T>
+__device__ __forceinline__ TileSmem<T> tile_layout(T *sm, int R) {
+    TileSmem<T> t;
     t.su0 = sm;
     t.su1 = sm + R;
     t.sf0 = sm + 2 * R;
@@ -189,6 +192,23 @@ __host__ __device__ inline size_t tile_smem_bytes(int TX, int TY, int nu, int nu
     return best;
 }
 
+// Shared memory (bytes) of the float64 form's staged legs (down_level and
+// up_level with T = double) for tile TX x TY and its halvings down to 8: six
+// float64 arrays over the tile plus the larger halo (2 nu1 + 1 down,
+// 2 nu2 + 1 on the level-0 up leg).
+__host__ __device__ inline size_t tile64_smem_bytes(int TX, int TY, int nu, int nu2) {
+    size_t best = 0;
+    const int H = 2 * (nu > nu2 ? nu : nu2) + 1;
+    for (int tx = TX, ty = TY;;) {
+        const size_t a = (size_t)6 * (tx + 2 * H) * (ty + 2 * H) * sizeof(double);
+        best = best > a ? best : a;
+        if (tx >= ty && tx > 8) tx >>= 1;
+        else if (ty > 8) ty >>= 1;
+        else break;
+    }
+    return best;
+}
+
 // Bilinear cell-centred interpolation (odd ghosts) of a coarse array of side
 // m held as a window with origin (cox, coy) and row pitch cp; the same
 // weights as qsmg::bilinear.
@@ -211,49 +231,61 @@ __device__ __forceinline__ float bilinear_win(const float *cs, int cox, int coy,
     return (9.f * v00 + 3.f * v10 + 3.f * v01 + v11) * 0.0625f;
 }
 
+__device__ __forceinline__ void cp_async_t(float *dst, const float *src, bool valid) {
+    cp_async_f32(dst, src, valid);
+}
+__device__ __forceinline__ void cp_async_t(double *dst, const double *src, bool valid) {
+    cp_async_f64(dst, src, valid);
+}
+
 // Down leg of grid level F -> coarse C for every tile owned by this block:
-// pre-smoothing from a zero iterate, residual, 4-cell restriction (and kappa,
-// inverse diagonal); the pre-smoothed tile is written to F.u.
-template <int NC>
-__device__ void down_level(const Lvl<float> F, const Lvl<float> C, int nu1, int TX, int TY,
-                           float *sm, int bid, int nblk,
+// pre-smoothing from u_in (nullptr: a zero iterate), residual, 4-cell
+// restriction (and kappa, inverse diagonal; the coarse level starts from
+// zero where it is solved); the pre-smoothed tile is written to u_out.
+// u_out must not be u_in: neighbours still stage u_in around their tiles
+// during the leg.
+template <typename T, int NC>
+__device__ void down_level(const Lvl<T> F, const Lvl<T> C, int nu1, int TX, int TY, T *sm,
+                           int bid, int nblk, T *const *u_out, const T *const *u_in = nullptr,
                            qsmg::Marks mark = qsmg::Marks{nullptr, nullptr, 0}) {
     const int n = F.n, m = C.n;
     const int H = 2 * nu1 + 1;
     const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
-    const float h2 = F.h2t, inv_h2 = F.inv_h2t, ch2 = C.h2t;
+    const T h2 = F.h2t, inv_h2 = F.inv_h2t, ch2 = C.h2t;
     const bool scr = F.k != nullptr;
-    const float *const gf0 = F.f[0];
-    const float *const gf1 = F.f[NC - 1];
+    const T *const gf0 = F.f[0];
+    const T *const gf1 = F.f[NC - 1];
     for (int tile = bid; tile < ntx * nty; tile += nblk) {
         const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
         const Region g = make_region(tx0, ty0, TX, TY, H, n);
-        const TileSmem t = tile_layout(sm, g.R);
-        float *const su0 = t.su0;
-        float *const su1 = t.su1;
-        float *const sf0 = t.sf0;
-        float *const sf1 = t.sf1;
-        float *const sk = scr ? t.sk : nullptr;
-        float *const sd = scr ? t.sd : nullptr;
+        const TileSmem<T> t = tile_layout(sm, g.R);
+        T *const su0 = t.su0;
+        T *const su1 = t.su1;
+        T *const sf0 = t.sf0;
+        T *const sf1 = t.sf1;
+        T *const sk = scr ? t.sk : nullptr;
+        T *const sd = scr ? t.sd : nullptr;
         for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
             const int x = g.ox + w.col, y = g.oy + w.row;
             const bool in = x >= 0 && x < n && y >= 0 && y < n;
             const int gi = in ? y * n + x : 0, li = w.q;
-            su0[li] = 0.f;
-            cp_async_f32(sf0 + li, gf0 + gi, in);
+            if (u_in) cp_async_t(su0 + li, u_in[0] + gi, in);
+            else su0[li] = T(0);
+            cp_async_t(sf0 + li, gf0 + gi, in);
             if (NC > 1) {
-                su1[li] = 0.f;
-                cp_async_f32(sf1 + li, gf1 + gi, in);
+                if (u_in) cp_async_t(su1 + li, u_in[1] + gi, in);
+                else su1[li] = T(0);
+                cp_async_t(sf1 + li, gf1 + gi, in);
             }
             if (scr) {
-                cp_async_f32(sk + li, F.k + gi, in);
-                cp_async_f32(sd + li, F.d + gi, in);
+                cp_async_t(sk + li, F.k + gi, in);
+                cp_async_t(sd + li, F.d + gi, in);
             }
         }
         cp_async_wait_all();
         __syncthreads();
         mark(60);
-        staged_sweeps<NC>(g, n, h2, su0, su1, sf0, sf1, sd, 2 * nu1, F.omega);
+        staged_sweeps<NC, T>(g, n, h2, su0, su1, sf0, sf1, sd, 2 * nu1, F.omega);
         mark(61);
         // residual on the tile, restricted to the coarse cells it covers
         const int CTX = TX / 2, CTY = TY / 2, cx0 = tx0 / 2, cy0 = ty0 / 2;
@@ -265,26 +297,90 @@ __device__ void down_level(const Lvl<float> F, const Lvl<float> C, int nu1, int 
             const int RX = g.RX;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                const float *su = c ? su1 : su0;
-                const float *sf = c ? sf1 : sf0;
-                float s = sf[l0] - staged_op(su, sk, RX, n, inv_h2, l0, x0, y0);
-                s += sf[l0 + 1] - staged_op(su, sk, RX, n, inv_h2, l0 + 1, x0 + 1, y0);
-                s += sf[l0 + RX] - staged_op(su, sk, RX, n, inv_h2, l0 + RX, x0, y0 + 1);
-                s += sf[l0 + RX + 1] - staged_op(su, sk, RX, n, inv_h2, l0 + RX + 1, x0 + 1, y0 + 1);
-                C.f[c][J * m + I] = 0.25f * s;
+                const T *su = c ? su1 : su0;
+                const T *sf = c ? sf1 : sf0;
+                T s = sf[l0] - staged_op<T>(su, sk, RX, n, inv_h2, l0, x0, y0);
+                s += sf[l0 + 1] - staged_op<T>(su, sk, RX, n, inv_h2, l0 + 1, x0 + 1, y0);
+                s += sf[l0 + RX] - staged_op<T>(su, sk, RX, n, inv_h2, l0 + RX, x0, y0 + 1);
+                s += sf[l0 + RX + 1] - staged_op<T>(su, sk, RX, n, inv_h2, l0 + RX + 1, x0 + 1, y0 + 1);
+                C.f[c][J * m + I] = T(0.25) * s;
             }
             if (scr) {
-                const float kk = 0.25f * (sk[l0] + sk[l0 + 1] + sk[l0 + RX] + sk[l0 + RX + 1]);
+                const T kk = T(0.25) * (sk[l0] + sk[l0 + 1] + sk[l0 + RX] + sk[l0 + RX + 1]);
                 C.k[J * m + I] = kk;
-                C.d[J * m + I] = 1.f / ((float)(4 + qsmg::walls(I, J, m)) + ch2 * kk);
+                C.d[J * m + I] = T(1) / ((T)(4 + qsmg::walls(I, J, m)) + ch2 * kk);
             }
         }
         for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
             const int x = tx0 + w.col, y = ty0 + w.row;
             if (x >= n || y >= n) continue;
             const int li = (y - g.oy) * g.RX + (x - g.ox);
-            F.u[0][y * n + x] = su0[li];
-            if (NC > 1) F.u[1][y * n + x] = su1[li];
+            u_out[0][y * n + x] = su0[li];
+            if (NC > 1) u_out[1][y * n + x] = su1[li];
+        }
+        __syncthreads();
+    }
+}
+
+// Up leg of grid level F for every tile owned by this block (the float64
+// form's cycle): the pre-smoothed iterate s_in (the down leg's u_out) plus
+// the bilinear prolongation of the coarse correction C.u, post-sweeps, the
+// tile written to F.u.  With `norm` (level 0) the halo is one cell wider
+// and the thread's sums of |f - A u|^2 and u^2 per component go to
+// norms[0 .. 3].
+template <typename T, int NC>
+__device__ void up_level(const Lvl<T> F, const Lvl<T> C, const T *const *s_in, int nu2, int TX,
+                         int TY, T *sm, int bid, int nblk, bool norm, double norms[4]) {
+    const int n = F.n, m = C.n;
+    const int H = 2 * nu2 + (norm ? 1 : 0);
+    const int ntx = (n + TX - 1) / TX, nty = (n + TY - 1) / TY;
+    const bool scr = F.k != nullptr;
+    for (int tile = bid; tile < ntx * nty; tile += nblk) {
+        const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
+        const Region g = make_region(tx0, ty0, TX, TY, H, n);
+        const TileSmem<T> t = tile_layout(sm, g.R);
+        T *const sk = scr ? t.sk : nullptr;
+        T *const sd = scr ? t.sd : nullptr;
+        for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
+            const int x = g.ox + w.col, y = g.oy + w.row;
+            const bool in = x >= 0 && x < n && y >= 0 && y < n;
+            const int gi = in ? y * n + x : 0, li = w.q;
+            cp_async_t(t.su0 + li, s_in[0] + gi, in);
+            cp_async_t(t.sf0 + li, F.f[0] + gi, in);
+            if (NC > 1) {
+                cp_async_t(t.su1 + li, s_in[1] + gi, in);
+                cp_async_t(t.sf1 + li, F.f[1] + gi, in);
+            }
+            if (scr) {
+                cp_async_t(sk + li, F.k + gi, in);
+                cp_async_t(sd + li, F.d + gi, in);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
+            const int x = g.ox + w.col, y = g.oy + w.row;
+            if (x < 0 || x >= n || y < 0 || y >= n) continue;
+            t.su0[w.q] += qsmg::bilinear(C.u[0], m, x, y);
+            if (NC > 1) t.su1[w.q] += qsmg::bilinear(C.u[1], m, x, y);
+        }
+        __syncthreads();
+        staged_sweeps<NC, T>(g, n, F.h2t, t.su0, t.su1, t.sf0, t.sf1, sd, 2 * nu2, F.omega);
+        for (Walk w(threadIdx.x, blockDim.x, TX); w.q < TX * TY; w.next()) {
+            const int x = tx0 + w.col, y = ty0 + w.row;
+            if (x >= n || y >= n) continue;
+            const int li = (y - g.oy) * g.RX + (x - g.ox);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const T *su = c ? t.su1 : t.su0;
+                F.u[c][y * n + x] = su[li];
+                if (norm) {
+                    const T r = (c ? t.sf1 : t.sf0)[li] -
+                                staged_op<T>(su, sk, g.RX, n, F.inv_h2t, li, x, y);
+                    norms[c] += (double)r * (double)r;
+                    norms[2 + c] += (double)su[li] * (double)su[li];
+                }
+            }
         }
         __syncthreads();
     }
@@ -412,7 +508,7 @@ __device__ void up_cascade_fused(const qsmg::Hier<float> &Hh, int lg, const floa
             const Region g = cascade_region(Hh, l, tx0, ty0, TX, TY, nu2);
             const CascadeSmem t = cascade_layout(sm, g.R, TX, TY, nu2);
             stage_cascade<NC>(F, g, t, src0, src1, sox, soy, sp, Hh.lv[l + 1].n);
-            staged_sweeps<NC>(g, F.n, F.h2t, t.su0, t.su1, t.sf0, t.sf1,
+            staged_sweeps<NC, float>(g, F.n, F.h2t, t.su0, t.su1, t.sf0, t.sf1,
                               F.d ? t.sd : nullptr, 2 * nu2, F.omega);
             // keep the window that the next finer region prolongs from
             const Region gf = cascade_region(Hh, l - 1, tx0, ty0, TX, TY, nu2);
@@ -452,7 +548,7 @@ __device__ void up_cascade_fused(const qsmg::Hier<float> &Hh, int lg, const floa
         }
         stage_cascade<NC>(F, g, t, src0, src1, sox, soy, sp, Hh.lv[1].n);
         mark(65);
-        staged_sweeps<NC>(g, n, F.h2t, t.su0, t.su1, t.sf0, t.sf1, F.d ? t.sd : nullptr,
+        staged_sweeps<NC, float>(g, n, F.h2t, t.su0, t.su1, t.sf0, t.sf1, F.d ? t.sd : nullptr,
                           2 * nu2, F.omega);
         mark(66);
         const int RX = g.RX;
