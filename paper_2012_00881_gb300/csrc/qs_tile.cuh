@@ -24,27 +24,65 @@ using qsmg::cp_async_f64;
 using qsmg::cp_async_wait_all;
 
 struct Region {
-    int ox, oy, RX, RY, R;   // staged region: origin and extent
-    int ax, bx, ay, by;      // its intersection with the domain
+    int ox, oy, RX, RY, R;   // staged storage: origin and extent (cell (x, y) at
+                             // (y - oy) RX + (x - ox))
+    int ax, bx, ay, by;      // the region's intersection with the domain
     bool cl, cr, cb, ct;     // which sides are cut (not the domain wall)
 };
 
-__device__ __forceinline__ Region make_region(int tx0, int ty0, int TX, int TY, int H, int n) {
+// Columns of padding a storage window may add to a region's width (V - 1 on
+// each side for vectors of V = 4 float32 values).
+constexpr int kAlignPad = 6;
+
+// The region of the tile at (tx0, ty0) with halo H on a level of side n.
+// Its storage starts at a column that is a multiple of V and has a width
+// that is a multiple of V, so that rows can be staged with 16-byte copies of
+// V = 16 / sizeof(element) values; the extra columns are never updated.
+__device__ __forceinline__ Region make_region(int tx0, int ty0, int TX, int TY, int H, int n,
+                                              int V = 1) {
     Region g;
-    g.ox = tx0 - H;
+    const int ox = tx0 - H;
     g.oy = ty0 - H;
-    g.RX = TX + 2 * H;
     g.RY = TY + 2 * H;
-    g.R = g.RX * g.RY;
-    g.ax = max(g.ox, 0);
-    g.bx = min(g.ox + g.RX - 1, n - 1);
+    g.ax = max(ox, 0);
+    g.bx = min(ox + TX + 2 * H - 1, n - 1);
     g.ay = max(g.oy, 0);
     g.by = min(g.oy + g.RY - 1, n - 1);
     g.cl = g.ax > 0;
     g.cr = g.bx < n - 1;
     g.cb = g.ay > 0;
     g.ct = g.by < n - 1;
+    g.ox = ox >= 0 ? ox - ox % V : -((-ox + V - 1) / V) * V;
+    const int end = ox + TX + 2 * H;  // one past the region's last column
+    g.RX = ((end - g.ox + V - 1) / V) * V;
+    g.R = g.RX * g.RY;
     return g;
+}
+
+// 16-byte global -> shared copy (zero-filled when !valid); both addresses
+// 16-byte aligned
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// Visit the storage of region g on a level of side n in groups of V cells
+// (V = 16 / sizeof(T)): f(li, gi, in) for the group's first cell, its
+// global index and whether the group lies in the domain.  With n a multiple
+// of V every group lies wholly inside or outside the domain (group origins
+// are multiples of V), so one 16-byte copy stages it.
+template <typename T, typename F>
+__device__ __forceinline__ void for_groups(const Region &g, int n, F f) {
+    constexpr int V = 16 / (int)sizeof(T);
+    const int gx = g.RX / V;
+    for (int q = threadIdx.x; q < g.RY * gx; q += blockDim.x) {
+        const int r = q / gx, c = q - r * gx;
+        const int x = g.ox + c * V, y = g.oy + r;
+        const bool in = x >= 0 && x < n && y >= 0 && y < n;
+        f(r * g.RX + c * V, in ? y * n + x : 0, in);
+    }
 }
 
 // Half sweeps 0 .. ns-1 on the staged region: a cell is updated in half
@@ -127,14 +165,14 @@ __device__ __forceinline__ TileSmem<T> tile_layout(T *sm, int R) {
 // levels bounds them.
 __host__ __device__ inline void cascade_bounds(int TX, int TY, int nu2, int &rbig, int &wbig) {
     int x = TX + 2 * (2 * nu2 + 1), y = TY + 2 * (2 * nu2 + 1);
-    rbig = x * y;
+    rbig = (x + kAlignPad) * y;  // storage may be kAlignPad columns wider
     wbig = 0;
     for (int l = 1; l < 16; ++l) {
         const int wx = x / 2 + 3, wy = y / 2 + 3;
         wbig = wbig > wx * wy ? wbig : wx * wy;
         x = wx + 4 * nu2;
         y = wy + 4 * nu2;
-        rbig = rbig > x * y ? rbig : x * y;
+        rbig = rbig > (x + kAlignPad) * y ? rbig : (x + kAlignPad) * y;
     }
 }
 
@@ -178,7 +216,7 @@ __host__ __device__ inline size_t tile_smem_bytes(int TX, int TY, int nu, int nu
     size_t best = 0;
     for (int tx = TX, ty = TY;;) {
         const int H = 2 * nu + 1;
-        const size_t a = (size_t)6 * (tx + 2 * H) * (ty + 2 * H) * sizeof(float);
+        const size_t a = (size_t)6 * (tx + 2 * H + kAlignPad) * (ty + 2 * H) * sizeof(float);
         int rbig, wbig;
         cascade_bounds(tx, ty, nu2, rbig, wbig);
         size_t b = ((size_t)(6 * rbig + 4 * wbig) * sizeof(float) + 15) & ~(size_t)15;
@@ -200,7 +238,7 @@ __host__ __device__ inline size_t tile64_smem_bytes(int TX, int TY, int nu, int 
     size_t best = 0;
     const int H = 2 * (nu > nu2 ? nu : nu2) + 1;
     for (int tx = TX, ty = TY;;) {
-        const size_t a = (size_t)6 * (tx + 2 * H) * (ty + 2 * H) * sizeof(double);
+        const size_t a = (size_t)6 * (tx + 2 * H + kAlignPad) * (ty + 2 * H) * sizeof(double);
         best = best > a ? best : a;
         if (tx >= ty && tx > 8) tx >>= 1;
         else if (ty > 8) ty >>= 1;
@@ -257,7 +295,8 @@ __device__ void down_level(const Lvl<T> F, const Lvl<T> C, int nu1, int TX, int 
     const T *const gf1 = F.f[NC - 1];
     for (int tile = bid; tile < ntx * nty; tile += nblk) {
         const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
-        const Region g = make_region(tx0, ty0, TX, TY, H, n);
+        constexpr int V = 16 / (int)sizeof(T);
+        const Region g = make_region(tx0, ty0, TX, TY, H, n, V);
         const TileSmem<T> t = tile_layout(sm, g.R);
         T *const su0 = t.su0;
         T *const su1 = t.su1;
@@ -265,7 +304,26 @@ __device__ void down_level(const Lvl<T> F, const Lvl<T> C, int nu1, int TX, int 
         T *const sf1 = t.sf1;
         T *const sk = scr ? t.sk : nullptr;
         T *const sd = scr ? t.sd : nullptr;
-        for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
+        if (n % V == 0) {  // whole rows in 16-byte copies
+            for_groups<T>(g, n, [&](int li, int gi, bool in) {
+                if (u_in) {
+                    cp_async16(su0 + li, u_in[0] + gi, in);
+                    if (NC > 1) cp_async16(su1 + li, u_in[1] + gi, in);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < V; ++k) {
+                        su0[li + k] = T(0);
+                        if (NC > 1) su1[li + k] = T(0);
+                    }
+                }
+                cp_async16(sf0 + li, gf0 + gi, in);
+                if (NC > 1) cp_async16(sf1 + li, gf1 + gi, in);
+                if (scr) {
+                    cp_async16(sk + li, F.k + gi, in);
+                    cp_async16(sd + li, F.d + gi, in);
+                }
+            });
+        } else for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
             const int x = g.ox + w.col, y = g.oy + w.row;
             const bool in = x >= 0 && x < n && y >= 0 && y < n;
             const int gi = in ? y * n + x : 0, li = w.q;
@@ -337,11 +395,25 @@ __device__ void up_level(const Lvl<T> F, const Lvl<T> C, const T *const *s_in, i
     const bool scr = F.k != nullptr;
     for (int tile = bid; tile < ntx * nty; tile += nblk) {
         const int tx0 = (tile % ntx) * TX, ty0 = (tile / ntx) * TY;
-        const Region g = make_region(tx0, ty0, TX, TY, H, n);
+        constexpr int V = 16 / (int)sizeof(T);
+        const Region g = make_region(tx0, ty0, TX, TY, H, n, V);
         const TileSmem<T> t = tile_layout(sm, g.R);
         T *const sk = scr ? t.sk : nullptr;
         T *const sd = scr ? t.sd : nullptr;
-        for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
+        if (n % V == 0) {  // whole rows in 16-byte copies
+            for_groups<T>(g, n, [&](int li, int gi, bool in) {
+                cp_async16(t.su0 + li, s_in[0] + gi, in);
+                cp_async16(t.sf0 + li, F.f[0] + gi, in);
+                if (NC > 1) {
+                    cp_async16(t.su1 + li, s_in[1] + gi, in);
+                    cp_async16(t.sf1 + li, F.f[1] + gi, in);
+                }
+                if (scr) {
+                    cp_async16(sk + li, F.k + gi, in);
+                    cp_async16(sd + li, F.d + gi, in);
+                }
+            });
+        } else for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
             const int x = g.ox + w.col, y = g.oy + w.row;
             const bool in = x >= 0 && x < n && y >= 0 && y < n;
             const int gi = in ? y * n + x : 0, li = w.q;
@@ -442,11 +514,11 @@ __device__ __forceinline__ void coarse_window(const Region &g, int m, int &wx0, 
 // region of cascade level l for the level-0 tile at (tx0, ty0)
 __device__ __forceinline__ Region cascade_region(const qsmg::Hier<float> &Hh, int l, int tx0,
                                                  int ty0, int TX, int TY, int nu2) {
-    Region g = make_region(tx0, ty0, TX, TY, 2 * nu2 + 1, Hh.lv[0].n);
+    Region g = make_region(tx0, ty0, TX, TY, 2 * nu2 + 1, Hh.lv[0].n, 4);
     for (int k = 1; k <= l; ++k) {
         int wx0, wy0, wx1, wy1;
         coarse_window(g, Hh.lv[k].n, wx0, wy0, wx1, wy1);
-        g = make_region(wx0, wy0, wx1 - wx0 + 1, wy1 - wy0 + 1, 2 * nu2, Hh.lv[k].n);
+        g = make_region(wx0, wy0, wx1 - wx0 + 1, wy1 - wy0 + 1, 2 * nu2, Hh.lv[k].n, 4);
     }
     return g;
 }
@@ -460,7 +532,17 @@ __device__ void stage_cascade(const Lvl<float> F, const Region &g, const Cascade
                               int m) {
     const int n = F.n;
     const bool scr = F.d != nullptr;
-    for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
+    if (n % 4 == 0) {  // whole rows in 16-byte copies
+        for_groups<float>(g, n, [&](int li, int gi, bool in) {
+            if (scr) cp_async16(t.sd + li, F.d + gi, in);
+            cp_async16(t.su0 + li, F.u[0] + gi, in);
+            cp_async16(t.sf0 + li, F.f[0] + gi, in);
+            if (NC > 1) {
+                cp_async16(t.su1 + li, F.u[1] + gi, in);
+                cp_async16(t.sf1 + li, F.f[1] + gi, in);
+            }
+        });
+    } else for (Walk w(threadIdx.x, blockDim.x, g.RX); w.q < g.R; w.next()) {
         const int x = g.ox + w.col, y = g.oy + w.row;
         const bool in = x >= 0 && x < n && y >= 0 && y < n;
         const int gi = in ? y * n + x : 0, li = w.q;
