@@ -100,7 +100,8 @@ typedef struct {
                                 /* history extrapolated in xi, linear/quadratic */
     int tile_x, tile_y;         /* output tile of the grid-wide multigrid      */
                                 /* levels staged in shared memory (both forms); */
-                                /* even, 0 = default 32 x 16                     */
+                                /* even, 0 = default 32 x 16 (QS_FP64 on grids  */
+                                /* of 512^2 and more: 64 x 32)                  */
     int omega_pct;              /* red-black smoother over-relaxation, percent: */
                                 /* u += omega (u_GS - u), omega = omega_pct/100 */
                                 /* in [0.5, 1.95]; 0 = default (1.2)            */
