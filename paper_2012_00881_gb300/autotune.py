@@ -4,7 +4,7 @@ For each transverse size in a batch it times candidate engine settings and
 keeps the fastest:
 
 * the output tile of the grid-wide multigrid levels staged in shared memory
-  (tile_x, tile_y, refined form),
+  (tile_x, tile_y; both forms stage their grid levels),
 * the red-black sweeps before and after the coarse correction (pre_sweeps,
   post_sweeps) and their over-relaxation factor (omega_pct),
 * the side below which a level is relaxed by one thread block
@@ -29,7 +29,7 @@ from typing import Dict, List, Sequence
 from . import _binding as B
 
 DEFAULT_TILES = ((32, 16), (32, 32), (64, 32))
-DEFAULT_SWEEPS = ((2, 2), (3, 3))
+DEFAULT_SWEEPS = ((3, 2), (2, 2), (3, 3))
 DEFAULT_COARSE = (16, 32)
 DEFAULT_OMEGAS = (0,)  # 0: the library default
 
